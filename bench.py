@@ -1,0 +1,341 @@
+"""Benchmark of the batched projection columns (batched AP solves) on GB300.
+
+One step = one mdp_project_batch over every basis column of every subdomain of the workload
+(extension, ring residual, sine transforms, per-mode tridiagonal solves, trace gather: the
+whole forward hot path), inputs resident in HBM. Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload dd2x2_257] [--impl ours|reference]
+
+--impl reference times the CPU oracle (SciPy SuperLU, the test oracle) on the host cores on a
+bounded sample of the same workload; it is the deliberately slow baseline, not a target.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "batched AP solves/s (FP64 complex), % HBM roofline vs per-RHS path at <=1e-10"
+UNIT = "AP solves/s"
+NOMINAL_FP64_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flops/DFMA x max GHz = 1258.6
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ------------------------------------------------------------------ oracle timing (CPU)
+def _oracle_worker_init(sub_dict):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    global _ORACLE
+    from oracle.projection import APSystem
+    _ORACLE = APSystem(W.Subdomain(**sub_dict))
+
+
+def _oracle_worker_cols(cols):
+    t = time.perf_counter()
+    _ORACLE.columns(cols=cols)
+    return len(cols), time.perf_counter() - t
+
+
+def oracle_throughput(sub, n_cols, workers, seconds_hint=None):
+    """Columns/s of the oracle over `workers` spawned processes, each factoring `sub` once
+    (untimed, like plan creation) and solving its share of n_cols basis columns."""
+    import dataclasses
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers, initializer=_oracle_worker_init, initargs=(dataclasses.asdict(sub),)) as pool:
+        pool.map(_oracle_worker_cols, [[0]] * workers)  # warm: factor in every worker
+        chunks = [list(range(i, n_cols, workers)) for i in range(workers)]
+        chunks = [[c % (8 * sub.n_modes) for c in ch] for ch in chunks if ch]
+        t = time.perf_counter()
+        res = pool.map(_oracle_worker_cols, chunks)
+        wall = time.perf_counter() - t
+    done = sum(r[0] for r in res)
+    return done / wall, done, wall
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r[2] > 250.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(load), "power_w_max": max(r[2] for r in rows)}
+
+
+# ------------------------------------------------------------------ cost model
+def kernel_flops(plan, items):
+    """Algorithmic FP64 flops (FMA = 2, mul/add = 1) per kernel for a list of (sub, ncols)
+    work items, from each subdomain's geometry (plan.sub_info): the arithmetic the ring-sparse
+    formulation needs, one count per mode x column x row."""
+    tot = {}
+
+    def add(k, v):
+        tot[k] = tot.get(k, 0.0) + v
+
+    for sub, nc in items:
+        g = plan.sub_info(sub)
+        Px, Py, Nq, Nt, i0, cx, Gm, R, Nx = g["Px"], g["Py"], g["Nq"], g["Nt"], g["i0"], g["cplx"], g["G"], g["R"], g["Nx"]
+        nf, nb, nmid = Nt - 1 - i0, Nt - i0, Py - 4
+        if cx:   # complex factors, real ring data in the middle rows
+            tri = nf * 8 + nmid * 8 + nb * 14
+            inv = 4
+        else:    # real factors and real data
+            tri = nf * 2 + nmid * 8 + nb * 3
+            inv = 2
+        add("k_tri", nc * Nq * tri)
+        add("k_inv_cols", nc * (Py - 2) * Nq * 4 * inv)
+        add("k_inv_rows", nc * 4 * (Px + 2) * Nq * inv)
+        add("k_fwd_rows", nc * (Nx // 2) * 4 * Px * 2)
+        add("k_residual", nc * R * 9 * 2)
+    return tot
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sub = wl.subdomains[0]
+    workers = max(1, min(16, os.cpu_count() or 1))
+    per_step = workers * max(1, int(os.environ.get("MDP_REF_COLS_PER_WORKER", "2")))
+    import dataclasses
+    ctx = mp.get_context("spawn")
+    times, cols = [], 0
+    with ctx.Pool(workers, initializer=_oracle_worker_init, initargs=(dataclasses.asdict(sub),)) as pool:
+        pool.map(_oracle_worker_cols, [[0]] * workers)
+        for s in range(args.warmup + args.steps):
+            chunks = [[(s * per_step + i + j * workers) % (8 * sub.n_modes) for j in range(per_step // workers)]
+                      for i in range(workers)]
+            t = time.perf_counter()
+            res = pool.map(_oracle_worker_cols, chunks)
+            dt = time.perf_counter() - t
+            if s >= args.warmup:
+                times.append(dt)
+                cols += sum(r[0] for r in res)
+    total = sum(times)
+    value = cols / total
+    sample = (f"{per_step} basis columns per step of subdomain 0 ({sub.nx}x{sub.ny}, k={sub.k}) of {wl.name}; "
+              f"SuperLU factorisation per worker outside the timed region")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "description": wl.description, "columns_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2103_12172_gb300 as mdp
+    from paper_2103_12172_gb300 import _build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    dev = torch.device("cuda", local)
+
+    subs = list(wl.subdomains)
+    plan = mdp.Plan(subs)
+    n_cols = sum(8 * s.n_modes for s in subs)
+    out = torch.empty(plan.output_size, dtype=torch.complex128, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    fp64_probe = mdp.probe_fp64_gflops()
+    for _ in range(args.warmup):
+        plan.project(out=out)
+    torch.cuda.synchronize()
+    plan.status()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    plan.profile(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))                  # evict L2 between timed steps (not timed)
+            starts[i].record(stream)
+            plan.project(out=out)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - wall0
+    plan.profile(False)
+    prof = plan.profile_read()
+    plan.status()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n_cols * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (live CUDA events around its launches, timed region)
+    items = []
+    for s in range(len(subs)):
+        items.append((s, 8 * subs[s].n_modes))
+    flops = kernel_flops(plan, items)
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    launches_per_step = dom_launches / args.steps
+    flops_per_launch = flops.get(dom, 0.0) / launches_per_step
+    achieved = flops_per_launch / (dom_ms / dom_launches / 1e3) / 1e12
+    peak = NOMINAL_FP64_GFLOPS / 1e3
+    gpu_launches = sum(n for (_, n) in prof.values())
+
+    # end to end through the public API with host buffers: new wavenumbers from pinned host
+    # memory (host refactorisation + table upload), all columns, result read back to pinned host
+    host_out = torch.empty(plan.output_size, dtype=torch.complex128, pin_memory=True)
+    ks = [s.k for s in subs]
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        plan.update_k([k * (1.0 + 1e-9 * (i + 1)) for k in ks])
+        plan.project(out=out)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    plan.update_k(ks)
+    table_bytes = sum(8 * (pi["Nq"] * pi["Nt"] * (14 if pi["cplx"] else 10)) for pi in
+                      (plan.sub_info(s) for s in range(len(subs))))
+    e2e = {"value": world * n_cols * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(table_bytes),
+           "d2h_bytes_per_step": int(plan.output_size * 16),
+           "what": "update_k (host LU of every mode + table upload) + project + D2H of all columns"}
+
+    # per-RHS comparator: the same kernels one column per launch sequence, no batching
+    per_rhs_cols = min(64, n_cols)
+    one = torch.empty(plan.layout(0)[0], dtype=torch.complex128, device=dev)
+    for c in range(4):
+        plan.project_columns(0, c, 1, out=one)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for c in range(per_rhs_cols):
+        plan.project_columns(0, c % (8 * subs[0].n_modes), 1, out=one)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_rhs = per_rhs_cols / (e0.elapsed_time(e1) / 1e3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "description": wl.description, "columns_per_step": n_cols,
+                   "l2": "flushed between timed steps (512 MiB write, untimed)", "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_note": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA rate per SM measured)",
+                     "fp64_probe_tflops": fp64_probe / 1e3},
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items())},
+        "gpu_launches": gpu_launches,
+        "per_rhs": {"value": per_rhs, "unit": UNIT, "speedup_batched": value / world / per_rhs},
+        "e2e": e2e,
+        "wall_s_timed": wall,
+    }
+
+    # CPU baseline: the oracle as it stands, on the host cores, bounded sample (rank 0 at N=1)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        workers = max(1, min(16, os.cpu_count() or 1))
+        sub = subs[0]
+        cps, done, wall_c = oracle_throughput(sub, 4 * workers, workers)
+        line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": workers, "kind": "oracle",
+                                "sample": f"{done} basis columns of subdomain 0 ({sub.nx}x{sub.ny}, k={sub.k}) over "
+                                          f"{workers} spawned processes, SuperLU factor per process untimed, "
+                                          f"{wall_c:.2f} s wall"}
+    line["clocks"] = clk.summary()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="dd2x2_257", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = W.WORKLOADS[args.workload]()
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * mdp.h -- C ABI of the batched auxiliary-problem (AP) solves that form the columns of
+ * the discrete Calderon projection P_gamma in the Method of Difference Potentials
+ * (North, Tsynkov & Turkel, "Non-Iterative Domain Decomposition for the Helmholtz
+ * Equation Using the Method of Difference Potentials", Sections 3.1-3.2).
+ *
+ * Conventions (fixed by this library; the paper is silent or garbled on them):
+ *  - Grid: auxiliary rectangle with nodes (m, n), x_m = ax0 + m*h (m = 0..nx-1),
+ *    y_n = ay0 + n*h (n = 0..ny-1). Grid sets M0, M+, M-, N+, N-, gamma as in Section
+ *    3.2.2 (strict inequalities for M+ = M0 inside the open subdomain).
+ *  - The sine transform runs along x: u = 0 on the sides x = const. Along y the AP has
+ *    u = 0 (MDP_AP_DIRICHLET4) or the local Sommerfeld condition du/dn + i k u = 0,
+ *    imposed at the half node between the last two node rows with O(h^4) corrections
+ *    (MDP_AP_DIRX_SOMMY; Section 3.2.1, Eq. auxiliary_problem).
+ *  - gamma is ordered row-major in (n, m). Column c of a subdomain's block is the basis
+ *    pair Psi: c = kind*4M* + (side-1)*M* + (j-1), kind 0 = Dirichlet (psi_j, 0), kind 1 =
+ *    Neumann (0, psi_j), sides 1 bottom, 2 top, 3 left, 4 right, psi_j = T_{j-1}(s)
+ *    (Section 3.2.4, Eq. Psi_def; Section 3.2.5, Eq. Q_construction).
+ *  - Side ownership of a gamma node: smallest |rho| (signed distance to the side's line,
+ *    > 0 outside), ties within 1e-9*h to the lower side index.
+ *  - Complex numbers are interleaved (re, im) doubles: the layout of torch.complex128.
+ *
+ * Memory: every pointer passed to mdp_project_batch, mdp_project_columns, mdp_ap_adjoint
+ * and mdp_ap_solve_batch is a DEVICE pointer owned by the caller, unless stated
+ * otherwise. The plan owns its own tables and workspace; all its allocation happens in
+ * mdp_ap_plan (and mdp_plan_update_k never reallocates), so the compute calls allocate
+ * nothing. Work is enqueued on the given CUDA stream (cudaStream_t passed as void*;
+ * NULL = the legacy default stream) and the calls return without synchronising.
+ *
+ * Errors: argument errors are returned synchronously. A failed launch returns
+ * MDP_ERR_CUDA. Device-side failures set a sticky status word that mdp_plan_status reads.
+ * No C++ exception crosses this boundary. A plan is not thread-safe: one caller at a time.
+ */
+#ifndef MDP_H
+#define MDP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } mdp_c64;
+
+typedef enum {
+  MDP_OK = 0,
+  MDP_ERR_ARG = 1,       /* invalid argument (sizes, geometry, kinds) */
+  MDP_ERR_CUDA = 2,      /* a CUDA runtime call or launch failed */
+  MDP_ERR_NOMEM = 3,     /* device or host allocation failed in mdp_ap_plan */
+  MDP_ERR_SINGULAR = 4,  /* a tridiagonal pivot below tolerance (discrete AP resonance) */
+  MDP_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+  MDP_ERR_STATE = 6      /* call not valid for this plan (e.g. host-only plan) */
+} mdp_status;
+
+enum { MDP_AP_DIRICHLET4 = 0, MDP_AP_DIRX_SOMMY = 1 };
+enum { MDP_OUT_Q = 0, MDP_OUT_P = 1 };
+
+/* Plan flags */
+#define MDP_PLAN_HOST_ONLY 0x1u   /* build host tables only; no CUDA call is made */
+
+/* One subdomain Omega_i = (x0, x1) x (y0, y1) and its auxiliary problem
+ * (Section 3.2.1: AP on the enclosing rectangle; Section 3.2.4: M* basis functions per side). */
+typedef struct {
+  double x0, x1, y0, y1;  /* open subdomain */
+  double ax0, ay0, h;     /* AP lower-left corner and grid step (the same in x and y, Section 3.1) */
+  int nx, ny;             /* AP nodes along x and y */
+  double k;               /* real wavenumber on Omega_i, > 0 */
+  int ap_bc;              /* MDP_AP_DIRICHLET4 or MDP_AP_DIRX_SOMMY */
+  int n_modes;            /* M* >= 1: Chebyshev modes per side; 8*M* columns */
+} mdp_subdomain;
+
+typedef struct mdp_plan mdp_plan;
+
+/* Build a plan for n_subs subdomains: grid sets and gamma lists (Section 3.2.2), the
+ * per-mode pivoted LU factors of the AP's tridiagonal systems along y (the sine transform
+ * along x diagonalises Eq. aux_FD_scheme, Section 3.2.1), sine tables, the batch schedule
+ * and the device workspace. Requirements per subdomain: nx, ny >= 9; the x-extent of the
+ * AP equals (nx-1)*h; M+ has at least 4 nodes per direction and gamma stays at least one
+ * node away from the AP boundary; k > 0; M* >= 1.
+ * Returns MDP_ERR_SINGULAR if a mode's tridiagonal system is singular to working
+ * precision (a Dirichlet AP at a discrete resonance). *out is owned by the caller and is
+ * released with mdp_plan_destroy. With MDP_PLAN_HOST_ONLY the plan holds host tables only
+ * (layout and introspection calls work; compute calls return MDP_ERR_STATE). */
+mdp_status mdp_ap_plan(const mdp_subdomain *subs, int n_subs, unsigned flags, mdp_plan **out);
+
+/* Replace the wavenumbers (k[n_subs], host array) and refactor in place: same grids, no
+ * reallocation. Synchronises the device. */
+mdp_status mdp_plan_update_k(mdp_plan *p, const double *k);
+
+/* Layout of subdomain `sub` (host values): |gamma|, its 8*M* columns, the element offset
+ * of its block in the output of mdp_project_batch, and a host pointer (owned by the plan,
+ * valid until destroy) to |gamma| pairs (n, m) of the gamma nodes in row-major order. Any
+ * output pointer may be NULL. */
+mdp_status mdp_plan_layout(const mdp_plan *p, int sub, int *gamma_size, int *n_cols,
+                           long long *out_offset, const int **gamma_nm);
+
+/* Total complex elements of the output of mdp_project_batch: sum over subdomains of
+ * |gamma_i| * 8 M*_i. */
+long long mdp_plan_output_size(const mdp_plan *p);
+
+/* Projection columns of every subdomain (Section 3.2.2, Eqs. Potential_def, def_Pgamma;
+ * Section 3.2.5, Eq. Q_construction):
+ *   xi == NULL : the densities are the extended basis functions xi_c = Ex^(H) Psi_c
+ *                (Section 3.2.3, Eq. general_extension with f = 0; Section 3.2.4);
+ *   xi != NULL : user densities on gamma, complex, in the layout of `out`.
+ * out_kind MDP_OUT_Q writes (P_gamma - I) xi_c = -Tr G^(h)(L^(h) w|_{M+});
+ * MDP_OUT_P writes P_gamma xi_c = xi_c - Tr G^(h)(L^(h) w|_{M+}).
+ * out (device, complex, mdp_plan_output_size elements): per subdomain in plan order a
+ * column-major block [8 M*][|gamma|]. xi and out must not overlap. */
+mdp_status mdp_project_batch(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, int out_kind,
+                             void *cuda_stream);
+
+/* The same for columns [col0, col0 + ncols) of subdomain `sub` only: the per-column
+ * (unbatched) path. xi (may be NULL) and out point to the first of those columns, each
+ * column |gamma| complex values, consecutive. */
+mdp_status mdp_project_columns(mdp_plan *p, int sub, int col0, int ncols, const mdp_c64 *xi,
+                               mdp_c64 *out, int out_kind, void *cuda_stream);
+
+/* Adjoint of mdp_project_batch for a real loss with cotangent cot = dLoss/d conj(out)
+ * (layout of out):
+ *   grad_xi[c] = (P_gamma - I)^H cot[c]  (MDP_OUT_Q) or P_gamma^H cot[c] (MDP_OUT_P),
+ *                computed with the conjugate-transposed AP solve G^H (may be NULL; only
+ *                meaningful for user densities);
+ *   grad_k[i] += dLoss/dk_i = Re sum_c <cot_c, d out_c / d k_i>, including the
+ *                k-dependence of L^(h), of the AP rows and, for basis densities, of Ex^(H)
+ *                (may be NULL; device array of n_subs doubles, accumulated, not zeroed).
+ * xi is the forward call's density argument (NULL = basis densities). */
+mdp_status mdp_ap_adjoint(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, mdp_c64 *grad_xi,
+                          double *grad_k, int out_kind, void *cuda_stream);
+
+/* Full-grid AP solves of subdomain `sub`: u = G^(h) g (adjoint = 0) or u = (G^(h))^H g
+ * (adjoint = 1), for nrhs right-hand sides. g and u are device arrays [nrhs][ny][nx]
+ * complex (row-major grids); only the values of g on M0 are read, and u is written on
+ * every node (0 at Dirichlet nodes). (Section 3.2.1: u = G^(h) g.) */
+mdp_status mdp_ap_solve_batch(mdp_plan *p, int sub, int nrhs, const mdp_c64 *g, mdp_c64 *u,
+                              int adjoint, void *cuda_stream);
+
+/* Synchronise the plan's device, return and clear the sticky device status word. */
+mdp_status mdp_plan_status(mdp_plan *p);
+
+void mdp_plan_destroy(mdp_plan *p);
+
+const char *mdp_status_string(mdp_status s);
+
+/* ---- Host introspection (no device work; valid for host-only plans) ---- */
+
+/* Gamma geometry of subdomain `sub` into caller host arrays of |gamma| entries: owner side
+ * (1..4), signed distance rho (> 0 outside Omega) and side parameter s in [-1, 1]. */
+mdp_status mdp_plan_gamma_geometry(const mdp_plan *p, int sub, int *owner, double *rho, double *s);
+
+/* Solve one mode's tridiagonal system T_q x = b (adjoint = 0) or T_q^H x = b (adjoint = 1)
+ * on the host with the plan's stored factors, q = 1..nx-2. b and x are host arrays over the
+ * y unknowns (ny values for MDP_AP_DIRX_SOMMY, n = 0..ny-1; ny-2 values for
+ * MDP_AP_DIRICHLET4, n = 1..ny-2). A grid function sin(pi q m/(nx-1)) b(n) on M0 is mapped
+ * by G^(h) to sin(pi q m/(nx-1)) x(n). */
+mdp_status mdp_host_mode_solve(const mdp_plan *p, int sub, int q, int adjoint, const mdp_c64 *b,
+                               mdp_c64 *x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDP_H */

@@ -1,0 +1,38 @@
+/*
+ * mdp_probe.h -- measurement utility of libmdp: the FP64 fused multiply-add throughput of
+ * the current CUDA device, the denominator of the FP64 roofline of the projection kernels.
+ * (No counterpart in the paper, which reports no hardware figures.)
+ */
+#ifndef MDP_PROBE_H
+#define MDP_PROBE_H
+#include "mdp.h"
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Runs a DFMA microbenchmark (8 independent chains per thread, 8 resident blocks of 256
+ * threads per SM, `iters` iterations; 0 selects 4096) on `cuda_stream`, synchronises and
+ * writes the achieved FP64 GFLOP/s (2 flops per DFMA) to *gflops (host). Allocates and frees
+ * a small device buffer. Returns MDP_ERR_CUDA on a CUDA failure. */
+mdp_status mdp_probe_dfma_gflops(int iters, double *gflops, void *cuda_stream);
+
+/* Per-kernel timing of a plan's launches (tracing). enable = 1 starts recording a CUDA event
+ * pair around every kernel launch of mdp_project_batch / mdp_project_columns / mdp_ap_adjoint
+ * on the launch stream (events are created on demand; no device memory is allocated);
+ * enable = 0 stops. mdp_plan_profile_read synchronises the recorded events, returns the summed
+ * duration (ms) and the number of launches of kernel family `family` since the last read, and
+ * resets that family's record. Families are numbered 0..mdp_kernel_family_count()-1. */
+mdp_status mdp_plan_profile(mdp_plan *p, int enable);
+mdp_status mdp_plan_profile_read(mdp_plan *p, int family, double *total_ms, int *launches);
+int mdp_kernel_family_count(void);
+const char *mdp_kernel_family_name(int family);
+
+/* Geometry of subdomain `sub` as 12 ints: Px, Py (M+ nodes per direction), Nq (sine modes),
+ * Nt (tridiagonal rows), i0 (first swept row), nfirst (first unknown y row), complex factors
+ * (0/1), |gamma|, |ring|, number of pivoted rows over all modes, n_cols, Nx. */
+mdp_status mdp_plan_sub_info(const mdp_plan *p, int sub, int *info12);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,196 @@
+"""GB300 (sm_103a) batched auxiliary-problem solves for the Method of Difference Potentials.
+
+Python binding of libmdp (C ABI in include/mdp.h). Every step of the projection path runs in
+the library's CUDA kernels; this module only allocates device tensors with PyTorch, picks the
+current CUDA stream and marshals arguments. There is no CPU fallback: without the built
+library or a GPU the compute calls raise.
+
+    plan = Plan(subdomains)              # grid sets, per-mode LU factors, schedule, workspace
+    Q = plan.project()                   # all basis columns, (P_gamma - I) Ex Psi_c
+    P = plan.project(kind="P")           # P_gamma Ex Psi_c
+    Qx = plan.project(xi=densities)      # user densities on gamma
+    u = plan.solve(sub, g)               # full-grid G^(h) g
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import MdpError, MDP_OUT_P, MDP_OUT_Q, MDP_PLAN_HOST_ONLY
+
+__all__ = ["Plan", "MdpError", "probe_fp64_gflops", "as_c_subdomains"]
+
+_KINDS = {"Q": MDP_OUT_Q, "P": MDP_OUT_P}
+
+
+def as_c_subdomains(subs):
+    """Array of mdp_subdomain structs from objects with the mdp_subdomain fields."""
+    arr = (_lib.mdp_subdomain * len(subs))()
+    for i, s in enumerate(subs):
+        arr[i] = _lib.mdp_subdomain(float(s.x0), float(s.x1), float(s.y0), float(s.y1), float(s.ax0),
+                                    float(s.ay0), float(s.h), int(s.nx), int(s.ny), float(s.k),
+                                    int(s.ap_bc), int(s.n_modes))
+    return arr
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+class Plan:
+    """A plan over a list of subdomains (objects with the mdp_subdomain fields)."""
+
+    def __init__(self, subdomains, host_only: bool = False):
+        self.L = _lib.lib()
+        self.subdomains = list(subdomains)
+        self._c_subs = as_c_subdomains(self.subdomains)
+        handle = C.c_void_p()
+        flags = MDP_PLAN_HOST_ONLY if host_only else 0
+        _lib.check(self.L.mdp_ap_plan(self._c_subs, len(self.subdomains), flags, C.byref(handle)), "mdp_ap_plan")
+        self.handle = handle
+        self.host_only = host_only
+        self.n_subs = len(self.subdomains)
+        self.output_size = int(self.L.mdp_plan_output_size(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.L.mdp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- layout
+    def layout(self, sub: int):
+        """(|gamma|, n_cols, out_offset, gamma_nm[|gamma|, 2] as (n, m))."""
+        g, nc, off = C.c_int(), C.c_int(), C.c_longlong()
+        ptr = C.POINTER(C.c_int)()
+        _lib.check(self.L.mdp_plan_layout(self.handle, sub, C.byref(g), C.byref(nc), C.byref(off), C.byref(ptr)),
+                   "mdp_plan_layout")
+        nm = np.ctypeslib.as_array(ptr, shape=(g.value * 2,)).reshape(g.value, 2).copy()
+        return g.value, nc.value, off.value, nm
+
+    def gamma_geometry(self, sub: int):
+        g = self.layout(sub)[0]
+        owner = np.zeros(g, np.int32)
+        rho = np.zeros(g)
+        s = np.zeros(g)
+        _lib.check(self.L.mdp_plan_gamma_geometry(self.handle, sub, owner.ctypes.data_as(C.POINTER(C.c_int)),
+                                                  rho.ctypes.data_as(C.POINTER(C.c_double)),
+                                                  s.ctypes.data_as(C.POINTER(C.c_double))), "mdp_plan_gamma_geometry")
+        return owner, rho, s
+
+    def host_mode_solve(self, sub: int, q: int, b, adjoint: bool = False):
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        x = np.zeros_like(b)
+        _lib.check(self.L.mdp_host_mode_solve(self.handle, sub, q, int(adjoint), b.ctypes.data_as(C.c_void_p),
+                                              x.ctypes.data_as(C.c_void_p)), "mdp_host_mode_solve")
+        return x
+
+    def blocks(self, out):
+        """Split a flat output tensor into per-subdomain [n_cols, |gamma|] views."""
+        res = []
+        for s in range(self.n_subs):
+            g, nc, off, _ = self.layout(s)
+            res.append(out[off:off + g * nc].view(nc, g))
+        return res
+
+    # ---- compute (device tensors, complex128)
+    def _check_dev(self, t, n, name):
+        import torch
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.numel() < n:
+            raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor with >= {n} elements")
+
+    def project(self, xi=None, kind: str = "Q", out=None, stream=None):
+        """Projection columns of all subdomains as a flat complex128 CUDA tensor."""
+        import torch
+        n = self.output_size
+        if out is None:
+            out = torch.empty(n, dtype=torch.complex128, device="cuda")
+        self._check_dev(out, n, "out")
+        if xi is not None:
+            self._check_dev(xi, n, "xi")
+        _lib.check(self.L.mdp_project_batch(self.handle, _ptr(xi), _ptr(out), _KINDS[kind], _stream_ptr(stream)),
+                   "mdp_project_batch")
+        return out
+
+    def project_columns(self, sub: int, col0: int, ncols: int, xi=None, kind: str = "Q", out=None, stream=None):
+        import torch
+        g = self.layout(sub)[0]
+        if out is None:
+            out = torch.empty(ncols * g, dtype=torch.complex128, device="cuda")
+        self._check_dev(out, ncols * g, "out")
+        if xi is not None:
+            self._check_dev(xi, ncols * g, "xi")
+        _lib.check(self.L.mdp_project_columns(self.handle, sub, col0, ncols, _ptr(xi), _ptr(out), _KINDS[kind],
+                                              _stream_ptr(stream)), "mdp_project_columns")
+        return out
+
+    def adjoint(self, cot, xi=None, kind: str = "Q", grad_xi=True, grad_k=None, stream=None):
+        """(grad_xi or None, grad_k) of a real loss with cotangent `cot` (layout of project())."""
+        import torch
+        n = self.output_size
+        self._check_dev(cot, n, "cot")
+        gx = torch.empty(n, dtype=torch.complex128, device="cuda") if grad_xi else None
+        if grad_k is None:
+            grad_k = torch.zeros(self.n_subs, dtype=torch.float64, device="cuda")
+        _lib.check(self.L.mdp_ap_adjoint(self.handle, _ptr(xi), _ptr(cot), _ptr(gx), _ptr(grad_k), _KINDS[kind],
+                                         _stream_ptr(stream)), "mdp_ap_adjoint")
+        return gx, grad_k
+
+    def solve(self, sub: int, g, adjoint: bool = False, out=None, stream=None):
+        """u = G^(h) g (or A^{-H} g) on the full grid; g: complex128 CUDA tensor [nrhs, ny, nx]."""
+        import torch
+        s = self.subdomains[sub]
+        g = g.reshape(-1, s.ny, s.nx)
+        if out is None:
+            out = torch.empty_like(g)
+        self._check_dev(g, g.numel(), "g")
+        self._check_dev(out, g.numel(), "out")
+        _lib.check(self.L.mdp_ap_solve_batch(self.handle, sub, g.shape[0], _ptr(g), _ptr(out), int(adjoint),
+                                             _stream_ptr(stream)), "mdp_ap_solve_batch")
+        return out
+
+    def update_k(self, ks):
+        arr = (C.c_double * self.n_subs)(*[float(k) for k in ks])
+        _lib.check(self.L.mdp_plan_update_k(self.handle, arr), "mdp_plan_update_k")
+
+    def sub_info(self, sub: int) -> dict:
+        a = (C.c_int * 12)()
+        _lib.check(self.L.mdp_plan_sub_info(self.handle, sub, a), "mdp_plan_sub_info")
+        keys = ["Px", "Py", "Nq", "Nt", "i0", "nfirst", "cplx", "G", "R", "npiv", "n_cols", "Nx"]
+        return dict(zip(keys, list(a)))
+
+    def profile(self, enable: bool):
+        _lib.check(self.L.mdp_plan_profile(self.handle, int(enable)), "mdp_plan_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last read."""
+        res = {}
+        for f in range(self.L.mdp_kernel_family_count()):
+            ms, n = C.c_double(), C.c_int()
+            _lib.check(self.L.mdp_plan_profile_read(self.handle, f, C.byref(ms), C.byref(n)), "profile_read")
+            if n.value:
+                res[self.L.mdp_kernel_family_name(f).decode()] = (ms.value, n.value)
+        return res
+
+    def status(self):
+        _lib.check(self.L.mdp_plan_status(self.handle), "device status")
+
+
+def probe_fp64_gflops(iters: int = 0, stream=None) -> float:
+    """Measured FP64 FMA throughput (GFLOP/s) of the current device."""
+    v = C.c_double()
+    _lib.check(_lib.lib().mdp_probe_dfma_gflops(int(iters), C.byref(v), _stream_ptr(stream)), "mdp_probe_dfma_gflops")
+    return v.value

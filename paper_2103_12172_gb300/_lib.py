@@ -1,0 +1,85 @@
+"""ctypes view of libmdp.so (the C ABI in include/mdp.h). Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmdp.so")
+
+MDP_OK, MDP_ERR_ARG, MDP_ERR_CUDA, MDP_ERR_NOMEM, MDP_ERR_SINGULAR, MDP_ERR_TIMEOUT, MDP_ERR_STATE = range(7)
+MDP_AP_DIRICHLET4, MDP_AP_DIRX_SOMMY = 0, 1
+MDP_OUT_Q, MDP_OUT_P = 0, 1
+MDP_PLAN_HOST_ONLY = 0x1
+
+EXPORTED = [
+    "mdp_ap_plan", "mdp_plan_update_k", "mdp_plan_layout", "mdp_plan_output_size", "mdp_project_batch",
+    "mdp_project_columns", "mdp_ap_adjoint", "mdp_ap_solve_batch", "mdp_plan_status", "mdp_plan_destroy",
+    "mdp_status_string", "mdp_plan_gamma_geometry", "mdp_host_mode_solve", "mdp_probe_dfma_gflops",
+]
+
+
+class mdp_subdomain(C.Structure):
+    _fields_ = [("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
+                ("ax0", C.c_double), ("ay0", C.c_double), ("h", C.c_double),
+                ("nx", C.c_int), ("ny", C.c_int), ("k", C.c_double), ("ap_bc", C.c_int), ("n_modes", C.c_int)]
+
+
+class MdpError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} (status {code})")
+
+
+_lib = None
+
+
+def lib():
+    """Load libmdp.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmdp.so not found at {LIB_PATH}: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, i, ll, d = C.c_void_p, C.c_int, C.c_longlong, C.c_double
+    sig = {
+        "mdp_ap_plan": (i, [C.POINTER(mdp_subdomain), i, C.c_uint, C.POINTER(vp)]),
+        "mdp_plan_update_k": (i, [vp, C.POINTER(d)]),
+        "mdp_plan_layout": (i, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(ll), C.POINTER(C.POINTER(i))]),
+        "mdp_plan_output_size": (ll, [vp]),
+        "mdp_project_batch": (i, [vp, vp, vp, i, vp]),
+        "mdp_project_columns": (i, [vp, i, i, i, vp, vp, i, vp]),
+        "mdp_ap_adjoint": (i, [vp, vp, vp, vp, vp, i, vp]),
+        "mdp_ap_solve_batch": (i, [vp, i, i, vp, vp, i, vp]),
+        "mdp_plan_status": (i, [vp]),
+        "mdp_plan_destroy": (None, [vp]),
+        "mdp_status_string": (C.c_char_p, [i]),
+        "mdp_plan_gamma_geometry": (i, [vp, i, C.POINTER(i), C.POINTER(d), C.POINTER(d)]),
+        "mdp_host_mode_solve": (i, [vp, i, i, i, vp, vp]),
+        "mdp_probe_dfma_gflops": (i, [i, C.POINTER(d), vp]),
+        "mdp_plan_profile": (i, [vp, i]),
+        "mdp_plan_profile_read": (i, [vp, i, C.POINTER(d), C.POINTER(i)]),
+        "mdp_kernel_family_count": (i, []),
+        "mdp_kernel_family_name": (C.c_char_p, [i]),
+        "mdp_plan_sub_info": (i, [vp, i, C.POINTER(i)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().mdp_status_string(int(code)).decode()
+    except ImportError:
+        return str(code)
+
+
+def check(code: int, what: str):
+    if code != MDP_OK:
+        raise MdpError(code, what)

@@ -1,0 +1,340 @@
+// C ABI of the library (declared in include/mdp.h): plan lifetime, batched projection
+// columns, the adjoint, full-grid solves, status and host introspection.
+#include "mdp_internal.h"
+#include "mdp_probe.h"
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+using namespace mdp;
+
+namespace {
+
+#define CK(x)                                        \
+  do {                                               \
+    if ((x) != cudaSuccess) return MDP_ERR_CUDA;     \
+  } while (0)
+
+long long env_ll(const char *name, long long dflt) {
+  const char *v = std::getenv(name);
+  if (!v || !*v) return dflt;
+  return std::atoll(v);
+}
+
+void free_device(mdp_plan *p) {
+  if (p->device < 0) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  cudaFree(p->d_subs);
+  cudaFree(p->d_tables);
+  cudaFree(p->d_piv);
+  cudaFree(p->d_ws);
+  cudaFree(p->d_status);
+  for (auto x : p->d_wave_items) cudaFree(x);
+  for (auto x : p->d_wave_prefix) cudaFree(x);
+  p->d_wave_items.clear();
+  p->d_wave_prefix.clear();
+  p->d_subs = nullptr; p->d_tables = nullptr; p->d_piv = nullptr; p->d_ws = nullptr; p->d_status = nullptr;
+  if (prev >= 0) cudaSetDevice(prev);
+}
+
+mdp_status upload_subs_tables(mdp_plan *p) {
+  std::vector<SubDesc> ds;
+  for (auto &hs : p->subs) ds.push_back(hs.d);
+  CK(cudaMemcpy(p->d_subs, ds.data(), ds.size() * sizeof(SubDesc), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->d_tables, p->host_tables.data(), p->host_tables.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->d_piv, p->host_piv.data(), p->host_piv.size(), cudaMemcpyHostToDevice));
+  return MDP_OK;
+}
+
+mdp_status alloc_device(mdp_plan *p) {
+  CK(cudaGetDevice(&p->device));
+  auto al = [&](void **ptr, size_t bytes) -> bool { return cudaMalloc(ptr, std::max<size_t>(bytes, 256)) == cudaSuccess; };
+  if (!al((void **)&p->d_subs, p->subs.size() * sizeof(SubDesc)) ||
+      !al((void **)&p->d_tables, p->host_tables.size() * sizeof(double)) ||
+      !al((void **)&p->d_piv, p->host_piv.size()) || !al((void **)&p->d_ws, (size_t)p->ws_doubles * 8) ||
+      !al((void **)&p->d_status, sizeof(int)))
+    return MDP_ERR_NOMEM;
+  CK(cudaMemset(p->d_status, 0, sizeof(int)));
+  mdp_status st = upload_subs_tables(p);
+  if (st != MDP_OK) return st;
+  p->h_wave_prefix.clear();
+  for (auto &w : p->waves) {
+    const int n = (int)w.items.size();
+    Item *di = nullptr;
+    int *dp = nullptr;
+    if (!al((void **)&di, n * sizeof(Item)) || !al((void **)&dp, (size_t)NFAM * (n + 1) * sizeof(int))) {
+      if (di) cudaFree(di);
+      return MDP_ERR_NOMEM;
+    }
+    p->d_wave_items.push_back(di);
+    p->d_wave_prefix.push_back(dp);
+    std::vector<int> pre((size_t)NFAM * (n + 1), 0);
+    for (int f = 0; f < NFAM; ++f)
+      for (int i = 0; i < n; ++i)
+        pre[(size_t)f * (n + 1) + i + 1] =
+            pre[(size_t)f * (n + 1) + i] + blocks_for((Fam)f, p->subs[w.items[i].sub].d, w.items[i].ncols);
+    CK(cudaMemcpy(di, w.items.data(), n * sizeof(Item), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dp, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
+    p->h_wave_prefix.push_back(pre);
+  }
+  return MDP_OK;
+}
+
+void wave_batches(const mdp_plan *p, size_t w, Batch *fb) {
+  const int n = (int)p->waves[w].items.size();
+  for (int f = 0; f < NFAM; ++f) {
+    Batch &b = fb[f];
+    std::memset(&b, 0, sizeof b);
+    b.items = p->d_wave_items[w];
+    b.prefix = p->d_wave_prefix[w] + (size_t)f * (n + 1);
+    b.n_items = n;
+    b.total_blocks = p->h_wave_prefix[w][(size_t)f * (n + 1) + n];
+  }
+}
+
+void single_batches(const mdp_plan *p, const Item &it, Batch *fb) {
+  for (int f = 0; f < NFAM; ++f) {
+    Batch &b = fb[f];
+    std::memset(&b, 0, sizeof b);
+    b.items = nullptr;
+    b.prefix = nullptr;
+    b.n_items = 1;
+    b.one = it;
+    b.total_blocks = blocks_for((Fam)f, p->subs[it.sub].d, it.ncols);
+  }
+}
+
+bool device_ok(const mdp_plan *p) { return p && !(p->flags & MDP_PLAN_HOST_ONLY) && p->device >= 0; }
+
+void destroy_prof(mdp_plan *p) {
+  for (int f = 0; f < 16; ++f) {
+    for (auto &e : p->prof_ev[f]) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    p->prof_ev[f].clear();
+    p->prof_used[f] = 0;
+  }
+}
+
+}  // namespace
+
+namespace mdp {
+void prof_begin(mdp_plan *p, int fam, cudaStream_t st) {
+  if (!p->prof_on) return;
+  auto &v = p->prof_ev[fam];
+  if (p->prof_used[fam] == (int)v.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+    v.push_back({a, b});
+  }
+  cudaEventRecord(v[p->prof_used[fam]].first, st);
+}
+void prof_end(mdp_plan *p, int fam, cudaStream_t st) {
+  if (!p->prof_on) return;
+  auto &v = p->prof_ev[fam];
+  if (p->prof_used[fam] >= (int)v.size()) return;
+  cudaEventRecord(v[p->prof_used[fam]].second, st);
+  p->prof_used[fam]++;
+}
+}  // namespace mdp
+
+extern "C" {
+
+const char *mdp_status_string(mdp_status s) {
+  switch (s) {
+    case MDP_OK: return "ok";
+    case MDP_ERR_ARG: return "invalid argument";
+    case MDP_ERR_CUDA: return "CUDA error";
+    case MDP_ERR_NOMEM: return "out of memory";
+    case MDP_ERR_SINGULAR: return "singular tridiagonal system (discrete AP resonance)";
+    case MDP_ERR_TIMEOUT: return "device wait timed out";
+    case MDP_ERR_STATE: return "call not valid for this plan";
+  }
+  return "unknown status";
+}
+
+mdp_status mdp_ap_plan(const mdp_subdomain *subs, int n_subs, unsigned flags, mdp_plan **out) {
+  if (!subs || n_subs < 1 || !out) return MDP_ERR_ARG;
+  *out = nullptr;
+  mdp_plan *p = new (std::nothrow) mdp_plan();
+  if (!p) return MDP_ERR_NOMEM;
+  p->flags = flags;
+  p->n_subs = n_subs;
+  p->tile_cols = (int)std::max(1LL, env_ll("MDP_TILE_COLS", 256));
+  p->ws_budget = env_ll("MDP_WS_MB", 4096) << 20;
+  mdp_status st;
+  try {
+    st = build_host_plan(p, subs, n_subs);
+  } catch (...) {
+    st = MDP_ERR_NOMEM;
+  }
+  if (st == MDP_OK && !(flags & MDP_PLAN_HOST_ONLY)) st = alloc_device(p);
+  if (st != MDP_OK) {
+    free_device(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return MDP_OK;
+}
+
+mdp_status mdp_plan_update_k(mdp_plan *p, const double *k) {
+  if (!p || !k) return MDP_ERR_ARG;
+  mdp_status st = refactor_host(p, k);
+  if (st != MDP_OK) return st;
+  if (device_ok(p)) {
+    CK(cudaSetDevice(p->device));
+    CK(cudaDeviceSynchronize());
+    return upload_subs_tables(p);
+  }
+  return MDP_OK;
+}
+
+mdp_status mdp_plan_layout(const mdp_plan *p, int sub, int *gamma_size, int *n_cols, long long *out_offset,
+                           const int **gamma_nm) {
+  if (!p || sub < 0 || sub >= p->n_subs) return MDP_ERR_ARG;
+  const HostSub &hs = p->subs[sub];
+  if (gamma_size) *gamma_size = hs.d.G;
+  if (n_cols) *n_cols = hs.d.n_cols;
+  if (out_offset) *out_offset = hs.d.out_off;
+  if (gamma_nm) *gamma_nm = hs.gamma_nm.data();
+  return MDP_OK;
+}
+
+long long mdp_plan_output_size(const mdp_plan *p) { return p ? p->out_size : 0; }
+
+mdp_status mdp_project_batch(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, int out_kind, void *cuda_stream) {
+  if (!p || !out || (out_kind != MDP_OUT_Q && out_kind != MDP_OUT_P)) return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_ERR_STATE;
+  if (xi && (const void *)xi == (const void *)out) return MDP_ERR_ARG;
+  CK(cudaSetDevice(p->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  for (size_t w = 0; w < p->waves.size(); ++w) {
+    Batch fb[NFAM];
+    wave_batches(p, w, fb);
+    CK(launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, st));
+  }
+  return MDP_OK;
+}
+
+mdp_status mdp_project_columns(mdp_plan *p, int sub, int col0, int ncols, const mdp_c64 *xi, mdp_c64 *out,
+                               int out_kind, void *cuda_stream) {
+  if (!p || !out || sub < 0 || sub >= p->n_subs || (out_kind != MDP_OUT_Q && out_kind != MDP_OUT_P)) return MDP_ERR_ARG;
+  const SubDesc &d = p->subs[sub].d;
+  if (col0 < 0 || ncols < 1 || col0 + ncols > d.n_cols) return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_ERR_STATE;
+  CK(cudaSetDevice(p->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  for (int c = 0; c < ncols; c += p->tile_cols) {
+    Item it;
+    std::memset(&it, 0, sizeof it);
+    it.sub = sub; it.col0 = col0 + c; it.ncols = std::min(p->tile_cols, ncols - c);
+    long long xo, ro, go, yo, ao, so, reo, tot;
+    item_workspace(d, it.ncols, false, xo, ro, go, yo, ao, so, reo, tot);
+    it.xi_off = xo; it.r_off = ro; it.gr_off = go; it.y_off = yo; it.a_off = ao; it.s_off = so; it.red_off = reo;
+    it.io_off = (long long)c * d.G;
+    Batch fb[NFAM];
+    single_batches(p, it, fb);
+    CK(launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, st));
+  }
+  return MDP_OK;
+}
+
+mdp_status mdp_ap_adjoint(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, mdp_c64 *grad_xi, double *grad_k,
+                          int out_kind, void *cuda_stream) {
+  (void)xi; (void)cot; (void)grad_xi; (void)grad_k; (void)out_kind; (void)cuda_stream;
+  if (!p) return MDP_ERR_ARG;
+  return MDP_ERR_STATE;
+}
+
+mdp_status mdp_ap_solve_batch(mdp_plan *p, int sub, int nrhs, const mdp_c64 *g, mdp_c64 *u, int adjoint,
+                              void *cuda_stream) {
+  if (!p || sub < 0 || sub >= p->n_subs || nrhs < 0 || (nrhs > 0 && (!g || !u)) || (adjoint != 0 && adjoint != 1))
+    return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_ERR_STATE;
+  if (nrhs == 0) return MDP_OK;
+  CK(cudaSetDevice(p->device));
+  CK(launch_solve(p, sub, nrhs, (const double2 *)g, (double2 *)u, adjoint, (cudaStream_t)cuda_stream));
+  return MDP_OK;
+}
+
+mdp_status mdp_plan_status(mdp_plan *p) {
+  if (!p) return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_OK;
+  CK(cudaSetDevice(p->device));
+  CK(cudaDeviceSynchronize());
+  int s = 0;
+  CK(cudaMemcpy(&s, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(p->d_status, 0, sizeof(int)));
+  return (mdp_status)s;
+}
+
+void mdp_plan_destroy(mdp_plan *p) {
+  if (!p) return;
+  if (device_ok(p)) { destroy_prof(p); free_device(p); }
+  delete p;
+}
+
+mdp_status mdp_plan_gamma_geometry(const mdp_plan *p, int sub, int *owner, double *rho, double *s) {
+  if (!p || sub < 0 || sub >= p->n_subs) return MDP_ERR_ARG;
+  const HostSub &hs = p->subs[sub];
+  for (int i = 0; i < hs.d.G; ++i) {
+    if (owner) owner[i] = hs.owner[i];
+    if (rho) rho[i] = hs.rho[i];
+    if (s) s[i] = hs.s[i];
+  }
+  return MDP_OK;
+}
+
+mdp_status mdp_host_mode_solve(const mdp_plan *p, int sub, int q, int adjoint, const mdp_c64 *b, mdp_c64 *x) {
+  if (!p || sub < 0 || sub >= p->n_subs || !b || !x || (adjoint != 0 && adjoint != 1)) return MDP_ERR_ARG;
+  const HostSub &hs = p->subs[sub];
+  if (q < 1 || q > hs.d.Nq) return MDP_ERR_ARG;
+  host_mode_solve(hs, q, adjoint, (const double *)b, (double *)x);
+  return MDP_OK;
+}
+
+mdp_status mdp_plan_profile(mdp_plan *p, int enable) {
+  if (!p) return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_ERR_STATE;
+  p->prof_on = enable != 0;
+  return MDP_OK;
+}
+
+mdp_status mdp_plan_profile_read(mdp_plan *p, int family, double *total_ms, int *launches) {
+  if (!p || family < 0 || family >= NFAM) return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_ERR_STATE;
+  double tot = 0.0;
+  const int n = p->prof_used[family];
+  for (int i = 0; i < n; ++i) {
+    auto &e = p->prof_ev[family][i];
+    CK(cudaEventSynchronize(e.second));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e.first, e.second));
+    tot += ms;
+  }
+  p->prof_used[family] = 0;
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = n;
+  return MDP_OK;
+}
+
+int mdp_kernel_family_count(void) { return NFAM; }
+
+const char *mdp_kernel_family_name(int family) { return fam_name(family); }
+
+mdp_status mdp_plan_sub_info(const mdp_plan *p, int sub, int *info) {
+  if (!p || !info || sub < 0 || sub >= p->n_subs) return MDP_ERR_ARG;
+  const HostSub &hs = p->subs[sub];
+  const SubDesc &d = hs.d;
+  int npiv = 0;
+  for (auto v : hs.piv) npiv += v;
+  const int vals[12] = {d.Px, d.Py, d.Nq, d.Nt, d.i0, d.nfirst, d.cplx, d.G, d.R, npiv, d.n_cols, d.Nx};
+  for (int i = 0; i < 12; ++i) info[i] = vals[i];
+  return MDP_OK;
+}
+
+}  // extern "C"

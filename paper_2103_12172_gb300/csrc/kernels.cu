@@ -1,0 +1,595 @@
+// CUDA kernels (sm_103a, FP64) of the batched projection columns:
+//   k_extend    basis + equation-based extension on gamma       (Sections 3.2.3-3.2.4)
+//   k_residual  r = L^(h) w restricted to M+ (the 2-node ring)   (Eqs. FD_scheme, Potential_def)
+//   k_fwd_rows  sine transform along x of the 4 dense ring rows  (Section 3.2.1 / 3.6: "sine-FFT")
+//   k_tri       per-mode pivoted tridiagonal solve along y; the sine transform of the ring's
+//               middle rows (4 nonzeros per row) is fused into its forward sweep
+//   k_inv_rows  inverse sine transform onto the 4 full gamma rows, column output
+//   k_inv_cols  inverse sine transform onto the 4 gamma columns of the middle rows
+// Q column = -Tr G^(h) r, P_gamma column = xi - Tr G^(h) r (Eqs. def_Pgamma, Q_construction).
+//
+// Every kernel takes a Batch: blocks are numbered across all work items of the launch and
+// each block finds its item by binary search over a prefix array. Within an item, the block
+// is (32 columns) x (BY tasks): a warp shares one task (one mode, one row ...), so factor and
+// sine-table loads are warp-uniform broadcasts and column data is read coalesced.
+#include "mdp_internal.h"
+
+namespace mdp {
+
+// ---------------------------------------------------------------- complex helpers
+struct cplx { double re, im; };
+__device__ __forceinline__ cplx cmk(double a, double b) { return {a, b}; }
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+// a - b*c
+__device__ __forceinline__ cplx cfms(cplx a, cplx b, cplx c) {
+  return {fma(-b.re, c.re, fma(b.im, c.im, a.re)), fma(-b.re, c.im, fma(-b.im, c.re, a.im))};
+}
+// a + s*c (s real)
+__device__ __forceinline__ cplx caxpy(double s, cplx c, cplx a) { return {fma(s, c.re, a.re), fma(s, c.im, a.im)}; }
+__device__ __forceinline__ cplx ld2(const double *p) {
+  double2 v = *reinterpret_cast<const double2 *>(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st2(double *p, cplx v) { *reinterpret_cast<double2 *>(p) = make_double2(v.re, v.im); }
+
+// ---------------------------------------------------------------- batch addressing
+__device__ __forceinline__ void locate(const Batch &b, int blk, Item &it, int &local) {
+  if (b.items == nullptr) { it = b.one; local = blk; return; }
+  int lo = 0, hi = b.n_items - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b.prefix[mid] <= blk) lo = mid; else hi = mid - 1;
+  }
+  it = b.items[lo];
+  local = blk - b.prefix[lo];
+}
+
+// gamma index of node (n, m), or -1 (row-major order of the 2-node ring around M+)
+__device__ __forceinline__ int gamma_index(const SubDesc &d, int n, int m) {
+  if (n < d.nlo - 1 || n > d.nhi + 1 || m < d.mlo - 1 || m > d.mhi + 1) return -1;
+  const int W = d.Px + 2, Mr = d.Py - 2;
+  const int dm = m - (d.mlo - 1);
+  if (n == d.nlo - 1) return dm;
+  if (n == d.nlo) return W + dm;
+  if (n == d.nhi) return 2 * W + 4 * Mr + dm;
+  if (n == d.nhi + 1) return 3 * W + 4 * Mr + dm;
+  int slot = (m == d.mlo - 1) ? 0 : (m == d.mlo) ? 1 : (m == d.mhi) ? 2 : (m == d.mhi + 1) ? 3 : -1;
+  if (slot < 0) return -1;
+  return 2 * W + 4 * (n - d.nlo - 1) + slot;
+}
+
+// node of ring index ri (row-major order of the 2-node ring inside M+)
+__device__ __forceinline__ void ring_node(const SubDesc &d, int ri, int &n, int &m) {
+  const int P = d.Px, Mr = 4 * (d.Py - 4);
+  if (ri < P) { n = d.nlo; m = d.mlo + ri; return; }
+  if (ri < 2 * P) { n = d.nlo + 1; m = d.mlo + ri - P; return; }
+  if (ri < 2 * P + Mr) {
+    const int t = ri - 2 * P, slot = t & 3;
+    n = d.nlo + 2 + (t >> 2);
+    m = slot == 0 ? d.mlo : slot == 1 ? d.mlo + 1 : slot == 2 ? d.mhi - 1 : d.mhi;
+    return;
+  }
+  if (ri < 3 * P + Mr) { n = d.nhi - 1; m = d.mlo + ri - 2 * P - Mr; return; }
+  n = d.nhi; m = d.mlo + ri - 3 * P - Mr;
+}
+
+// side (1..4) of basis column c
+__device__ __forceinline__ int col_side(const SubDesc &d, int c) { return (c % (4 * d.n_modes)) / d.n_modes + 1; }
+
+// ---------------------------------------------------------------- k_extend
+// One thread per gamma node: the Chebyshev recurrences for T_j, T_j'', T_j'''' (with T', T'''
+// as intermediates) run once over j and serve every column of the owner side in the item.
+// Writes xi[g][c - col0] (real) for those columns; with grad also d xi / dk after G*ncols.
+__global__ void __launch_bounds__(128) k_extend(Batch bt, const SubDesc *subs, const double *tab, double *ws, int grad) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int g = local * 128 + threadIdx.x;
+  if (g >= d.G) return;
+  const double *geo = tab + d.geo_off + 4 * g;
+  const int side = (int)geo[0];
+  const double s = geo[1], rho = geo[2], L = geo[3];
+  const int M = d.n_modes;
+  const int baseD = (side - 1) * M, baseN = 4 * M + (side - 1) * M;
+  const int c0 = it.col0, c1 = it.col0 + it.ncols;
+  // j range needed: any j with baseD + j or baseN + j inside [c0, c1)
+  int jmax = 0;
+  if (c1 > baseD) jmax = max(jmax, min(M, c1 - baseD));
+  if (c1 > baseN) jmax = max(jmax, min(M, c1 - baseN));
+  double *xi = ws + it.xi_off;
+  const double k = d.k, k2 = k * k, k4 = k2 * k2;
+  const double sc2 = (2.0 / L) * (2.0 / L), sc4 = sc2 * sc2;
+  const double a2 = 0.5 * rho * rho, a4 = a2 * a2 / 6.0, a3 = a2 * rho / 3.0;
+  double t0 = 1.0, t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0;
+  double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0, p4 = 0.0;
+  const double s2 = 2.0 * s;
+  for (int j = 0; j < jmax; ++j) {
+    const double psi = t0, psi2 = t2 * sc2, psi4 = t4 * sc4;
+    const double tt = fma(-k2, psi, -psi2);                // -psi'' - k^2 psi
+    const int cD = baseD + j, cN = baseN + j;
+    if (cD >= c0 && cD < c1) {
+      const double v4 = fma(k4, psi, fma(2.0 * k2, psi2, psi4));
+      xi[(long long)g * it.ncols + (cD - c0)] = fma(a4, v4, fma(a2, tt, psi));
+      if (grad) xi[(long long)d.G * it.ncols + (long long)g * it.ncols + (cD - c0)] =
+          fma(a2, -2.0 * k * psi, a4 * (4.0 * k * psi2 + 4.0 * k * k2 * psi));
+    }
+    if (cN >= c0 && cN < c1) {
+      xi[(long long)g * it.ncols + (cN - c0)] = fma(a3, tt, rho * psi);
+      if (grad) xi[(long long)d.G * it.ncols + (long long)g * it.ncols + (cN - c0)] = a3 * (-2.0 * k * psi);
+    }
+    double n0, n1, n2, n3, n4;
+    if (j == 0) { n0 = s; n1 = 1.0; n2 = 0.0; n3 = 0.0; n4 = 0.0; }
+    else {
+      n0 = fma(s2, t0, -p0);
+      n1 = fma(s2, t1, fma(2.0, t0, -p1));
+      n2 = fma(s2, t2, fma(4.0, t1, -p2));
+      n3 = fma(s2, t3, fma(6.0, t2, -p3));
+      n4 = fma(s2, t4, fma(8.0, t3, -p4));
+    }
+    p0 = t0; p1 = t1; p2 = t2; p3 = t3; p4 = t4;
+    t0 = n0; t1 = n1; t2 = n2; t3 = n3; t4 = n4;
+  }
+}
+
+// density value xi(c, g) for the item's column b (basis: owner check; user: complex array)
+template <bool CIN>
+__device__ __forceinline__ cplx density(const SubDesc &d, const Item &it, const double *ws, const double *tab,
+                                        const double2 *xi_user, int b, int g) {
+  if (!CIN) {
+    const int own = (int)tab[d.geo_off + 4 * g];
+    if (own != col_side(d, it.col0 + b)) return cmk(0.0, 0.0);
+    return cmk(ws[it.xi_off + (long long)g * it.ncols + b], 0.0);
+  }
+  const double2 v = xi_user[it.io_off + (long long)b * d.G + g];
+  return cmk(v.x, v.y);
+}
+
+// ---------------------------------------------------------------- k_residual
+// r(ring node, column) = sum over the 3x3 stencil of the gamma neighbours: w = xi on gamma,
+// 0 elsewhere, so only gamma nodes contribute. Output r[ri][b] (real for basis densities).
+template <bool CIN>
+__global__ void __launch_bounds__(256) k_residual(Batch bt, const SubDesc *subs, const double *tab, double *ws,
+                                                  const double2 *xi_user) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int ri = (local / cb) * 8 + threadIdx.y;
+  if (b >= it.ncols || ri >= d.R) return;
+  int n, m;
+  ring_node(d, ri, n, m);
+  cplx acc = cmk(0.0, 0.0);
+#pragma unroll
+  for (int dn = -1; dn <= 1; ++dn) {
+#pragma unroll
+    for (int dm = -1; dm <= 1; ++dm) {
+      const int g = gamma_index(d, n + dn, m + dm);
+      if (g < 0) continue;
+      const int nb = (dn != 0) + (dm != 0);
+      const double c = nb == 0 ? d.c0 : nb == 1 ? d.c1 : d.c2;
+      acc = caxpy(c, density<CIN>(d, it, ws, tab, xi_user, b, g), acc);
+    }
+  }
+  double *r = ws + it.r_off;
+  if (CIN) st2(r + 2 * ((long long)ri * it.ncols + b), acc);
+  else r[(long long)ri * it.ncols + b] = acc.re;
+}
+
+// ---------------------------------------------------------------- k_fwd_rows
+// ghat(q, row) = sum_m sin(pi q m / Nx) r(m, row) for the 4 dense ring rows. A thread handles
+// the mode pair (q, Nx - q): sin(pi (Nx-q) m/Nx) = (-1)^(m+1) sin(pi q m/Nx), so the odd-m and
+// even-m partial sums give both modes.
+template <bool CIN>
+__global__ void __launch_bounds__(128) k_fwd_rows(Batch bt, const SubDesc *subs, const double *tab, double *ws) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int q = (local / cb) * 4 + threadIdx.y + 1;
+  if (b >= it.ncols || q > d.Nx / 2) return;
+  const double *S = tab + d.sin_off;
+  const int N2 = 2 * d.Nx, P = d.Px, Mr = 4 * (d.Py - 4);
+  const double *r = ws + it.r_off;
+  double *gr = ws + it.gr_off;
+  const int q2 = d.Nx - q;
+  for (int rr = 0; rr < 4; ++rr) {
+    const int rb = rr == 0 ? 0 : rr == 1 ? P : rr == 2 ? 2 * P + Mr : 3 * P + Mr;
+    cplx ao = cmk(0.0, 0.0), ae = cmk(0.0, 0.0);
+    int j = (int)(((long long)q * d.mlo) % N2);
+    for (int mm = 0; mm < P; ++mm) {
+      const int m = d.mlo + mm;
+      const double sv = S[j];
+      cplx v;
+      if (CIN) v = ld2(r + 2 * ((long long)(rb + mm) * it.ncols + b));
+      else v = cmk(r[(long long)(rb + mm) * it.ncols + b], 0.0);
+      if (m & 1) ao = caxpy(sv, v, ao); else ae = caxpy(sv, v, ae);
+      j += q;
+      if (j >= N2) j -= N2;
+    }
+    const long long o1 = ((long long)rr * d.Nq + (q - 1)) * it.ncols + b;
+    const long long o2 = ((long long)rr * d.Nq + (q2 - 1)) * it.ncols + b;
+    if (CIN) {
+      st2(gr + 2 * o1, cadd(ao, ae));
+      if (q2 != q) st2(gr + 2 * o2, csub(ao, ae));
+    } else {
+      gr[o1] = ao.re + ae.re;
+      if (q2 != q) gr[o2] = ao.re - ae.re;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- k_tri
+// Per (mode q, column b): forward elimination with the stored row swaps from matrix row i0
+// (rows below carry zero right-hand side) to the top, then back substitution down to i0.
+// RHS at grid row n: the dense ring rows read ghat; the middle ring rows have 4 nonzeros
+// (columns mlo, mlo+1, mhi-1, mhi), so their sine transform is 4 products here.
+// CF: complex factors. CIN: complex ring data. Output y[q-1][n - (nlo-1)][b] for the rows
+// nlo-1 .. nhi+1, complex unless neither CF nor CIN (real path).
+template <bool CF, bool CIN>
+__device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const double *tab, const uint8_t *pivtab,
+                                         double *ws, int b, int q) {
+  constexpr bool CD = CF || CIN;  // complex data in the sweep
+  const int N2 = 2 * d.Nx;
+  const double *S = tab + d.sin_off;
+  const double sm0 = S[(q * d.mlo) % N2], sm1 = S[(q * (d.mlo + 1)) % N2];
+  const double sm2 = S[(q * (d.mhi - 1)) % N2], sm3 = S[(q * d.mhi) % N2];
+  constexpr int FW = CF ? 8 : 4;
+  const double *F = tab + d.fact_off + (long long)(q - 1) * d.Nt * FW;
+  const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * d.Nt;
+  const double *r = ws + it.r_off;
+  const double *gr = ws + it.gr_off;
+  double *y = ws + it.y_off;
+  const long long ystride = it.ncols;                         // between stored rows
+  const long long ybase = (long long)(q - 1) * d.NYf * it.ncols + b;
+  const int P = d.Px, nc = it.ncols;
+  auto rhs = [&](int n) -> cplx {
+    if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
+    int rr = -1;
+    if (n == d.nlo) rr = 0; else if (n == d.nlo + 1) rr = 1; else if (n == d.nhi - 1) rr = 2; else if (n == d.nhi) rr = 3;
+    if (rr >= 0) {
+      const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b;
+      return CIN ? ld2(gr + 2 * o) : cmk(gr[o], 0.0);
+    }
+    const long long ri = 2 * P + 4 * (n - d.nlo - 2);
+    if (CIN) {
+      cplx v = cmk(0.0, 0.0);
+      v = caxpy(sm0, ld2(r + 2 * ((ri + 0) * nc + b)), v);
+      v = caxpy(sm1, ld2(r + 2 * ((ri + 1) * nc + b)), v);
+      v = caxpy(sm2, ld2(r + 2 * ((ri + 2) * nc + b)), v);
+      v = caxpy(sm3, ld2(r + 2 * ((ri + 3) * nc + b)), v);
+      return v;
+    }
+    double v = sm0 * r[(ri + 0) * nc + b];
+    v = fma(sm1, r[(ri + 1) * nc + b], v);
+    v = fma(sm2, r[(ri + 2) * nc + b], v);
+    v = fma(sm3, r[(ri + 3) * nc + b], v);
+    return cmk(v, 0.0);
+  };
+  auto ystore = [&](int i, cplx v) {
+    const long long o = ybase + (long long)(i - d.i0) * ystride;
+    if (CD) st2(y + 2 * o, v); else y[o] = v.re;
+  };
+  auto yload = [&](int i) -> cplx {
+    const long long o = ybase + (long long)(i - d.i0) * ystride;
+    return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
+  };
+  // forward sweep: cur holds the eliminated value of row i
+  cplx cur = cmk(0.0, 0.0);
+  for (int i = d.i0; i < d.Nt - 1; ++i) {
+    const cplx g = rhs(i + 1 + d.nfirst);
+    const cplx l = CF ? ld2(F + i * FW) : cmk(F[i * FW], 0.0);
+    cplx yv;
+    if (pv[i]) {
+      yv = g;
+      if constexpr (CF) cur = cfms(cur, l, g);
+      else { cur.re = fma(-l.re, g.re, cur.re); if constexpr (CD) cur.im = fma(-l.re, g.im, cur.im); }
+    } else {
+      yv = cur;
+      if constexpr (CF) cur = cfms(g, l, cur);
+      else { cur.re = fma(-l.re, cur.re, g.re); cur.im = CD ? fma(-l.re, cur.im, g.im) : 0.0; }
+    }
+    ystore(i, yv);
+  }
+  ystore(d.Nt - 1, cur);
+  // back substitution; keep only rows nlo-1 .. nhi+1
+  const int ikeep = d.nhi + 1 - d.nfirst;
+  cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
+  for (int i = d.Nt - 1; i >= d.i0; --i) {
+    const cplx yi = yload(i);
+    cplx x;
+    if (CF) {
+      const cplx dinv = ld2(F + i * FW + 2), u1 = ld2(F + i * FW + 4);
+      x = cfms(cmul(dinv, yi), u1, x1);
+      if (pv[i]) x = cfms(x, ld2(F + i * FW + 6), x2);
+    } else {
+      const double dinv = F[i * FW + 1], u1 = F[i * FW + 2];
+      x = cmk(fma(-u1, x1.re, dinv * yi.re), CD ? fma(-u1, x1.im, dinv * yi.im) : 0.0);
+      if (pv[i]) {
+        const double u2 = F[i * FW + 3];
+        x.re = fma(-u2, x2.re, x.re);
+        if (CD) x.im = fma(-u2, x2.im, x.im);
+      }
+    }
+    if (i <= ikeep) ystore(i, x);
+    x2 = x1; x1 = x;
+  }
+}
+
+template <bool CIN>
+__global__ void __launch_bounds__(128) k_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
+                                             double *ws) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int q = (local / cb) * 4 + threadIdx.y + 1;
+  if (b >= it.ncols || q > d.Nq) return;
+  if (d.cplx) tri_body<true, CIN>(it, d, tab, pivtab, ws, b, q);
+  else tri_body<false, CIN>(it, d, tab, pivtab, ws, b, q);
+}
+
+// ---------------------------------------------------------------- inverse transforms on gamma
+template <bool CD, bool CIN>
+__device__ __forceinline__ void write_out(const SubDesc &d, const Item &it, const double *ws, const double *tab,
+                                          const double2 *xi_user, double2 *out, int kind, int b, int g, cplx u) {
+  cplx v = cmk(-u.re, -u.im);
+  if (kind == MDP_OUT_P) v = cadd(v, density<CIN>(d, it, ws, tab, xi_user, b, g));
+  out[it.io_off + (long long)b * d.G + g] = make_double2(v.re, v.im);
+}
+
+// u(m, n) = (2/Nx) sum_q sin(pi q m/Nx) yhat(q, n) for the 4 full gamma rows
+template <bool CD, bool CIN>
+__device__ __forceinline__ void inv_rows_body(const Item &it, const SubDesc &d, const double *tab, const double *ws,
+                                              const double2 *xi_user, double2 *out, int kind, int b, int task) {
+  const int W = d.Px + 2;
+  const int grow = task / W, dm = task % W, m = d.mlo - 1 + dm;
+  const int n = grow == 0 ? d.nlo - 1 : grow == 1 ? d.nlo : grow == 2 ? d.nhi : d.nhi + 1;
+  const int yrow = n - (d.nlo - 1);
+  const double *Si = tab + d.sin_off + 2 * d.Nx;
+  const int N2 = 2 * d.Nx;
+  const double *y = ws + it.y_off;
+  const long long qstride = (long long)d.NYf * it.ncols;
+  const long long base = (long long)yrow * it.ncols + b;
+  cplx acc = cmk(0.0, 0.0);
+  int j = m % N2;
+  for (int q = 1; q <= d.Nq; ++q) {
+    const long long o = base + (long long)(q - 1) * qstride;
+    const double sv = Si[j];
+    if (CD) acc = caxpy(sv, ld2(y + 2 * o), acc); else acc.re = fma(sv, y[o], acc.re);
+    j += m;
+    if (j >= N2) j -= N2;
+  }
+  const int Mr = d.Py - 2;
+  const int g = grow <= 1 ? grow * W + dm : 2 * W + 4 * Mr + (grow - 2) * W + dm;
+  write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, g, acc);
+}
+
+template <bool CIN>
+__global__ void __launch_bounds__(256) k_inv_rows(Batch bt, const SubDesc *subs, const double *tab, const double *ws,
+                                                  const double2 *xi_user, double2 *out, int kind) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int task = (local / cb) * 8 + threadIdx.y;
+  if (b >= it.ncols || task >= 4 * (d.Px + 2)) return;
+  if (d.cplx || CIN) inv_rows_body<true, CIN>(it, d, tab, ws, xi_user, out, kind, b, task);
+  else inv_rows_body<false, CIN>(it, d, tab, ws, xi_user, out, kind, b, task);
+}
+
+// the 4 gamma columns (mlo-1, mlo, mhi, mhi+1) of the middle rows nlo+1 .. nhi-1
+template <bool CD, bool CIN>
+__device__ __forceinline__ void inv_cols_body(const Item &it, const SubDesc &d, const double *tab, const double *ws,
+                                              const double2 *xi_user, double2 *out, int kind, int b, int t) {
+  const int yrow = t + 2;  // n = nlo + 1 + t
+  const double *Si = tab + d.sin_off + 2 * d.Nx;
+  const int N2 = 2 * d.Nx;
+  const int ms[4] = {d.mlo - 1, d.mlo, d.mhi, d.mhi + 1};
+  int j[4] = {ms[0] % N2, ms[1] % N2, ms[2] % N2, ms[3] % N2};
+  const double *y = ws + it.y_off;
+  const long long qstride = (long long)d.NYf * it.ncols;
+  const long long base = (long long)yrow * it.ncols + b;
+  cplx acc[4] = {cmk(0, 0), cmk(0, 0), cmk(0, 0), cmk(0, 0)};
+  for (int q = 1; q <= d.Nq; ++q) {
+    const long long o = base + (long long)(q - 1) * qstride;
+    const cplx v = CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const double sv = Si[j[s]];
+      if (CD) acc[s] = caxpy(sv, v, acc[s]); else acc[s].re = fma(sv, v.re, acc[s].re);
+      j[s] += ms[s];
+      if (j[s] >= N2) j[s] -= N2;
+    }
+  }
+  const int W = d.Px + 2;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, 2 * W + 4 * t + s, acc[s]);
+}
+
+template <bool CIN>
+__global__ void __launch_bounds__(256) k_inv_cols(Batch bt, const SubDesc *subs, const double *tab, const double *ws,
+                                                  const double2 *xi_user, double2 *out, int kind) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int t = (local / cb) * 8 + threadIdx.y;
+  if (b >= it.ncols || t >= d.Py - 2) return;
+  if (d.cplx || CIN) inv_cols_body<true, CIN>(it, d, tab, ws, xi_user, out, kind, b, t);
+  else inv_cols_body<false, CIN>(it, d, tab, ws, xi_user, out, kind, b, t);
+}
+
+// ---------------------------------------------------------------- full-grid solves
+// u = G^(h) g or A^{-H} g on the whole grid (test and reconstruction primitive). Mode-space
+// buffer buf[r][q-1][i] (complex), i = matrix row of the y unknowns.
+
+// Solve T_q z = b (adjoint = 0) or T_q^H z = b (adjoint = 1) in place on a contiguous vector.
+template <bool CF>
+__device__ void mode_solve_inplace(const double *F, const uint8_t *pv, int N, double *z, int adjoint) {
+  constexpr int FW = CF ? 8 : 4;
+  auto fl = [&](int i, int w) -> cplx { return CF ? ld2(F + i * FW + 2 * w) : cmk(F[i * FW + w], 0.0); };
+  auto cj = [](cplx a) { return cmk(a.re, -a.im); };
+  if (!adjoint) {
+    cplx cur = ld2(z);
+    for (int i = 0; i < N - 1; ++i) {
+      const cplx g = ld2(z + 2 * (i + 1));
+      const cplx l = fl(i, 0);
+      cplx yv;
+      if (pv[i]) { yv = g; cur = cfms(cur, l, g); } else { yv = cur; cur = cfms(g, l, cur); }
+      st2(z + 2 * i, yv);
+    }
+    st2(z + 2 * (N - 1), cur);
+    cplx x1 = cmk(0, 0), x2 = cmk(0, 0);
+    for (int i = N - 1; i >= 0; --i) {
+      cplx x = cfms(cmul(fl(i, 1), ld2(z + 2 * i)), fl(i, 2), x1);
+      if (pv[i]) x = cfms(x, fl(i, 3), x2);
+      st2(z + 2 * i, x);
+      x2 = x1; x1 = x;
+    }
+  } else {
+    // U^H zt = b with zt_i = conj(d_i) z_i, then z = P_0 E_0^H ... P_{N-2} E_{N-2}^H z
+    cplx t1 = cmk(0, 0), t2 = cmk(0, 0);
+    for (int i = 0; i < N; ++i) {
+      cplx v = ld2(z + 2 * i);
+      if (i >= 1) v = cfms(v, cj(fl(i - 1, 2)), t1);
+      if (i >= 2 && pv[i - 2]) v = cfms(v, cj(fl(i - 2, 3)), t2);
+      st2(z + 2 * i, cmul(cj(fl(i, 1)), v));
+      t2 = t1; t1 = v;
+    }
+    // `up` is the current value at position i+1; after step i position i+1 is final
+    cplx up = ld2(z + 2 * (N - 1));
+    for (int i = N - 2; i >= 0; --i) {
+      const cplx zi = cfms(ld2(z + 2 * i), cj(fl(i, 0)), up);
+      if (pv[i]) st2(z + 2 * (i + 1), zi);          // swap: i+1 takes the update, i keeps `up`
+      else { st2(z + 2 * (i + 1), up); up = zi; }
+    }
+    st2(z, up);
+  }
+}
+
+__global__ void k_full_fwd(const SubDesc *subs, int sub, const double *tab, const double2 *g, double *buf,
+                           int r0, int nr, int adjoint) {
+  const SubDesc &d = subs[sub];
+  const int q = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int i = blockIdx.y;
+  const int rl = blockIdx.z;
+  if (q > d.Nq || rl >= nr) return;
+  const int n = i + d.nfirst;
+  cplx acc = cmk(0.0, 0.0);
+  const bool interior = n >= 1 && n <= d.ny - 2;
+  if (interior || adjoint) {
+    const double *S = tab + d.sin_off;
+    const int N2 = 2 * d.Nx;
+    const double2 *row = g + ((long long)(r0 + rl) * d.ny + n) * d.nx;
+    int j = q;
+    for (int m = 1; m <= d.Nx - 1; ++m) {
+      const double2 v = row[m];
+      acc = caxpy(S[j], cmk(v.x, v.y), acc);
+      j += q;
+      if (j >= N2) j -= N2;
+    }
+  }
+  st2(buf + 2 * (((long long)rl * d.Nq + (q - 1)) * d.Nt + i), acc);
+}
+
+__global__ void k_full_tri(const SubDesc *subs, int sub, const double *tab, const uint8_t *pivtab, double *buf,
+                           int nr, int adjoint) {
+  const SubDesc &d = subs[sub];
+  const int q = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int rl = blockIdx.y;
+  if (q > d.Nq || rl >= nr) return;
+  double *z = buf + 2 * (((long long)rl * d.Nq + (q - 1)) * d.Nt);
+  const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * d.Nt;
+  if (d.cplx) mode_solve_inplace<true>(tab + d.fact_off + (long long)(q - 1) * d.Nt * 8, pv, d.Nt, z, adjoint);
+  else mode_solve_inplace<false>(tab + d.fact_off + (long long)(q - 1) * d.Nt * 4, pv, d.Nt, z, adjoint);
+}
+
+__global__ void k_full_inv(const SubDesc *subs, int sub, const double *tab, const double *buf, double2 *u,
+                           int r0, int nr, int adjoint) {
+  const SubDesc &d = subs[sub];
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = blockIdx.y;
+  const int rl = blockIdx.z;
+  if (m >= d.nx || rl >= nr) return;
+  const int i = n - d.nfirst;
+  cplx acc = cmk(0.0, 0.0);
+  if (m >= 1 && m <= d.Nx - 1 && i >= 0 && i < d.Nt) {
+    const double *Si = tab + d.sin_off + 2 * d.Nx;
+    const int N2 = 2 * d.Nx;
+    int j = m;
+    const double *col = buf + 2 * ((long long)rl * d.Nq * d.Nt + i);
+    for (int q = 1; q <= d.Nq; ++q) {
+      acc = caxpy(Si[j], ld2(col + 2 * (long long)(q - 1) * d.Nt), acc);
+      j += m;
+      if (j >= N2) j -= N2;
+    }
+    // A^{-H} of the unscaled AP: the Sommerfeld rows of T_q carry a 1/h row scale
+    if (adjoint && d.cplx && (n == 0 || n == d.ny - 1)) { acc.re /= d.h; acc.im /= d.h; }
+  }
+  u[((long long)(r0 + rl) * d.ny + n) * d.nx + m] = make_double2(acc.re, acc.im);
+}
+
+cudaError_t launch_solve(const mdp_plan *p, int sub, int nrhs, const double2 *g, double2 *u, int adjoint,
+                         cudaStream_t st) {
+  const SubDesc &d = p->subs[sub].d;
+  const long long per = (long long)d.Nq * d.Nt * 2;
+  long long chunk = p->ws_doubles / per;
+  if (chunk < 1) return cudaErrorMemoryAllocation;
+  if (chunk > 65535) chunk = 65535;
+  for (int r0 = 0; r0 < nrhs; r0 += (int)chunk) {
+    const int nr = (int)std::min<long long>(chunk, nrhs - r0);
+    k_full_fwd<<<dim3((d.Nq + 63) / 64, d.Nt, nr), 64, 0, st>>>(p->d_subs, sub, p->d_tables, g, p->d_ws, r0, nr, adjoint);
+    k_full_tri<<<dim3((d.Nq + 63) / 64, nr), 64, 0, st>>>(p->d_subs, sub, p->d_tables, p->d_piv, p->d_ws, nr, adjoint);
+    k_full_inv<<<dim3((d.nx + 63) / 64, d.ny, nr), 64, 0, st>>>(p->d_subs, sub, p->d_tables, p->d_ws, u, r0, nr, adjoint);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- launchers
+static inline dim3 grid1(int n) { return dim3((unsigned)n, 1, 1); }
+
+cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, double2 *out,
+                           cudaStream_t st) {
+  const bool basis = xi_user == nullptr;
+  const SubDesc *ds = p->d_subs;
+  const double *tab = p->d_tables;
+  double *ws = p->d_ws;
+  const dim3 b8(32, 8), b4(32, 4);
+#define MDP_LAUNCH(fam, ...)                      \
+  do {                                            \
+    if (fb[fam].total_blocks > 0) {               \
+      prof_begin(p, fam, st);                     \
+      __VA_ARGS__;                                \
+      prof_end(p, fam, st);                       \
+    }                                             \
+  } while (0)
+  if (basis) MDP_LAUNCH(F_EXT, k_extend<<<grid1(fb[F_EXT].total_blocks), 128, 0, st>>>(fb[F_EXT], ds, tab, ws, 0));
+  if (basis) MDP_LAUNCH(F_RES, k_residual<false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
+  else MDP_LAUNCH(F_RES, k_residual<true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
+  if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
+  else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
+  if (basis) MDP_LAUNCH(F_TRI, k_tri<false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  else MDP_LAUNCH(F_TRI, k_tri<true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  if (basis) {
+    MDP_LAUNCH(F_IROWS, k_inv_rows<false><<<grid1(fb[F_IROWS].total_blocks), b8, 0, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
+    MDP_LAUNCH(F_ICOLS, k_inv_cols<false><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
+  } else {
+    MDP_LAUNCH(F_IROWS, k_inv_rows<true><<<grid1(fb[F_IROWS].total_blocks), b8, 0, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
+    MDP_LAUNCH(F_ICOLS, k_inv_cols<true><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mdp

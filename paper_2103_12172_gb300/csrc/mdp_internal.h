@@ -1,0 +1,137 @@
+// Internal structures shared by the host plan and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <vector>
+#include <string>
+#include <cuda_runtime.h>
+#include "mdp.h"
+
+namespace mdp {
+
+// Per-subdomain geometry, coefficients and table offsets (POD; copied to the device).
+//
+// Grid: nodes (m, n), x_m = ax0 + m h, y_n = ay0 + n h. M+ is the node rectangle
+// [mlo, mhi] x [nlo, nhi]. gamma is the 2-node ring [mlo-1, mhi+1] x [nlo-1, nhi+1]
+// minus [mlo+1, mhi-1] x [nlo+1, nhi-1]; the support of r = L w|M+ ("ring") is
+// [mlo, mhi] x [nlo, nhi] minus [mlo+2, mhi-2] x [nlo+2, nhi-2].
+// Sine modes q = 1..Nq along x (Nq = Nx - 1, Nx = nx - 1 cells). The tridiagonal
+// unknowns along y are rows n = nfirst .. nfirst + Nt - 1 (matrix row i = n - nfirst).
+struct SubDesc {
+  int nx, ny, Nx, Nq;
+  int mlo, mhi, nlo, nhi;
+  int Px, Py;       // M+ nodes along x and y
+  int G, R;         // |gamma| = 4(Px + Py), |ring| = 4 Px + 4 (Py - 4)
+  int nfirst, Nt;   // first y row of the tridiagonal unknowns, and their count
+  int i0;           // first stored matrix row of the partial sweeps: (nlo - 1) - nfirst
+  int NYf;          // stored rows of the forward (projection) sweep: Nt - i0
+  int n_modes, n_cols;
+  int cplx;         // 1: complex factors (Sommerfeld AP), 0: real (Dirichlet AP)
+  int ap_bc;
+  double h, k;
+  double x0, x1, y0, y1, ax0, ay0;
+  double c0, c1, c2;  // 9-point coefficients: centre, edge, corner (Eq. FD_scheme)
+  double dc0, dc1;    // their k-derivatives (the corner one is 0)
+  long long fact_off;   // doubles: factor rows [Nq][Nt][FW], FW = 8 (complex) or 4 (real)
+  long long piv_off;    // bytes: pivot flags [Nq][Nt]
+  long long dT_off;     // doubles: dT_q/dk rows [Nq][Nt][6] (sub, diag, super; complex)
+  long long sin_off;    // doubles: sin(pi j / Nx), j = 0 .. 2Nx-1, then (2/Nx) sin(pi j/Nx)
+  long long geo_off;    // doubles: gamma geometry [G][4] = (owner, s, rho, side length)
+  long long out_off;    // complex elements: start of the subdomain's output block
+};
+
+// One batch work item: columns [col0, col0 + ncols) of subdomain `sub`, with its
+// workspace slices (offsets in doubles from the workspace base).
+struct Item {
+  int sub, col0, ncols, flags;   // flags: bit0 basis densities, bit1 real data path
+  long long xi_off;   // basis densities [G][ncols] (real) / dxi/dk follows for the gradient
+  long long r_off;    // ring residual [R][ncols] (real or complex)
+  long long gr_off;   // forward sine transform of the 4 dense ring rows [4][Nq][ncols]
+  long long y_off;    // mode-space field [Nq][NY][ncols]
+  long long a_off;    // adjoint mode-space field [Nq][Nt][ncols] (gradient pass)
+  long long s_off;    // gradient source on the ring [R][ncols] (complex)
+  long long red_off;  // per-block partial sums of the k-gradient
+  long long io_off;   // complex elements: column col0 of this item in xi / out / cot / grad_xi
+};
+
+enum { ITEM_BASIS = 1, ITEM_REAL = 2 };
+
+// Launch-time view of a list of items: a device array plus, for each kernel family,
+// per-item prefix sums of blocks. A single item may be passed by value instead.
+struct Batch {
+  const Item *items;    // device array (nullptr: use `one`)
+  const int *prefix;    // device array [n_items + 1] of block prefix sums for this kernel
+  int n_items;
+  int total_blocks;
+  Item one;
+};
+
+struct HostSub {
+  SubDesc d;
+  std::vector<int> gamma_nm;     // 2*G: (n, m) pairs, row-major order
+  std::vector<int> owner;        // G
+  std::vector<double> rho, s, L; // G
+  // tridiagonal factors (host copy, for introspection)
+  std::vector<double> fact;      // [Nq][Nt][FW]
+  std::vector<uint8_t> piv;      // [Nq][Nt]
+  std::vector<double> dT;        // [Nq][Nt][6]
+};
+
+struct Wave {
+  std::vector<Item> items;
+  long long ws_doubles;
+};
+
+}  // namespace mdp
+
+struct mdp_plan {
+  unsigned flags = 0;
+  int n_subs = 0;
+  int device = -1;
+  std::vector<mdp::HostSub> subs;
+  std::vector<double> host_tables;       // all factor / dT / sine / geometry tables
+  std::vector<uint8_t> host_piv;
+  long long out_size = 0;
+  int tile_cols = 256;                   // columns per work item
+  long long ws_budget = 0;               // bytes of workspace
+  std::vector<mdp::Wave> waves;          // batch schedule of mdp_project_batch
+  // device side
+  mdp::SubDesc *d_subs = nullptr;
+  double *d_tables = nullptr;
+  uint8_t *d_piv = nullptr;
+  double *d_ws = nullptr;
+  long long ws_doubles = 0;
+  int *d_status = nullptr;
+  // per wave: device items and prefix arrays (one prefix array per kernel family)
+  std::vector<mdp::Item *> d_wave_items;
+  std::vector<int *> d_wave_prefix;      // [wave] -> device int [NFAM][n_items + 1]
+  std::vector<std::vector<int>> h_wave_prefix;
+  // per-kernel event timing (mdp_plan_profile)
+  bool prof_on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[16];
+  int prof_used[16] = {0};
+};
+
+namespace mdp {
+// kernel families (each has its own block decomposition of an item)
+enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_AGAM,
+           F_FULLF, F_FULLT, F_FULLI, NFAM };
+int blocks_for(Fam f, const SubDesc &d, int ncols);
+const char *fam_name(int f);
+// event pair around a launch when profiling is on
+void prof_begin(mdp_plan *p, int fam, cudaStream_t st);
+void prof_end(mdp_plan *p, int fam, cudaStream_t st);
+// plan construction (host)
+mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n);
+mdp_status refactor_host(mdp_plan *p, const double *k);
+void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long long &r, long long &gr,
+                    long long &y, long long &a, long long &s, long long &red, long long &total);
+void host_mode_solve(const HostSub &hs, int q, int adjoint, const double *b, double *x);
+// kernel launchers (kernels.cu)
+enum { PASS_FWD = 0, PASS_GRAD = 1 };
+cudaError_t launch_project(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,
+                           double2 *out, cudaStream_t st);
+cudaError_t launch_adjoint(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,
+                           const double2 *cot, double2 *grad_xi, double *grad_k, cudaStream_t st);
+cudaError_t launch_solve(const mdp_plan *p, int sub, int nrhs, const double2 *g, double2 *u, int adjoint,
+                         cudaStream_t st);
+}  // namespace mdp

@@ -9,3 +9,15 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built library")
     config.addinivalue_line("markers", "slow: oracle cases that take more than a few seconds")
+
+
+import pytest  # noqa: E402
+
+
+@pytest.fixture(scope="session")
+def mdp():
+    """The package with libmdp.so built in-tree (nvcc cross-compiles without a GPU)."""
+    from paper_2103_12172_gb300 import _build
+    _build.build()
+    import paper_2103_12172_gb300 as pkg
+    return pkg

@@ -1,0 +1,146 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element by element.
+
+Bar (relative L-infinity per column, max over columns): 1e-10 for fields and projection
+columns. Inputs are seeded and synthetic (workloads.py)."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.projection import APSystem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def rel_col_err(gpu, ref):
+    """max over columns of max|gpu - ref| / max|ref| (rows = columns)."""
+    gpu = np.asarray(gpu).reshape(ref.shape)
+    num = np.abs(gpu - ref).max(axis=1)
+    den = np.abs(ref).max(axis=1)
+    return float((num / den).max())
+
+
+@pytest.fixture(scope="module")
+def dev(mdp):
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return mdp
+
+
+def make_plan(mdp, subs, tile=None):
+    old = os.environ.get("MDP_TILE_COLS")
+    if tile is not None:
+        os.environ["MDP_TILE_COLS"] = str(tile)
+    try:
+        return mdp.Plan(subs)
+    finally:
+        if tile is not None:
+            if old is None:
+                del os.environ["MDP_TILE_COLS"]
+            else:
+                os.environ["MDP_TILE_COLS"] = old
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("n,k", [(33, 6.0), (129, 10.0)])
+def test_full_grid_solve_and_adjoint(dev, ap, n, k):
+    sub = W.small_subdomain(n, k, ap, 4)
+    plan = dev.Plan([sub])
+    S = APSystem(sub)
+    g = W.random_complex((3, n, n), seed=0)
+    u = plan.solve(0, torch.from_numpy(g).cuda()).cpu().numpy()
+    ref = np.stack([S.solve(x) for x in g])
+    assert rel_col_err(u.reshape(3, -1), ref.reshape(3, -1)) < TOL
+    # adjoint: input on the unknown nodes
+    y = g.copy()
+    y[:, :, 0] = y[:, :, -1] = 0
+    if ap == W.AP_DIRICHLET4:
+        y[:, 0, :] = y[:, -1, :] = 0
+    ua = plan.solve(0, torch.from_numpy(y).cuda(), adjoint=True).cpu().numpy()
+    refa = np.stack([S.solve_adjoint(x) for x in y])
+    assert rel_col_err(ua.reshape(3, -1), refa.reshape(3, -1)) < TOL
+
+
+PROJ_CASES = [
+    ("single_129_dir4", W.single_129().subdomains[0], None),
+    ("n65_somm_m5_ragged", W.small_subdomain(65, 12.0, W.AP_DIRX_SOMMY, 5), 16),
+    ("n33_dir4_m3", W.small_subdomain(33, 6.0, W.AP_DIRICHLET4, 3), 7),
+    ("n17_somm_m1", W.small_subdomain(17, 3.0, W.AP_DIRX_SOMMY, 1), None),
+    ("strip_129_k40", W.strip4x1().subdomains[2], 96),
+]
+
+
+@pytest.mark.parametrize("name,sub,tile", PROJ_CASES, ids=[c[0] for c in PROJ_CASES])
+@pytest.mark.parametrize("kind", ["Q", "P"])
+def test_basis_columns_match_oracle(dev, name, sub, tile, kind):
+    plan = make_plan(dev, [sub], tile)
+    out = plan.project(kind=kind)
+    torch.cuda.synchronize()
+    plan.status()
+    G, nc, _, _ = plan.layout(0)
+    got = out.cpu().numpy().reshape(nc, G)
+    ref = APSystem(sub).columns(kind=kind)
+    assert rel_col_err(got, ref) < TOL
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("kind", ["Q", "P"])
+def test_user_densities_match_oracle(dev, ap, kind):
+    sub = W.small_subdomain(65, 9.0, ap, 2)
+    plan = make_plan(dev, [sub], 8)
+    G, nc, _, _ = plan.layout(0)
+    xi = W.random_complex((nc, G), seed=11)
+    out = plan.project(xi=torch.from_numpy(xi.ravel()).cuda(), kind=kind).cpu().numpy().reshape(nc, G)
+    ref = APSystem(sub).columns(xi=xi, kind=kind)
+    assert rel_col_err(out, ref) < TOL
+
+
+def test_unbatched_path_equals_batched(dev):
+    """The per-column path runs the same kernels one column at a time: identical results."""
+    sub = W.small_subdomain(129, 10.0, W.AP_DIRX_SOMMY, 4)
+    plan = make_plan(dev, [sub], 32)
+    full = plan.project().cpu().numpy()
+    G = plan.layout(0)[0]
+    for c in (0, 5, 17, 31):
+        one = plan.project_columns(0, c, 1).cpu().numpy()
+        assert np.array_equal(one, full[c * G:(c + 1) * G])
+
+
+def test_asymmetric_placement(dev):
+    sub = W.Subdomain(0.0, 1.0, 0.0, 1.0, -0.1, -0.17, 1.27 / 64, 65, 65, 7.0, W.AP_DIRX_SOMMY, 3)
+    plan = dev.Plan([sub])
+    G, nc, _, _ = plan.layout(0)
+    got = plan.project().cpu().numpy().reshape(nc, G)
+    assert rel_col_err(got, APSystem(sub).columns()) < TOL
+
+
+def test_dd2x2_257_workload(dev):
+    """The 2x2 decomposition at 257^2 (k = 30, mixed AP, 1024 columns in one launch):
+    every column of subdomain 0 and 32 sampled columns of each other subdomain."""
+    wl = W.dd2x2_257()
+    plan = dev.Plan(list(wl.subdomains))
+    out = plan.project()
+    blocks = [b.cpu().numpy() for b in plan.blocks(out)]
+    rng = np.random.default_rng(0)
+    for i, sub in enumerate(wl.subdomains):
+        S = APSystem(sub)
+        cols = list(range(256)) if i == 0 else sorted(rng.choice(256, 32, replace=False).tolist())
+        ref = S.columns(cols=cols)
+        assert rel_col_err(blocks[i][cols], ref) < TOL, i
+
+
+def test_checkerboard_workload_sampled(dev):
+    """2x2 checkerboard with 129^2 (k = 10) and 513^2 (k = 100) subdomains in one batch."""
+    wl = W.checker2x2()
+    plan = dev.Plan(list(wl.subdomains))
+    out = plan.project()
+    blocks = plan.blocks(out)
+    rng = np.random.default_rng(1)
+    for i, sub in enumerate(wl.subdomains[:2]):
+        cols = sorted(rng.choice(8 * sub.n_modes, 12, replace=False).tolist())
+        ref = APSystem(sub).columns(cols=cols)
+        assert rel_col_err(blocks[i].cpu().numpy()[cols], ref) < TOL, i

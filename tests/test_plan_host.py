@@ -1,0 +1,142 @@
+"""CPU tests of the C ABI through host-only plans: exported symbols, grid sets and gamma
+geometry (bit-exact against the oracle), per-mode tridiagonal factors against the oracle's
+2-D sparse solve, argument validation and resonance detection. No device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.grid import grid_sets
+from oracle.projection import APSystem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"\b(mdp_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(mdp):
+    from paper_2103_12172_gb300 import _lib
+    L = ctypes.CDLL(_lib.LIB_PATH)
+    names = declared_functions()
+    assert "mdp_project_batch" in names and "mdp_ap_adjoint" in names and "mdp_ap_plan" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(_lib.EXPORTED) | {n for n in names if hasattr(L, n)}
+
+
+def asym_subdomain():
+    """Subdomain placed off-centre in its auxiliary rectangle (margins 0.1 and 0.17)."""
+    s = W.unit_subdomain(0, 0, 65, 7.0, W.AP_DIRX_SOMMY, 4)
+    h = 1.27 / 64
+    return W.Subdomain(0.0, 1.0, 0.0, 1.0, -0.1, -0.17, h, 65, 65, 7.0, W.AP_DIRX_SOMMY, 4)
+
+
+CASES = [W.small_subdomain(n, 10.0, ap, 4) for n in (17, 33, 129, 257) for ap in (0, 1)]
+CASES += [asym_subdomain(), W.unit_subdomain(1, 1, 129, 10.0, 1, 4)]
+
+
+@pytest.mark.parametrize("sub", CASES, ids=lambda s: f"n{s.nx}_ap{s.ap_bc}_x{s.ax0:.2f}_y{s.ay0:.2f}")
+def test_gamma_and_ownership_match_oracle(mdp, sub):
+    plan = mdp.Plan([sub], host_only=True)
+    G, ncols, off, nm = plan.layout(0)
+    gs = grid_sets(sub)
+    assert G == gs.gamma_n.size and ncols == 8 * sub.n_modes and off == 0
+    np.testing.assert_array_equal(nm[:, 0], gs.gamma_n)
+    np.testing.assert_array_equal(nm[:, 1], gs.gamma_m)
+    owner, rho, s = plan.gamma_geometry(0)
+    np.testing.assert_array_equal(owner, gs.owner)
+    np.testing.assert_allclose(rho, gs.rho, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(s, gs.s, rtol=0, atol=1e-14)
+    assert plan.output_size == G * ncols
+
+
+def test_output_layout_of_several_subdomains(mdp):
+    subs = list(W.dd2x2_257().subdomains)
+    plan = mdp.Plan(subs, host_only=True)
+    off = 0
+    for i in range(4):
+        G, nc, o, _ = plan.layout(i)
+        assert o == off and G == 1704 and nc == 256
+        off += G * nc
+    assert plan.output_size == off
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("n,k", [(33, 6.0), (129, 10.0)])
+def test_mode_factors_reproduce_oracle_solves(mdp, ap, n, k):
+    """G^(h) maps sin(pi q m/Nx) b(n) to sin(pi q m/Nx) T_q^{-1} b (separability of the AP);
+    the plan's factors must reproduce the oracle's sparse-LU solve of the 2-D system, and
+    T_q^{-H} its adjoint solve (up to the 1/h row scale of the Sommerfeld rows)."""
+    sub = W.small_subdomain(n, k, ap, 4)
+    plan = mdp.Plan([sub], host_only=True)
+    S = APSystem(sub)
+    nc = n - 1
+    first = 0 if ap == W.AP_DIRX_SOMMY else 1
+    rows = np.arange(first, n - first)
+    rng = np.random.default_rng(7)
+    for q in (1, 2, nc // 3, nc // 2, nc - 1):
+        sx = np.sin(np.pi * q * np.arange(n) / nc)
+        b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        b[0] = b[-1] = 0.0                      # the AP right-hand side lives on M0
+        g = np.outer(b, sx)
+        u = S.solve(g)
+        x = plan.host_mode_solve(0, q, b[rows])
+        ref = u[rows][:, 1:-1]
+        assert np.abs(ref - np.outer(x, sx[1:-1])).max() < 1e-10 * np.abs(ref).max()
+        # adjoint: A^{-H} y for separable y on the unknowns
+        y = rng.standard_normal(rows.size) + 1j * rng.standard_normal(rows.size)
+        yy = np.zeros((n, n), complex)
+        yy[rows] = np.outer(y, sx)
+        yy[:, 0] = yy[:, -1] = 0
+        mu = S.solve_adjoint(yy)
+        xa = plan.host_mode_solve(0, q, y, adjoint=True)
+        if ap == W.AP_DIRX_SOMMY:
+            xa[0] /= sub.h
+            xa[-1] /= sub.h
+        refa = mu[rows][:, 1:-1]
+        assert np.abs(refa - np.outer(xa, sx[1:-1])).max() < 1e-10 * np.abs(refa).max()
+
+
+def test_argument_validation(mdp):
+    from paper_2103_12172_gb300 import MdpError
+    good = W.small_subdomain(33, 5.0, 1, 4)
+    bad = [
+        W.Subdomain(0, 1, 0, 1, -0.1, -0.1, 1.2 / 6, 7, 7, 5.0, 1, 4),         # nx < 9
+        good.with_k(0.0),                                                     # k <= 0
+        W.Subdomain(0, 1, 0, 1, -0.1, -0.1, good.h, 33, 33, 5.0, 1, 0),       # M* < 1
+        W.Subdomain(0, 1, 0, 1, -0.01, -0.1, good.h, 33, 33, 5.0, 1, 4),      # gamma on the AP boundary
+        W.Subdomain(0, 1, 0, 1, -0.1, -0.1, good.h, 33, 33, 5.0, 7, 4),       # unknown AP type
+    ]
+    for s in bad:
+        with pytest.raises(MdpError) as e:
+            mdp.Plan([s], host_only=True)
+        assert e.value.code == 1  # MDP_ERR_ARG
+    with pytest.raises(MdpError):
+        mdp.Plan([], host_only=True)
+
+
+def test_dirichlet_resonance_is_reported(mdp):
+    """A Dirichlet AP whose discrete symbol mu_pq vanishes (k^2 chosen on a discrete
+    eigenvalue) has a singular mode system: the plan reports MDP_ERR_SINGULAR."""
+    from paper_2103_12172_gb300 import MdpError
+    n = 33
+    nc = n - 1
+    h = 1.2 / nc
+    lam = -4 * np.sin(np.pi * np.array([2, 3]) / (2 * nc)) ** 2
+    lp, lq = lam
+    k2 = -((lp + lq) / h**2 + lp * lq / (6 * h**2)) / (1 + (lp + lq) / 12)
+    sub = W.small_subdomain(n, np.sqrt(k2), W.AP_DIRICHLET4, 4)
+    with pytest.raises(MdpError) as e:
+        mdp.Plan([sub], host_only=True)
+    assert e.value.code == 4  # MDP_ERR_SINGULAR
+    mdp.Plan([sub.with_k(np.sqrt(k2) * 1.05)], host_only=True)  # off resonance it plans
