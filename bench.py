@@ -46,19 +46,22 @@ def _oracle_worker_cols(cols):
     return len(cols), time.perf_counter() - t
 
 
-def oracle_throughput(sub, n_cols, workers, seconds_hint=None):
+def oracle_throughput(sub, workers, min_seconds=10.0):
     """Columns/s of the oracle over `workers` spawned processes, each factoring `sub` once
-    (untimed, like plan creation) and solving its share of n_cols basis columns."""
+    (untimed, like plan creation) and solving basis columns in rounds of one column per
+    worker until at least `min_seconds` of wall time have passed."""
     import dataclasses
     ctx = mp.get_context("spawn")
+    ncol = 8 * sub.n_modes
     with ctx.Pool(workers, initializer=_oracle_worker_init, initargs=(dataclasses.asdict(sub),)) as pool:
         pool.map(_oracle_worker_cols, [[0]] * workers)  # warm: factor in every worker
-        chunks = [list(range(i, n_cols, workers)) for i in range(workers)]
-        chunks = [[c % (8 * sub.n_modes) for c in ch] for ch in chunks if ch]
+        done, c = 0, 0
         t = time.perf_counter()
-        res = pool.map(_oracle_worker_cols, chunks)
+        while time.perf_counter() - t < min_seconds:
+            chunks = [[(c + i) % ncol] for i in range(workers)]
+            c += workers
+            done += sum(r[0] for r in pool.map(_oracle_worker_cols, chunks))
         wall = time.perf_counter() - t
-    done = sum(r[0] for r in res)
     return done / wall, done, wall
 
 
@@ -307,7 +310,7 @@ def run_ours(args, wl):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         workers = max(1, min(16, os.cpu_count() or 1))
         sub = subs[0]
-        cps, done, wall_c = oracle_throughput(sub, 4 * workers, workers)
+        cps, done, wall_c = oracle_throughput(sub, workers)
         line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": workers, "kind": "oracle",
                                 "sample": f"{done} basis columns of subdomain 0 ({sub.nx}x{sub.ny}, k={sub.k}) over "
                                           f"{workers} spawned processes, SuperLU factor per process untimed, "
