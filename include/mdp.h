@@ -133,6 +133,24 @@ mdp_status mdp_ap_adjoint(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, md
 mdp_status mdp_ap_solve_batch(mdp_plan *p, int sub, int nrhs, const mdp_c64 *g, mdp_c64 *u,
                               int adjoint, void *cuda_stream);
 
+/* The full-grid solve of mdp_ap_solve_batch without a plan and without any device
+ * allocation, for callers that cannot call cudaMalloc (an allocator-free runtime, or a caller
+ * that owns every device byte). The paper has no counterpart: this is an interface choice.
+ * `sub` (host) describes one subdomain; g and u are caller-owned device arrays
+ * [nrhs][ny][nx] with the meaning of mdp_ap_solve_batch. Each call recomputes the per-mode
+ * factors on the host and copies them, with the descriptor, into a fixed scratch array of
+ * mdp_ap_solve_noalloc_limit_bytes() bytes (32 MiB) that lives in device memory for the
+ * lifetime of the process on every device that loads the library; the mode-space buffer uses
+ * the rest of it, in chunks of right-hand sides. Grids whose tables plus one right-hand side do
+ * not fit return MDP_ERR_ARG. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture. All calls share the one
+ * array: calls whose work overlaps on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller. Nothing needs zeroing between calls: every call
+ * overwrites what it reads. */
+mdp_status mdp_ap_solve_noalloc(const mdp_subdomain *sub, int nrhs, const mdp_c64 *g, mdp_c64 *u,
+                                int adjoint, void *cuda_stream);
+long long mdp_ap_solve_noalloc_limit_bytes(void);
+
 /* Synchronise the plan's device, return and clear the sticky device status word. */
 mdp_status mdp_plan_status(mdp_plan *p);
 

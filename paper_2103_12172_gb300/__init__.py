@@ -20,7 +20,7 @@ import numpy as np
 from . import _lib
 from ._lib import MdpError, MDP_OUT_P, MDP_OUT_Q, MDP_PLAN_HOST_ONLY
 
-__all__ = ["Plan", "MdpError", "probe_fp64_gflops", "as_c_subdomains"]
+__all__ = ["Plan", "MdpError", "probe_fp64_gflops", "as_c_subdomains", "solve_noalloc"]
 
 _KINDS = {"Q": MDP_OUT_Q, "P": MDP_OUT_P}
 
@@ -187,6 +187,19 @@ class Plan:
 
     def status(self):
         _lib.check(self.L.mdp_plan_status(self.handle), "device status")
+
+
+def solve_noalloc(sub, g, adjoint: bool = False, out=None, stream=None):
+    """Full-grid AP solve of one subdomain without a plan and without device allocation
+    inside the library (mdp_ap_solve_noalloc); g, out: complex128 CUDA tensors [nrhs, ny, nx]."""
+    import torch
+    g = g.reshape(-1, sub.ny, sub.nx)
+    if out is None:
+        out = torch.empty_like(g)
+    arr = as_c_subdomains([sub])
+    _lib.check(_lib.lib().mdp_ap_solve_noalloc(arr, g.shape[0], _ptr(g), _ptr(out), int(adjoint), _stream_ptr(stream)),
+               "mdp_ap_solve_noalloc")
+    return out
 
 
 def probe_fp64_gflops(iters: int = 0, stream=None) -> float:

@@ -64,6 +64,8 @@ def lib():
         "mdp_kernel_family_count": (i, []),
         "mdp_kernel_family_name": (C.c_char_p, [i]),
         "mdp_plan_sub_info": (i, [vp, i, C.POINTER(i)]),
+        "mdp_ap_solve_noalloc": (i, [C.POINTER(mdp_subdomain), i, vp, vp, i, vp]),
+        "mdp_ap_solve_noalloc_limit_bytes": (ll, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -557,6 +557,25 @@ cudaError_t launch_solve(const mdp_plan *p, int sub, int nrhs, const double2 *g,
   return cudaSuccess;
 }
 
+// Full-grid solve on caller-provided device tables and scratch (one subdomain at d_sub[0]).
+cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const double *tab, const uint8_t *piv,
+                             double *buf, long long buf_doubles, int nrhs, const double2 *g, double2 *u, int adjoint,
+                             cudaStream_t st) {
+  const long long per = (long long)hd.Nq * hd.Nt * 2;
+  long long chunk = buf_doubles / per;
+  if (chunk < 1) return cudaErrorInvalidValue;
+  if (chunk > 65535) chunk = 65535;
+  for (int r0 = 0; r0 < nrhs; r0 += (int)chunk) {
+    const int nr = (int)std::min<long long>(chunk, nrhs - r0);
+    k_full_fwd<<<dim3((hd.Nq + 63) / 64, hd.Nt, nr), 64, 0, st>>>(d_sub, 0, tab, g, buf, r0, nr, adjoint);
+    k_full_tri<<<dim3((hd.Nq + 63) / 64, nr), 64, 0, st>>>(d_sub, 0, tab, piv, buf, nr, adjoint);
+    k_full_inv<<<dim3((hd.nx + 63) / 64, hd.ny, nr), 64, 0, st>>>(d_sub, 0, tab, buf, u, r0, nr, adjoint);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // ---------------------------------------------------------------- launchers
 static inline dim3 grid1(int n) { return dim3((unsigned)n, 1, 1); }
 

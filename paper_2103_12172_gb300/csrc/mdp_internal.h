@@ -134,4 +134,7 @@ cudaError_t launch_adjoint(mdp_plan *p, const Batch *fam_batches, int out_kind, 
                            const double2 *cot, double2 *grad_xi, double *grad_k, cudaStream_t st);
 cudaError_t launch_solve(const mdp_plan *p, int sub, int nrhs, const double2 *g, double2 *u, int adjoint,
                          cudaStream_t st);
+cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const double *tab, const uint8_t *piv,
+                             double *buf, long long buf_doubles, int nrhs, const double2 *g, double2 *u, int adjoint,
+                             cudaStream_t st);
 }  // namespace mdp

@@ -1,0 +1,83 @@
+// mdp_ap_solve_noalloc: the full-grid AP solve of mdp_ap_solve_batch for callers that cannot
+// allocate device memory (for example code running where cudaMalloc is unavailable or
+// forbidden, such as inside an allocator-free runtime or a caller that owns every device byte).
+// Its scratch -- the subdomain descriptor, the per-mode LU factors and sine tables, and the
+// mode-space buffer -- lives in one file-scope device array of fixed size that every GPU loading
+// this library holds until the process exits. Nothing is allocated on the device per call.
+#include "mdp_internal.h"
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 32u << 20;  // 32 MiB per device
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
+
+// Device address of the scratch array on the current device. The first call on a device looks
+// it up with cudaGetSymbolAddress (the host-side symbol is only a stand-in, not a device address).
+mdp_status scratch_address(int dev, void **out) {
+  if (dev < 0 || dev >= kMaxDevices) return MDP_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return MDP_ERR_CUDA;
+    g_scratch_addr[dev] = ptr;
+  }
+  *out = g_scratch_addr[dev];
+  return MDP_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" mdp_status mdp_ap_solve_noalloc(const mdp_subdomain *sub, int nrhs, const mdp_c64 *g, mdp_c64 *u,
+                                           int adjoint, void *cuda_stream) {
+  if (!sub || nrhs < 0 || (nrhs > 0 && (!g || !u)) || (adjoint != 0 && adjoint != 1)) return MDP_ERR_ARG;
+  // host tables for this one subdomain (geometry checks, per-mode factors, sine tables)
+  mdp_plan hp;
+  hp.flags = MDP_PLAN_HOST_ONLY;
+  hp.n_subs = 1;
+  mdp_status st;
+  try {
+    st = mdp::build_host_plan(&hp, sub, 1);
+  } catch (...) {
+    st = MDP_ERR_NOMEM;
+  }
+  if (st != MDP_OK) return st;
+  const mdp::SubDesc &hd = hp.subs[0].d;
+  // scratch layout: [descriptor | tables | pivot flags | mode-space buffer]
+  const size_t off_tab = align256(sizeof(mdp::SubDesc));
+  const size_t off_piv = off_tab + align256(hp.host_tables.size() * sizeof(double));
+  const size_t off_buf = off_piv + align256(hp.host_piv.size());
+  const size_t per_rhs = (size_t)hd.Nq * hd.Nt * 2 * sizeof(double);
+  if (off_buf + per_rhs > kNoAllocScratchBytes) return MDP_ERR_ARG;  // grid too large for the fixed scratch
+  if (nrhs == 0) return MDP_OK;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MDP_ERR_CUDA;
+  void *base = nullptr;
+  st = scratch_address(dev, &base);
+  if (st != MDP_OK) return st;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned char *b = (unsigned char *)base;
+  // pageable-source copies are staged before these calls return, so the host tables may go
+  if (cudaMemcpyAsync(b, &hd, sizeof hd, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b + off_tab, hp.host_tables.data(), hp.host_tables.size() * sizeof(double),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b + off_piv, hp.host_piv.data(), hp.host_piv.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return MDP_ERR_CUDA;
+  const long long buf_doubles = (long long)((kNoAllocScratchBytes - off_buf) / sizeof(double));
+  if (mdp::launch_solve_raw((const mdp::SubDesc *)b, hd, (const double *)(b + off_tab), (const uint8_t *)(b + off_piv),
+                            (double *)(b + off_buf), buf_doubles, nrhs, (const double2 *)g, (double2 *)u, adjoint,
+                            s) != cudaSuccess)
+    return MDP_ERR_CUDA;
+  return MDP_OK;
+}
+
+extern "C" long long mdp_ap_solve_noalloc_limit_bytes(void) { return (long long)kNoAllocScratchBytes; }
