@@ -145,6 +145,8 @@ class Plan:
         gx = torch.empty(n, dtype=torch.complex128, device="cuda") if grad_xi else None
         if grad_k is None:
             grad_k = torch.zeros(self.n_subs, dtype=torch.float64, device="cuda")
+        elif grad_k is False:
+            grad_k = None
         _lib.check(self.L.mdp_ap_adjoint(self.handle, _ptr(xi), _ptr(cot), _ptr(gx), _ptr(grad_k), _KINDS[kind],
                                          _stream_ptr(stream)), "mdp_ap_adjoint")
         return gx, grad_k

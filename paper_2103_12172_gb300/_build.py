@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmdp.so")
-SOURCES = ["plan.cpp", "kernels.cu", "api.cu", "probe.cu", "noalloc.cu"]
+SOURCES = ["plan.cpp", "kernels.cu", "kernels_adj.cu", "api.cu", "probe.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,7 +40,7 @@ def _stale(target, deps):
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if needed) and return the path of libmdp.so."""
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "mdp.h"))
     objs = []
     jobs = []

@@ -35,8 +35,12 @@ void free_device(mdp_plan *p) {
   cudaFree(p->d_status);
   for (auto x : p->d_wave_items) cudaFree(x);
   for (auto x : p->d_wave_prefix) cudaFree(x);
+  for (auto x : p->d_gwave_items) cudaFree(x);
+  for (auto x : p->d_gwave_prefix) cudaFree(x);
   p->d_wave_items.clear();
   p->d_wave_prefix.clear();
+  p->d_gwave_items.clear();
+  p->d_gwave_prefix.clear();
   p->d_subs = nullptr; p->d_tables = nullptr; p->d_piv = nullptr; p->d_ws = nullptr; p->d_status = nullptr;
   if (prev >= 0) cudaSetDevice(prev);
 }
@@ -61,38 +65,43 @@ mdp_status alloc_device(mdp_plan *p) {
   CK(cudaMemset(p->d_status, 0, sizeof(int)));
   mdp_status st = upload_subs_tables(p);
   if (st != MDP_OK) return st;
-  p->h_wave_prefix.clear();
-  for (auto &w : p->waves) {
-    const int n = (int)w.items.size();
-    Item *di = nullptr;
-    int *dp = nullptr;
-    if (!al((void **)&di, n * sizeof(Item)) || !al((void **)&dp, (size_t)NFAM * (n + 1) * sizeof(int))) {
-      if (di) cudaFree(di);
-      return MDP_ERR_NOMEM;
+  for (int pass = 0; pass < 2; ++pass) {
+    auto &waves = pass ? p->gwaves : p->waves;
+    auto &ditems = pass ? p->d_gwave_items : p->d_wave_items;
+    auto &dpre = pass ? p->d_gwave_prefix : p->d_wave_prefix;
+    auto &hpre = pass ? p->h_gwave_prefix : p->h_wave_prefix;
+    hpre.clear();
+    for (auto &w : waves) {
+      const int n = (int)w.items.size();
+      Item *di = nullptr;
+      int *dp = nullptr;
+      if (!al((void **)&di, n * sizeof(Item))) return MDP_ERR_NOMEM;
+      ditems.push_back(di);
+      if (!al((void **)&dp, (size_t)NFAM * (n + 1) * sizeof(int))) return MDP_ERR_NOMEM;
+      dpre.push_back(dp);
+      std::vector<int> pre((size_t)NFAM * (n + 1), 0);
+      for (int f = 0; f < NFAM; ++f)
+        for (int i = 0; i < n; ++i)
+          pre[(size_t)f * (n + 1) + i + 1] =
+              pre[(size_t)f * (n + 1) + i] + blocks_for((Fam)f, p->subs[w.items[i].sub].d, w.items[i].ncols);
+      CK(cudaMemcpy(di, w.items.data(), n * sizeof(Item), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(dp, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
+      hpre.push_back(pre);
     }
-    p->d_wave_items.push_back(di);
-    p->d_wave_prefix.push_back(dp);
-    std::vector<int> pre((size_t)NFAM * (n + 1), 0);
-    for (int f = 0; f < NFAM; ++f)
-      for (int i = 0; i < n; ++i)
-        pre[(size_t)f * (n + 1) + i + 1] =
-            pre[(size_t)f * (n + 1) + i] + blocks_for((Fam)f, p->subs[w.items[i].sub].d, w.items[i].ncols);
-    CK(cudaMemcpy(di, w.items.data(), n * sizeof(Item), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(dp, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
-    p->h_wave_prefix.push_back(pre);
   }
   return MDP_OK;
 }
 
-void wave_batches(const mdp_plan *p, size_t w, Batch *fb) {
-  const int n = (int)p->waves[w].items.size();
+void wave_batches(const mdp_plan *p, size_t w, Batch *fb, bool grad = false) {
+  const auto &waves = grad ? p->gwaves : p->waves;
+  const int n = (int)waves[w].items.size();
   for (int f = 0; f < NFAM; ++f) {
     Batch &b = fb[f];
     std::memset(&b, 0, sizeof b);
-    b.items = p->d_wave_items[w];
-    b.prefix = p->d_wave_prefix[w] + (size_t)f * (n + 1);
+    b.items = grad ? p->d_gwave_items[w] : p->d_wave_items[w];
+    b.prefix = (grad ? p->d_gwave_prefix[w] : p->d_wave_prefix[w]) + (size_t)f * (n + 1);
     b.n_items = n;
-    b.total_blocks = p->h_wave_prefix[w][(size_t)f * (n + 1) + n];
+    b.total_blocks = (grad ? p->h_gwave_prefix[w] : p->h_wave_prefix[w])[(size_t)f * (n + 1) + n];
   }
 }
 
@@ -245,9 +254,19 @@ mdp_status mdp_project_columns(mdp_plan *p, int sub, int col0, int ncols, const 
 
 mdp_status mdp_ap_adjoint(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, mdp_c64 *grad_xi, double *grad_k,
                           int out_kind, void *cuda_stream) {
-  (void)xi; (void)cot; (void)grad_xi; (void)grad_k; (void)out_kind; (void)cuda_stream;
-  if (!p) return MDP_ERR_ARG;
-  return MDP_ERR_STATE;
+  if (!p || !cot || (out_kind != MDP_OUT_Q && out_kind != MDP_OUT_P)) return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_ERR_STATE;
+  if (!grad_xi && !grad_k) return MDP_OK;
+  if ((grad_xi && ((const void *)grad_xi == (const void *)cot || (const void *)grad_xi == (const void *)xi)))
+    return MDP_ERR_ARG;
+  CK(cudaSetDevice(p->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  for (size_t w = 0; w < p->gwaves.size(); ++w) {
+    Batch fb[NFAM];
+    wave_batches(p, w, fb, true);
+    CK(launch_adjoint(p, fb, out_kind, (const double2 *)xi, (const double2 *)cot, (double2 *)grad_xi, grad_k, st));
+  }
+  return MDP_OK;
 }
 
 mdp_status mdp_ap_solve_batch(mdp_plan *p, int sub, int nrhs, const mdp_c64 *g, mdp_c64 *u, int adjoint,

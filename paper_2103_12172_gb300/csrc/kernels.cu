@@ -12,73 +12,9 @@
 // each block finds its item by binary search over a prefix array. Within an item, the block
 // is (32 columns) x (BY tasks): a warp shares one task (one mode, one row ...), so factor and
 // sine-table loads are warp-uniform broadcasts and column data is read coalesced.
-#include "mdp_internal.h"
+#include "kernels_common.cuh"
 
 namespace mdp {
-
-// ---------------------------------------------------------------- complex helpers
-struct cplx { double re, im; };
-__device__ __forceinline__ cplx cmk(double a, double b) { return {a, b}; }
-__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
-  return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
-}
-// a - b*c
-__device__ __forceinline__ cplx cfms(cplx a, cplx b, cplx c) {
-  return {fma(-b.re, c.re, fma(b.im, c.im, a.re)), fma(-b.re, c.im, fma(-b.im, c.re, a.im))};
-}
-// a + s*c (s real)
-__device__ __forceinline__ cplx caxpy(double s, cplx c, cplx a) { return {fma(s, c.re, a.re), fma(s, c.im, a.im)}; }
-__device__ __forceinline__ cplx ld2(const double *p) {
-  double2 v = *reinterpret_cast<const double2 *>(p);
-  return {v.x, v.y};
-}
-__device__ __forceinline__ void st2(double *p, cplx v) { *reinterpret_cast<double2 *>(p) = make_double2(v.re, v.im); }
-
-// ---------------------------------------------------------------- batch addressing
-__device__ __forceinline__ void locate(const Batch &b, int blk, Item &it, int &local) {
-  if (b.items == nullptr) { it = b.one; local = blk; return; }
-  int lo = 0, hi = b.n_items - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (b.prefix[mid] <= blk) lo = mid; else hi = mid - 1;
-  }
-  it = b.items[lo];
-  local = blk - b.prefix[lo];
-}
-
-// gamma index of node (n, m), or -1 (row-major order of the 2-node ring around M+)
-__device__ __forceinline__ int gamma_index(const SubDesc &d, int n, int m) {
-  if (n < d.nlo - 1 || n > d.nhi + 1 || m < d.mlo - 1 || m > d.mhi + 1) return -1;
-  const int W = d.Px + 2, Mr = d.Py - 2;
-  const int dm = m - (d.mlo - 1);
-  if (n == d.nlo - 1) return dm;
-  if (n == d.nlo) return W + dm;
-  if (n == d.nhi) return 2 * W + 4 * Mr + dm;
-  if (n == d.nhi + 1) return 3 * W + 4 * Mr + dm;
-  int slot = (m == d.mlo - 1) ? 0 : (m == d.mlo) ? 1 : (m == d.mhi) ? 2 : (m == d.mhi + 1) ? 3 : -1;
-  if (slot < 0) return -1;
-  return 2 * W + 4 * (n - d.nlo - 1) + slot;
-}
-
-// node of ring index ri (row-major order of the 2-node ring inside M+)
-__device__ __forceinline__ void ring_node(const SubDesc &d, int ri, int &n, int &m) {
-  const int P = d.Px, Mr = 4 * (d.Py - 4);
-  if (ri < P) { n = d.nlo; m = d.mlo + ri; return; }
-  if (ri < 2 * P) { n = d.nlo + 1; m = d.mlo + ri - P; return; }
-  if (ri < 2 * P + Mr) {
-    const int t = ri - 2 * P, slot = t & 3;
-    n = d.nlo + 2 + (t >> 2);
-    m = slot == 0 ? d.mlo : slot == 1 ? d.mlo + 1 : slot == 2 ? d.mhi - 1 : d.mhi;
-    return;
-  }
-  if (ri < 3 * P + Mr) { n = d.nhi - 1; m = d.mlo + ri - 2 * P - Mr; return; }
-  n = d.nhi; m = d.mlo + ri - 3 * P - Mr;
-}
-
-// side (1..4) of basis column c
-__device__ __forceinline__ int col_side(const SubDesc &d, int c) { return (c % (4 * d.n_modes)) / d.n_modes + 1; }
 
 // ---------------------------------------------------------------- k_extend
 // One thread per gamma node: the Chebyshev recurrences for T_j, T_j'', T_j'''' (with T', T'''
@@ -135,19 +71,6 @@ __global__ void __launch_bounds__(128) k_extend(Batch bt, const SubDesc *subs, c
   }
 }
 
-// density value xi(c, g) for the item's column b (basis: owner check; user: complex array)
-template <bool CIN>
-__device__ __forceinline__ cplx density(const SubDesc &d, const Item &it, const double *ws, const double *tab,
-                                        const double2 *xi_user, int b, int g) {
-  if (!CIN) {
-    const int own = (int)tab[d.geo_off + 4 * g];
-    if (own != col_side(d, it.col0 + b)) return cmk(0.0, 0.0);
-    return cmk(ws[it.xi_off + (long long)g * it.ncols + b], 0.0);
-  }
-  const double2 v = xi_user[it.io_off + (long long)b * d.G + g];
-  return cmk(v.x, v.y);
-}
-
 // ---------------------------------------------------------------- k_residual
 // r(ring node, column) = sum over the 3x3 stencil of the gamma neighbours: w = xi on gamma,
 // 0 elsewhere, so only gamma nodes contribute. Output r[ri][b] (real for basis densities).
@@ -178,6 +101,44 @@ __global__ void __launch_bounds__(256) k_residual(Batch bt, const SubDesc *subs,
   double *r = ws + it.r_off;
   if (CIN) st2(r + 2 * ((long long)ri * it.ncols + b), acc);
   else r[(long long)ri * it.ncols + b] = acc.re;
+}
+
+// Gradient pass: r = L w|ring as k_residual, and s = (dL/dk w + L dw/dk)|ring (complex [R][b]),
+// the k-derivative of the ring residual (dw/dk: the extension's own k-dependence, basis only).
+template <bool CIN>
+__global__ void __launch_bounds__(256) k_residual_grad(Batch bt, const SubDesc *subs, const double *tab, double *ws,
+                                                       const double2 *xi_user) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int ri = (local / cb) * 8 + threadIdx.y;
+  if (b >= it.ncols || ri >= d.R) return;
+  int n, m;
+  ring_node(d, ri, n, m);
+  const int side = col_side(d, it.col0 + b);
+  const double *dxi = ws + it.xi_off + (long long)d.G * it.ncols;
+  cplx acc = cmk(0.0, 0.0), sacc = cmk(0.0, 0.0);
+#pragma unroll
+  for (int dn = -1; dn <= 1; ++dn) {
+#pragma unroll
+    for (int dm = -1; dm <= 1; ++dm) {
+      const int g = gamma_index(d, n + dn, m + dm);
+      if (g < 0) continue;
+      const int nb = (dn != 0) + (dm != 0);
+      const double c = nb == 0 ? d.c0 : nb == 1 ? d.c1 : d.c2;
+      const double dc = nb == 0 ? d.dc0 : nb == 1 ? d.dc1 : 0.0;
+      const cplx v = density<CIN>(d, it, ws, tab, xi_user, b, g);
+      acc = caxpy(c, v, acc);
+      sacc = caxpy(dc, v, sacc);
+      if (!CIN && (int)tab[d.geo_off + 4 * g] == side) sacc.re = fma(c, dxi[(long long)g * it.ncols + b], sacc.re);
+    }
+  }
+  double *r = ws + it.r_off;
+  if (CIN) st2(r + 2 * ((long long)ri * it.ncols + b), acc);
+  else r[(long long)ri * it.ncols + b] = acc.re;
+  st2(ws + it.s_off + 2 * ((long long)ri * it.ncols + b), sacc);
 }
 
 // ---------------------------------------------------------------- k_fwd_rows
@@ -231,10 +192,12 @@ __global__ void __launch_bounds__(128) k_fwd_rows(Batch bt, const SubDesc *subs,
 // (columns mlo, mlo+1, mhi-1, mhi), so their sine transform is 4 products here.
 // CF: complex factors. CIN: complex ring data. Output y[q-1][n - (nlo-1)][b] for the rows
 // nlo-1 .. nhi+1, complex unless neither CF nor CIN (real path).
-template <bool CF, bool CIN>
+// FULL: back substitution down to row 0 and every row stored as y[q-1][i][b] (i = 0..Nt-1),
+// the layout of the gradient pass.
+template <bool CF, bool CIN, bool FULL>
 __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const double *tab, const uint8_t *pivtab,
                                          double *ws, int b, int q) {
-  constexpr bool CD = CF || CIN;  // complex data in the sweep
+  constexpr bool CD = CF || CIN || FULL;  // complex data in the sweep (the gradient pass stores complex)
   const int N2 = 2 * d.Nx;
   const double *S = tab + d.sin_off;
   const double sm0 = S[(q * d.mlo) % N2], sm1 = S[(q * (d.mlo + 1)) % N2];
@@ -246,7 +209,8 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
   const double *gr = ws + it.gr_off;
   double *y = ws + it.y_off;
   const long long ystride = it.ncols;                         // between stored rows
-  const long long ybase = (long long)(q - 1) * d.NYf * it.ncols + b;
+  const int yrows = FULL ? d.Nt : d.NYf, yfirst = FULL ? 0 : d.i0;
+  const long long ybase = (long long)(q - 1) * yrows * it.ncols + b;
   const int P = d.Px, nc = it.ncols;
   auto rhs = [&](int n) -> cplx {
     if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
@@ -272,11 +236,12 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
     return cmk(v, 0.0);
   };
   auto ystore = [&](int i, cplx v) {
-    const long long o = ybase + (long long)(i - d.i0) * ystride;
+    const long long o = ybase + (long long)(i - yfirst) * ystride;
     if (CD) st2(y + 2 * o, v); else y[o] = v.re;
   };
   auto yload = [&](int i) -> cplx {
-    const long long o = ybase + (long long)(i - d.i0) * ystride;
+    if (FULL && i < d.i0) return cmk(0.0, 0.0);   // rows below the ring: zero after elimination
+    const long long o = ybase + (long long)(i - yfirst) * ystride;
     return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
   };
   // forward sweep: cur holds the eliminated value of row i
@@ -300,7 +265,7 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
   // back substitution; keep only rows nlo-1 .. nhi+1
   const int ikeep = d.nhi + 1 - d.nfirst;
   cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
-  for (int i = d.Nt - 1; i >= d.i0; --i) {
+  for (int i = d.Nt - 1; i >= (FULL ? 0 : d.i0); --i) {
     const cplx yi = yload(i);
     cplx x;
     if (CF) {
@@ -316,12 +281,12 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
         if (CD) x.im = fma(-u2, x2.im, x.im);
       }
     }
-    if (i <= ikeep) ystore(i, x);
+    if (FULL || i <= ikeep) ystore(i, x);
     x2 = x1; x1 = x;
   }
 }
 
-template <bool CIN>
+template <bool CIN, bool FULL>
 __global__ void __launch_bounds__(128) k_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
                                              double *ws) {
   Item it; int local;
@@ -331,8 +296,8 @@ __global__ void __launch_bounds__(128) k_tri(Batch bt, const SubDesc *subs, cons
   const int b = (local % cb) * 32 + threadIdx.x;
   const int q = (local / cb) * 4 + threadIdx.y + 1;
   if (b >= it.ncols || q > d.Nq) return;
-  if (d.cplx) tri_body<true, CIN>(it, d, tab, pivtab, ws, b, q);
-  else tri_body<false, CIN>(it, d, tab, pivtab, ws, b, q);
+  if (d.cplx) tri_body<true, CIN, FULL>(it, d, tab, pivtab, ws, b, q);
+  else tri_body<false, CIN, FULL>(it, d, tab, pivtab, ws, b, q);
 }
 
 // ---------------------------------------------------------------- inverse transforms on gamma
@@ -599,8 +564,8 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
   else MDP_LAUNCH(F_RES, k_residual<true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
   if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
   else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
-  if (basis) MDP_LAUNCH(F_TRI, k_tri<false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
-  else MDP_LAUNCH(F_TRI, k_tri<true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  else MDP_LAUNCH(F_TRI, k_tri<true, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   if (basis) {
     MDP_LAUNCH(F_IROWS, k_inv_rows<false><<<grid1(fb[F_IROWS].total_blocks), b8, 0, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
     MDP_LAUNCH(F_ICOLS, k_inv_cols<false><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
@@ -609,6 +574,27 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
     MDP_LAUNCH(F_ICOLS, k_inv_cols<true><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, const double2 *cot,
+                           double2 *grad_xi, double *grad_k, cudaStream_t st) {
+  const bool basis = xi_user == nullptr;
+  const SubDesc *ds = p->d_subs;
+  const double *tab = p->d_tables;
+  double *ws = p->d_ws;
+  const dim3 b8(32, 8), b4(32, 4);
+  if (grad_k) {  // forward recompute with every mode-space row kept, and the k-derivative sources
+    if (basis) MDP_LAUNCH(F_EXT, k_extend<<<grid1(fb[F_EXT].total_blocks), 128, 0, st>>>(fb[F_EXT], ds, tab, ws, 1));
+    if (basis) MDP_LAUNCH(F_RES, k_residual_grad<false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
+    else MDP_LAUNCH(F_RES, k_residual_grad<true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
+    if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
+    else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
+    if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+    else MDP_LAUNCH(F_TRI, k_tri<true, true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_adjoint_tail(p, fb, out_kind, xi_user, cot, grad_xi, grad_k, st);
 }
 
 }  // namespace mdp

@@ -1,0 +1,354 @@
+// Adjoint of the projection columns and the wavenumber gradient (CUDA, sm_103a, FP64).
+//
+// For out_c = (P_gamma - I) xi_c = -Tr G^(h) R L^(h) W xi_c (Sections 3.2.2, 3.2.5) and a real
+// loss with cotangent c = dLoss/d conj(out):
+//   grad_xi_c = -W^T L^T R^T G^H Tr^T c_c   (+ c_c for P_gamma),
+//   dLoss/dk  = Re sum_c [ <mu_c, A' u_c> - <R^T mu_c, s_c> ]   (+ Re <c_c, dxi_c/dk>, P kind),
+// with mu_c = A^{-H} Tr^T c_c, u_c = G^(h) r_c, A' = dA/dk, s_c = (L' w_c + L w'_c)|_{M+}.
+// Along x the sine transform S (unnormalised) diagonalises A: with yhat = S Tr^T c,
+//   muhat_q = T_q^{-H} yhat_q,  mu = (2/Nx) S muhat,  <mu, A'u> = (2/Nx) sum_q <muhat_q, T_q' uhat_q>,
+// so the adjoint is the forward path with gamma and the ring exchanging roles and the
+// conjugate-transposed mode solve. Partial sums of the gradient are reduced per block in a
+// fixed order and then per subdomain in item order (deterministic).
+#include "kernels_common.cuh"
+
+namespace mdp {
+
+static inline dim3 g1(int n) { return dim3((unsigned)n, 1, 1); }
+
+// yhat(q, row) of the 4 full gamma rows of the cotangent (mode pair (q, Nx - q) per thread)
+__global__ void __launch_bounds__(128) k_adj_rows(Batch bt, const SubDesc *subs, const double *tab, double *ws,
+                                                  const double2 *cot) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int q = (local / cb) * 4 + threadIdx.y + 1;
+  if (b >= it.ncols || q > d.Nx / 2) return;
+  const double *S = tab + d.sin_off;
+  const int N2 = 2 * d.Nx, W = d.Px + 2, M4 = 4 * (d.Py - 2);
+  const double2 *ct = cot + it.io_off + (long long)b * d.G;
+  double *gr = ws + it.gr_off;
+  const int q2 = d.Nx - q;
+  for (int rr = 0; rr < 4; ++rr) {
+    const int g0 = rr == 0 ? 0 : rr == 1 ? W : rr == 2 ? 2 * W + M4 : 3 * W + M4;
+    cplx ao = cmk(0.0, 0.0), ae = cmk(0.0, 0.0);
+    int j = (int)(((long long)q * (d.mlo - 1)) % N2);
+    for (int mm = 0; mm < W; ++mm) {
+      const int m = d.mlo - 1 + mm;
+      const double2 cv = ct[g0 + mm];
+      const cplx v = cmk(cv.x, cv.y);
+      if (m & 1) ao = caxpy(S[j], v, ao); else ae = caxpy(S[j], v, ae);
+      j += q;
+      if (j >= N2) j -= N2;
+    }
+    st2(gr + 2 * (((long long)rr * d.Nq + (q - 1)) * it.ncols + b), cadd(ao, ae));
+    if (q2 != q) st2(gr + 2 * (((long long)rr * d.Nq + (q2 - 1)) * it.ncols + b), csub(ao, ae));
+  }
+}
+
+// muhat = T_q^{-H} yhat for one (mode, column): U^H forward substitution (rows below the
+// gamma band carry zero), then the transposed eliminations and row swaps from the top down to
+// row 0. With DK the term Re <muhat, T_q' uhat> is accumulated as rows become final; muhat is
+// kept on the ring rows nlo..nhi (a buffer, rows in matrix numbering).
+template <bool CF, bool DK>
+__device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d, const double *tab,
+                                               const uint8_t *pivtab, double *ws, const double2 *cot, int b, int q) {
+  constexpr int FW = CF ? 8 : 4;
+  const double *F = tab + d.fact_off + (long long)(q - 1) * d.Nt * FW;
+  const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * d.Nt;
+  auto fl = [&](int i, int w) -> cplx { return CF ? ld2(F + i * FW + 2 * w) : cmk(F[i * FW + w], 0.0); };
+  const int N2 = 2 * d.Nx;
+  const double *S = tab + d.sin_off;
+  const double sg0 = S[(q * (d.mlo - 1)) % N2], sg1 = S[(q * d.mlo) % N2];
+  const double sg2 = S[(q * d.mhi) % N2], sg3 = S[(q * (d.mhi + 1)) % N2];
+  const int W = d.Px + 2, nc = it.ncols;
+  const double2 *ct = cot + it.io_off + (long long)b * d.G;
+  const double *gr = ws + it.gr_off;
+  double *a = ws + it.a_off;
+  const long long abase = (long long)(q - 1) * d.Nt * nc + b;
+  auto aptr = [&](int i) { return a + 2 * (abase + (long long)i * nc); };
+  auto rhs = [&](int n) -> cplx {
+    if (n < d.nlo - 1 || n > d.nhi + 1) return cmk(0.0, 0.0);
+    const int rr = n == d.nlo - 1 ? 0 : n == d.nlo ? 1 : n == d.nhi ? 2 : n == d.nhi + 1 ? 3 : -1;
+    if (rr >= 0) return ld2(gr + 2 * (((long long)rr * d.Nq + (q - 1)) * nc + b));
+    const int g0 = 2 * W + 4 * (n - d.nlo - 1);
+    cplx v = cmk(0.0, 0.0);
+    v = caxpy(sg0, cmk(ct[g0].x, ct[g0].y), v);
+    v = caxpy(sg1, cmk(ct[g0 + 1].x, ct[g0 + 1].y), v);
+    v = caxpy(sg2, cmk(ct[g0 + 2].x, ct[g0 + 2].y), v);
+    v = caxpy(sg3, cmk(ct[g0 + 3].x, ct[g0 + 3].y), v);
+    return v;
+  };
+  // U^H zt = yhat, zt_i = conj(d_i) z_i, from the first nonzero row (i0) up
+  cplx t1 = cmk(0.0, 0.0), t2 = cmk(0.0, 0.0);
+  for (int i = d.i0; i < d.Nt; ++i) {
+    cplx v = rhs(i + d.nfirst);
+    if (i - 1 >= d.i0) v = cfms(v, cconj(fl(i - 1, 2)), t1);
+    if (i - 2 >= d.i0 && pv[i - 2]) v = cfms(v, cconj(fl(i - 2, 3)), t2);
+    st2(aptr(i), cmul(cconj(fl(i, 1)), v));
+    t2 = t1; t1 = v;
+  }
+  // z = P_0 E_0^H ... P_{N-2} E_{N-2}^H z; position i+1 is final after step i
+  const double *dT = tab + d.dT_off + (long long)(q - 1) * d.Nt * 6;
+  const double *y = ws + it.y_off;
+  const long long ybase = (long long)(q - 1) * d.Nt * nc + b;
+  auto uhat = [&](int i) -> cplx {
+    if (i < 0 || i >= d.Nt) return cmk(0.0, 0.0);
+    return ld2(y + 2 * (ybase + (long long)i * nc));
+  };
+  double dk = 0.0;
+  cplx uj1 = cmk(0.0, 0.0), uj = DK ? uhat(d.Nt - 1) : cmk(0.0, 0.0);
+  const int jlo = d.nlo - d.nfirst, jhi = d.nhi - d.nfirst;
+  auto emit = [&](int j, cplx mu) {
+    if (DK) {
+      const cplx ujm = uhat(j - 1);
+      const double *t = dT + 6 * j;
+      cplx v = cmul(ld2(t), ujm);
+      v = cadd(v, cmul(ld2(t + 2), uj));
+      v = cadd(v, cmul(ld2(t + 4), uj1));
+      dk = fma(mu.re, v.re, fma(mu.im, v.im, dk));
+      uj1 = uj; uj = ujm;
+    }
+    if (j >= jlo && j <= jhi) st2(aptr(j), mu);
+  };
+  cplx up = ld2(aptr(d.Nt - 1));
+  for (int i = d.Nt - 2; i >= 0; --i) {
+    const cplx zi0 = i >= d.i0 ? ld2(aptr(i)) : cmk(0.0, 0.0);
+    const cplx zi = cfms(zi0, cconj(fl(i, 0)), up);
+    if (pv[i]) emit(i + 1, zi);
+    else { emit(i + 1, up); up = zi; }
+  }
+  emit(0, up);
+  return dk;
+}
+
+template <bool DK>
+__global__ void __launch_bounds__(128) k_adj_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
+                                                 double *ws, const double2 *cot) {
+  __shared__ double sh[128];
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int q = (local / cb) * 4 + threadIdx.y + 1;
+  double dk = 0.0;
+  if (b < it.ncols && q <= d.Nq)
+    dk = d.cplx ? adj_tri_body<true, DK>(it, d, tab, pivtab, ws, cot, b, q)
+                : adj_tri_body<false, DK>(it, d, tab, pivtab, ws, cot, b, q);
+  if (DK) {
+    const double s = block_sum<128>(dk * (2.0 / d.Nx), sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) ws[it.red_off + local] = s;   // slot base 0: k_adj_tri
+  }
+}
+
+// mu on the 4 full ring rows (into the r buffer, complex [R][b]); DK: -Re <mu, s>
+template <bool DK>
+__global__ void __launch_bounds__(256) k_adj_ring_rows(Batch bt, const SubDesc *subs, const double *tab, double *ws) {
+  __shared__ double sh[256];
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int task = (local / cb) * 8 + threadIdx.y;
+  const int P = d.Px, Mr = 4 * (d.Py - 4);
+  double dk = 0.0;
+  if (b < it.ncols && task < 4 * P) {
+    const int rr = task / P, m = d.mlo + task % P;
+    const int n = rr == 0 ? d.nlo : rr == 1 ? d.nlo + 1 : rr == 2 ? d.nhi - 1 : d.nhi;
+    const int j = n - d.nfirst;
+    const double *Si = tab + d.sin_off + 2 * d.Nx;
+    const int N2 = 2 * d.Nx;
+    const double *a = ws + it.a_off;
+    const long long qstride = (long long)d.Nt * it.ncols;
+    const long long base = (long long)j * it.ncols + b;
+    cplx acc = cmk(0.0, 0.0);
+    int jj = m % N2;
+    for (int q = 1; q <= d.Nq; ++q) {
+      acc = caxpy(Si[jj], ld2(a + 2 * (base + (long long)(q - 1) * qstride)), acc);
+      jj += m;
+      if (jj >= N2) jj -= N2;
+    }
+    const int rb = rr == 0 ? 0 : rr == 1 ? P : rr == 2 ? 2 * P + Mr : 3 * P + Mr;
+    const long long o = (long long)(rb + m - d.mlo) * it.ncols + b;
+    st2(ws + it.r_off + 2 * o, acc);
+    if (DK) {
+      const cplx s = ld2(ws + it.s_off + 2 * o);
+      dk = -(acc.re * s.re + acc.im * s.im);
+    }
+  }
+  if (DK) {
+    int base[5];
+    red_slots(d, it.ncols, base);
+    const double s = block_sum<256>(dk, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) ws[it.red_off + base[1] + local] = s;
+  }
+}
+
+// mu on the ring's middle rows nlo+2 .. nhi-2 at the columns mlo, mlo+1, mhi-1, mhi
+template <bool DK>
+__global__ void __launch_bounds__(256) k_adj_ring_cols(Batch bt, const SubDesc *subs, const double *tab, double *ws) {
+  __shared__ double sh[256];
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int t = (local / cb) * 8 + threadIdx.y;
+  double dk = 0.0;
+  if (b < it.ncols && t < d.Py - 4) {
+    const int n = d.nlo + 2 + t, j = n - d.nfirst;
+    const double *Si = tab + d.sin_off + 2 * d.Nx;
+    const int N2 = 2 * d.Nx;
+    const int ms[4] = {d.mlo, d.mlo + 1, d.mhi - 1, d.mhi};
+    int jj[4] = {ms[0] % N2, ms[1] % N2, ms[2] % N2, ms[3] % N2};
+    const double *a = ws + it.a_off;
+    const long long qstride = (long long)d.Nt * it.ncols;
+    const long long base = (long long)j * it.ncols + b;
+    cplx acc[4] = {cmk(0, 0), cmk(0, 0), cmk(0, 0), cmk(0, 0)};
+    for (int q = 1; q <= d.Nq; ++q) {
+      const cplx v = ld2(a + 2 * (base + (long long)(q - 1) * qstride));
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        acc[s] = caxpy(Si[jj[s]], v, acc[s]);
+        jj[s] += ms[s];
+        if (jj[s] >= N2) jj[s] -= N2;
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const long long o = (long long)(2 * d.Px + 4 * t + s) * it.ncols + b;
+      st2(ws + it.r_off + 2 * o, acc[s]);
+      if (DK) {
+        const cplx sv = ld2(ws + it.s_off + 2 * o);
+        dk -= acc[s].re * sv.re + acc[s].im * sv.im;
+      }
+    }
+  }
+  if (DK) {
+    int base[5];
+    red_slots(d, it.ncols, base);
+    const double s = block_sum<256>(dk, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) ws[it.red_off + base[2] + local] = s;
+  }
+}
+
+// grad_xi = -(L mu|ring) on gamma (+ cot for P_gamma); DK with basis densities and the P kind:
+// + Re <cot, dxi/dk>
+template <bool CIN, bool DK>
+__global__ void __launch_bounds__(256) k_adj_gamma(Batch bt, const SubDesc *subs, const double *tab, double *ws,
+                                                   const double2 *cot, double2 *grad_xi, int kind) {
+  __shared__ double sh[256];
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int g = (local / cb) * 8 + threadIdx.y;
+  double dk = 0.0;
+  if (b < it.ncols && g < d.G) {
+    int n, m;
+    gamma_node(d, g, n, m);
+    cplx acc = cmk(0.0, 0.0);
+#pragma unroll
+    for (int dn = -1; dn <= 1; ++dn) {
+#pragma unroll
+      for (int dm = -1; dm <= 1; ++dm) {
+        const int ri = ring_index(d, n + dn, m + dm);
+        if (ri < 0) continue;
+        const int nb = (dn != 0) + (dm != 0);
+        const double c = nb == 0 ? d.c0 : nb == 1 ? d.c1 : d.c2;
+        acc = caxpy(c, ld2(ws + it.r_off + 2 * ((long long)ri * it.ncols + b)), acc);
+      }
+    }
+    const long long io = it.io_off + (long long)b * d.G + g;
+    cplx gx = cmk(-acc.re, -acc.im);
+    if (kind == MDP_OUT_P) {
+      const cplx c = cmk(cot[io].x, cot[io].y);
+      gx = cadd(gx, c);
+      if (DK && !CIN && (int)tab[d.geo_off + 4 * g] == col_side(d, it.col0 + b)) {
+        const double dxi = ws[it.xi_off + (long long)d.G * it.ncols + (long long)g * it.ncols + b];
+        dk = c.re * dxi;
+      }
+    }
+    if (grad_xi) grad_xi[io] = make_double2(gx.re, gx.im);
+  }
+  if (DK) {
+    int base[5];
+    red_slots(d, it.ncols, base);
+    const double s = block_sum<256>(dk, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) ws[it.red_off + base[3] + local] = s;
+  }
+}
+
+// per item: the sum of its partials in slot order; then per subdomain in item order
+__global__ void __launch_bounds__(256) k_red_items(const Item *items, const SubDesc *subs, double *ws) {
+  __shared__ double sh[256];
+  const Item it = items[blockIdx.x];
+  const SubDesc &d = subs[it.sub];
+  int base[5];
+  red_slots(d, it.ncols, base);
+  double v = 0.0;
+  for (int i = threadIdx.x; i < base[4]; i += 256) v += ws[it.red_off + i];
+  // block_sum expects a (32 x 8) layout; use a flat block of 256
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ws[it.red_off + base[4]] = sh[0];
+}
+
+__global__ void k_red_subs(const Item *items, int n_items, const SubDesc *subs, const double *ws, double *grad_k) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < n_items; ++i) {
+    const Item it = items[i];
+    int base[5];
+    red_slots(subs[it.sub], it.ncols, base);
+    grad_k[it.sub] += ws[it.red_off + base[4]];
+  }
+}
+
+cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, const double2 *cot,
+                                double2 *grad_xi, double *grad_k, cudaStream_t st) {
+  const SubDesc *ds = p->d_subs;
+  const double *tab = p->d_tables;
+  double *ws = p->d_ws;
+  const dim3 b8(32, 8), b4(32, 4);
+  const bool dk = grad_k != nullptr, basis = xi_user == nullptr;
+#define ADJ_LAUNCH(fam, ...)                      \
+  do {                                            \
+    if (fb[fam].total_blocks > 0) {               \
+      prof_begin(p, fam, st);                     \
+      __VA_ARGS__;                                \
+      prof_end(p, fam, st);                       \
+    }                                             \
+  } while (0)
+  ADJ_LAUNCH(F_AFWD, k_adj_rows<<<g1(fb[F_AFWD].total_blocks), b4, 0, st>>>(fb[F_AFWD], ds, tab, ws, cot));
+  if (dk) ADJ_LAUNCH(F_ATRI, k_adj_tri<true><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot));
+  else ADJ_LAUNCH(F_ATRI, k_adj_tri<false><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot));
+  if (dk) {
+    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<true><<<g1(fb[F_ARING].total_blocks), b8, 0, st>>>(fb[F_ARING], ds, tab, ws));
+    ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<true><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));
+  } else {
+    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<false><<<g1(fb[F_ARING].total_blocks), b8, 0, st>>>(fb[F_ARING], ds, tab, ws));
+    ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<false><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));
+  }
+  if (dk && basis)
+    ADJ_LAUNCH(F_AGAM, k_adj_gamma<false, true><<<g1(fb[F_AGAM].total_blocks), b8, 0, st>>>(fb[F_AGAM], ds, tab, ws, cot, grad_xi, out_kind));
+  else if (dk)
+    ADJ_LAUNCH(F_AGAM, k_adj_gamma<true, true><<<g1(fb[F_AGAM].total_blocks), b8, 0, st>>>(fb[F_AGAM], ds, tab, ws, cot, grad_xi, out_kind));
+  else if (grad_xi)
+    ADJ_LAUNCH(F_AGAM, k_adj_gamma<true, false><<<g1(fb[F_AGAM].total_blocks), b8, 0, st>>>(fb[F_AGAM], ds, tab, ws, cot, grad_xi, out_kind));
+  if (dk) {
+    k_red_items<<<fb[F_ATRI].n_items, 256, 0, st>>>(fb[F_ATRI].items, ds, ws);
+    k_red_subs<<<1, 32, 0, st>>>(fb[F_ATRI].items, fb[F_ATRI].n_items, ds, ws, grad_k);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mdp

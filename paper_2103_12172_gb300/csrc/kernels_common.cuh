@@ -1,0 +1,131 @@
+// Device helpers shared by the projection and adjoint kernels: complex FP64 arithmetic,
+// batch addressing, and the index maps of gamma (the 2-node ring around M+) and of the ring
+// that carries r = L^(h) w restricted to M+.
+#pragma once
+#include "mdp_internal.h"
+
+namespace mdp {
+
+// ---------------------------------------------------------------- complex helpers
+struct cplx { double re, im; };
+__device__ __forceinline__ cplx cmk(double a, double b) { return {a, b}; }
+__device__ __forceinline__ cplx cadd(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cplx csub(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+  return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+// a - b*c
+__device__ __forceinline__ cplx cfms(cplx a, cplx b, cplx c) {
+  return {fma(-b.re, c.re, fma(b.im, c.im, a.re)), fma(-b.re, c.im, fma(-b.im, c.re, a.im))};
+}
+// a + s*c (s real)
+__device__ __forceinline__ cplx caxpy(double s, cplx c, cplx a) { return {fma(s, c.re, a.re), fma(s, c.im, a.im)}; }
+__device__ __forceinline__ cplx ld2(const double *p) {
+  double2 v = *reinterpret_cast<const double2 *>(p);
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st2(double *p, cplx v) { *reinterpret_cast<double2 *>(p) = make_double2(v.re, v.im); }
+
+// ---------------------------------------------------------------- batch addressing
+__device__ __forceinline__ void locate(const Batch &b, int blk, Item &it, int &local) {
+  if (b.items == nullptr) { it = b.one; local = blk; return; }
+  int lo = 0, hi = b.n_items - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (b.prefix[mid] <= blk) lo = mid; else hi = mid - 1;
+  }
+  it = b.items[lo];
+  local = blk - b.prefix[lo];
+}
+
+// gamma index of node (n, m), or -1 (row-major order of the 2-node ring around M+)
+__device__ __forceinline__ int gamma_index(const SubDesc &d, int n, int m) {
+  if (n < d.nlo - 1 || n > d.nhi + 1 || m < d.mlo - 1 || m > d.mhi + 1) return -1;
+  const int W = d.Px + 2, Mr = d.Py - 2;
+  const int dm = m - (d.mlo - 1);
+  if (n == d.nlo - 1) return dm;
+  if (n == d.nlo) return W + dm;
+  if (n == d.nhi) return 2 * W + 4 * Mr + dm;
+  if (n == d.nhi + 1) return 3 * W + 4 * Mr + dm;
+  int slot = (m == d.mlo - 1) ? 0 : (m == d.mlo) ? 1 : (m == d.mhi) ? 2 : (m == d.mhi + 1) ? 3 : -1;
+  if (slot < 0) return -1;
+  return 2 * W + 4 * (n - d.nlo - 1) + slot;
+}
+
+// node of ring index ri (row-major order of the 2-node ring inside M+)
+__device__ __forceinline__ void ring_node(const SubDesc &d, int ri, int &n, int &m) {
+  const int P = d.Px, Mr = 4 * (d.Py - 4);
+  if (ri < P) { n = d.nlo; m = d.mlo + ri; return; }
+  if (ri < 2 * P) { n = d.nlo + 1; m = d.mlo + ri - P; return; }
+  if (ri < 2 * P + Mr) {
+    const int t = ri - 2 * P, slot = t & 3;
+    n = d.nlo + 2 + (t >> 2);
+    m = slot == 0 ? d.mlo : slot == 1 ? d.mlo + 1 : slot == 2 ? d.mhi - 1 : d.mhi;
+    return;
+  }
+  if (ri < 3 * P + Mr) { n = d.nhi - 1; m = d.mlo + ri - 2 * P - Mr; return; }
+  n = d.nhi; m = d.mlo + ri - 3 * P - Mr;
+}
+
+// ring index of node (n, m), or -1
+__device__ __forceinline__ int ring_index(const SubDesc &d, int n, int m) {
+  if (n < d.nlo || n > d.nhi || m < d.mlo || m > d.mhi) return -1;
+  const int P = d.Px, Mr = 4 * (d.Py - 4);
+  if (n == d.nlo) return m - d.mlo;
+  if (n == d.nlo + 1) return P + m - d.mlo;
+  if (n == d.nhi - 1) return 2 * P + Mr + m - d.mlo;
+  if (n == d.nhi) return 3 * P + Mr + m - d.mlo;
+  const int slot = m == d.mlo ? 0 : m == d.mlo + 1 ? 1 : m == d.mhi - 1 ? 2 : m == d.mhi ? 3 : -1;
+  if (slot < 0) return -1;
+  return 2 * P + 4 * (n - d.nlo - 2) + slot;
+}
+
+// node of gamma index g
+__device__ __forceinline__ void gamma_node(const SubDesc &d, int g, int &n, int &m) {
+  const int W = d.Px + 2, M4 = 4 * (d.Py - 2);
+  if (g < W) { n = d.nlo - 1; m = d.mlo - 1 + g; return; }
+  if (g < 2 * W) { n = d.nlo; m = d.mlo - 1 + g - W; return; }
+  if (g < 2 * W + M4) {
+    const int t = g - 2 * W, slot = t & 3;
+    n = d.nlo + 1 + (t >> 2);
+    m = slot == 0 ? d.mlo - 1 : slot == 1 ? d.mlo : slot == 2 ? d.mhi : d.mhi + 1;
+    return;
+  }
+  if (g < 3 * W + M4) { n = d.nhi; m = d.mlo - 1 + g - 2 * W - M4; return; }
+  n = d.nhi + 1; m = d.mlo - 1 + g - 3 * W - M4;
+}
+
+__device__ __forceinline__ cplx cconj(cplx a) { return {a.re, -a.im}; }
+
+// side (1..4) of basis column c
+__device__ __forceinline__ int col_side(const SubDesc &d, int c) { return (c % (4 * d.n_modes)) / d.n_modes + 1; }
+
+// density value xi(c, g) for the item's column b (basis: owner check; user: complex array)
+template <bool CIN>
+__device__ __forceinline__ cplx density(const SubDesc &d, const Item &it, const double *ws, const double *tab,
+                                        const double2 *xi_user, int b, int g) {
+  if (!CIN) {
+    const int own = (int)tab[d.geo_off + 4 * g];
+    if (own != col_side(d, it.col0 + b)) return cmk(0.0, 0.0);
+    return cmk(ws[it.xi_off + (long long)g * it.ncols + b], 0.0);
+  }
+  const double2 v = xi_user[it.io_off + (long long)b * d.G + g];
+  return cmk(v.x, v.y);
+}
+
+
+// Deterministic sum of one double per thread of a (32 x BY) block; thread (0, 0) gets it.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+#pragma unroll
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (t < s) sh[t] += sh[t + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+}  // namespace mdp

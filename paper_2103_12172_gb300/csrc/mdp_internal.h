@@ -94,6 +94,7 @@ struct mdp_plan {
   int tile_cols = 256;                   // columns per work item
   long long ws_budget = 0;               // bytes of workspace
   std::vector<mdp::Wave> waves;          // batch schedule of mdp_project_batch
+  std::vector<mdp::Wave> gwaves;         // batch schedule of mdp_ap_adjoint (larger workspace)
   // device side
   mdp::SubDesc *d_subs = nullptr;
   double *d_tables = nullptr;
@@ -102,9 +103,9 @@ struct mdp_plan {
   long long ws_doubles = 0;
   int *d_status = nullptr;
   // per wave: device items and prefix arrays (one prefix array per kernel family)
-  std::vector<mdp::Item *> d_wave_items;
-  std::vector<int *> d_wave_prefix;      // [wave] -> device int [NFAM][n_items + 1]
-  std::vector<std::vector<int>> h_wave_prefix;
+  std::vector<mdp::Item *> d_wave_items, d_gwave_items;
+  std::vector<int *> d_wave_prefix, d_gwave_prefix;  // [wave] -> device int [NFAM][n_items + 1]
+  std::vector<std::vector<int>> h_wave_prefix, h_gwave_prefix;
   // per-kernel event timing (mdp_plan_profile)
   bool prof_on = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[16];
@@ -112,10 +113,38 @@ struct mdp_plan {
 };
 
 namespace mdp {
-// kernel families (each has its own block decomposition of an item)
-enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_AGAM,
-           F_FULLF, F_FULLT, F_FULLI, NFAM };
-int blocks_for(Fam f, const SubDesc &d, int ncols);
+
+// kernel families (each has its own block decomposition of an item); F_A* are the adjoint's
+enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_ARINGC, F_AGAM, NFAM };
+
+// Blocks of kernel family f for an item of ncols columns: 32 columns (x) times BY tasks (y).
+// The same function numbers the blocks on the host (prefix sums) and in the kernels.
+inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
+  const int cb = (ncols + 31) / 32;
+  switch (f) {
+    case F_EXT: return (d.G + 127) / 128;
+    case F_RES: return cb * ((d.R + 7) / 8);
+    case F_FROWS: return cb * ((d.Nx / 2 + 3) / 4);
+    case F_TRI: return cb * ((d.Nq + 3) / 4);
+    case F_IROWS: return cb * ((4 * (d.Px + 2) + 7) / 8);
+    case F_ICOLS: return cb * ((d.Py - 2 + 7) / 8);
+    case F_AFWD: return cb * ((d.Nx / 2 + 3) / 4);
+    case F_ATRI: return cb * ((d.Nq + 3) / 4);
+    case F_ARING: return cb * ((4 * d.Px + 7) / 8);
+    case F_ARINGC: return cb * ((d.Py - 4 + 7) / 8);
+    case F_AGAM: return cb * ((d.G + 7) / 8);
+    default: return 0;
+  }
+}
+
+// slot bases of the per-block gradient partials of an item: [ATRI | ARING | ARINGC | AGAM], total
+inline __host__ __device__ void red_slots(const SubDesc &d, int ncols, int base[5]) {
+  base[0] = 0;
+  base[1] = base[0] + blocks_for(F_ATRI, d, ncols);
+  base[2] = base[1] + blocks_for(F_ARING, d, ncols);
+  base[3] = base[2] + blocks_for(F_ARINGC, d, ncols);
+  base[4] = base[3] + blocks_for(F_AGAM, d, ncols);
+}
 const char *fam_name(int f);
 // event pair around a launch when profiling is on
 void prof_begin(mdp_plan *p, int fam, cudaStream_t st);
@@ -132,6 +161,10 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fam_batches, int out_kind, 
                            double2 *out, cudaStream_t st);
 cudaError_t launch_adjoint(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,
                            const double2 *cot, double2 *grad_xi, double *grad_k, cudaStream_t st);
+// the adjoint's own kernels (kernels_adj.cu), after the forward recompute of the gradient pass
+cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, const double2 *cot,
+                                double2 *grad_xi, double *grad_k, cudaStream_t st);
+
 cudaError_t launch_solve(const mdp_plan *p, int sub, int nrhs, const double2 *g, double2 *u, int adjoint,
                          cudaStream_t st);
 cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const double *tab, const uint8_t *piv,

@@ -18,25 +18,9 @@ using cd = std::complex<double>;
 static const double kTieTol = 1e-9;       // side-ownership ties within 1e-9*h
 static const double kSingularTol = 1e-13; // pivot below this x max|T| -> singular
 
-// ---------------------------------------------------------------- block decomposition
-// Threads per block: 32 columns (x) times BY tasks (y). Shared with kernels.cu.
-int blocks_for(Fam f, const SubDesc &d, int ncols) {
-  const int cb = (ncols + 31) / 32;
-  switch (f) {
-    case F_EXT: return (d.G + 127) / 128;
-    case F_RES: return cb * ((d.R + 7) / 8);
-    case F_FROWS: return cb * ((d.Nx / 2 + 3) / 4);
-    case F_TRI: return cb * ((d.Nq + 3) / 4);
-    case F_IROWS: return cb * ((4 * (d.Px + 2) + 7) / 8);
-    case F_ICOLS: return cb * ((d.Py - 2 + 7) / 8);
-    default: return 0;
-  }
-}
-
 const char *fam_name(int f) {
   static const char *names[NFAM] = {"k_extend", "k_residual", "k_fwd_rows", "k_tri", "k_inv_rows", "k_inv_cols",
-                                    "k_adj_fwd", "k_adj_tri", "k_adj_ring", "k_adj_gamma", "k_full_fwd",
-                                    "k_full_tri", "k_full_inv"};
+                                    "k_adj_rows", "k_adj_tri", "k_adj_ring_rows", "k_adj_ring_cols", "k_adj_gamma"};
   return (f >= 0 && f < NFAM) ? names[f] : "?";
 }
 
@@ -50,7 +34,9 @@ void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long 
   y = off;  off += al((long long)d.Nq * (grad ? d.Nt : d.NYf) * ncols * 2);
   a = off;  off += grad ? al((long long)d.Nq * d.Nt * ncols * 2) : 0;
   s = off;  off += grad ? al((long long)d.R * ncols * 2) : 0;
-  red = off; off += grad ? al(4096) : 0;
+  int rs[5];
+  red_slots(d, ncols, rs);
+  red = off; off += grad ? al(rs[4] + 1) : 0;
   total = off;
 }
 
@@ -285,11 +271,11 @@ static void fill_tables(mdp_plan *p) {
   }
 }
 
-static void schedule(mdp_plan *p) {
-  p->waves.clear();
+static void schedule_pass(mdp_plan *p, bool grad, std::vector<Wave> &waves) {
+  waves.clear();
   Wave cur;
   cur.ws_doubles = 0;
-  long long budget = p->ws_budget / 8;
+  const long long budget = p->ws_budget / 8;
   for (int si = 0; si < (int)p->subs.size(); ++si) {
     const SubDesc &d = p->subs[si].d;
     for (int c0 = 0; c0 < d.n_cols; c0 += p->tile_cols) {
@@ -297,9 +283,9 @@ static void schedule(mdp_plan *p) {
       std::memset(&it, 0, sizeof it);
       it.sub = si; it.col0 = c0; it.ncols = std::min(p->tile_cols, d.n_cols - c0);
       long long xi, r, gr, y, a, s, red, tot;
-      item_workspace(d, it.ncols, false, xi, r, gr, y, a, s, red, tot);
+      item_workspace(d, it.ncols, grad, xi, r, gr, y, a, s, red, tot);
       if (!cur.items.empty() && cur.ws_doubles + tot > budget) {
-        p->waves.push_back(cur);
+        waves.push_back(cur);
         cur.items.clear();
         cur.ws_doubles = 0;
       }
@@ -311,15 +297,15 @@ static void schedule(mdp_plan *p) {
       cur.ws_doubles += tot;
     }
   }
-  if (!cur.items.empty()) p->waves.push_back(cur);
+  if (!cur.items.empty()) waves.push_back(cur);
+}
+
+static void schedule(mdp_plan *p) {
+  schedule_pass(p, false, p->waves);
+  schedule_pass(p, true, p->gwaves);
   long long mx = 0;
   for (auto &w : p->waves) mx = std::max(mx, w.ws_doubles);
-  // room for a single-item pass of the largest tile (gradient layout) as well
-  for (auto &hs : p->subs) {
-    long long xi, r, gr, y, a, s, red, tot;
-    item_workspace(hs.d, std::min(p->tile_cols, hs.d.n_cols), true, xi, r, gr, y, a, s, red, tot);
-    mx = std::max(mx, tot);
-  }
+  for (auto &w : p->gwaves) mx = std::max(mx, w.ws_doubles);
   p->ws_doubles = mx;
 }
 
