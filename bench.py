@@ -121,8 +121,10 @@ class ClockSampler:
 # ------------------------------------------------------------------ cost model
 def kernel_flops(plan, items):
     """Algorithmic FP64 flops (FMA = 2, mul/add = 1) per kernel for a list of (sub, ncols)
-    work items, from each subdomain's geometry (plan.sub_info): the arithmetic the ring-sparse
-    formulation needs, one count per mode x column x row."""
+    work items, from each subdomain's geometry (plan.sub_info): the arithmetic of the
+    ring-sparse formulation as the kernels perform it -- complex factor rows cost complex
+    multiply-adds, rows whose LU factors are real cost real-by-complex ones, and a centred
+    subdomain pairs m with Nx - m in the sine transforms."""
     tot = {}
 
     def add(k, v):
@@ -130,18 +132,20 @@ def kernel_flops(plan, items):
 
     for sub, nc in items:
         g = plan.sub_info(sub)
-        Px, Py, Nq, Nt, i0, cx, Gm, R, Nx = g["Px"], g["Py"], g["Nq"], g["Nt"], g["i0"], g["cplx"], g["G"], g["R"], g["Nx"]
+        Px, Py, Nq, Nt, i0, cx, R, Nx = g["Px"], g["Py"], g["Nq"], g["Nt"], g["i0"], g["cplx"], g["R"], g["Nx"]
+        xs = g["xsym"]
         nf, nb, nmid = Nt - 1 - i0, Nt - i0, Py - 4
-        if cx:   # complex factors, real ring data in the middle rows
-            tri = nf * 8 + nmid * 8 + nb * 14
+        if cx:
+            f = g["complex_rows"] / float(Nq * (Nt - i0))
+            tri = nf * (8 * f + 4 * (1 - f)) + nmid * (3 if xs else 8) + nb * (14 * f + 6 * (1 - f))
             inv = 4
-        else:    # real factors and real data
-            tri = nf * 2 + nmid * 8 + nb * 3
+        else:
+            tri = nf * 2 + nmid * (3 if xs else 8) + nb * 3
             inv = 2
         add("k_tri", nc * Nq * tri)
-        add("k_inv_cols", nc * (Py - 2) * Nq * 4 * inv)
-        add("k_inv_rows", nc * 4 * (Px + 2) * Nq * inv)
-        add("k_fwd_rows", nc * (Nx // 2) * 4 * Px * 2)
+        add("k_inv_cols", nc * (Py - 2) * Nq * (2 if xs else 4) * inv)
+        add("k_inv_rows", nc * 4 * ((Px // 2 + 2) if xs else (Px + 2)) * Nq * inv)
+        add("k_fwd_rows", nc * (Nx // 2) * 4 * ((Px + 1) // 2 if xs else Px) * 2)
         add("k_residual", nc * R * 9 * 2)
     return tot
 

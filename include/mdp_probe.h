@@ -27,10 +27,11 @@ mdp_status mdp_plan_profile_read(mdp_plan *p, int family, double *total_ms, int 
 int mdp_kernel_family_count(void);
 const char *mdp_kernel_family_name(int family);
 
-/* Geometry of subdomain `sub` as 12 ints: Px, Py (M+ nodes per direction), Nq (sine modes),
+/* Geometry of subdomain `sub` as 14 ints: Px, Py (M+ nodes per direction), Nq (sine modes),
  * Nt (tridiagonal rows), i0 (first swept row), nfirst (first unknown y row), complex factors
- * (0/1), |gamma|, |ring|, number of pivoted rows over all modes, n_cols, Nx. */
-mdp_status mdp_plan_sub_info(const mdp_plan *p, int sub, int *info12);
+ * (0/1), |gamma|, |ring|, number of pivoted rows over all modes, n_cols, Nx, x-centred (0/1),
+ * number of factor rows with complex entries swept by the projection, over all modes. */
+mdp_status mdp_plan_sub_info(const mdp_plan *p, int sub, int *info14);
 
 #ifdef __cplusplus
 }

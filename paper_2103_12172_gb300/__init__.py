@@ -169,9 +169,10 @@ class Plan:
         _lib.check(self.L.mdp_plan_update_k(self.handle, arr), "mdp_plan_update_k")
 
     def sub_info(self, sub: int) -> dict:
-        a = (C.c_int * 12)()
+        a = (C.c_int * 14)()
         _lib.check(self.L.mdp_plan_sub_info(self.handle, sub, a), "mdp_plan_sub_info")
-        keys = ["Px", "Py", "Nq", "Nt", "i0", "nfirst", "cplx", "G", "R", "npiv", "n_cols", "Nx"]
+        keys = ["Px", "Py", "Nq", "Nt", "i0", "nfirst", "cplx", "G", "R", "npiv", "n_cols", "Nx", "xsym",
+                "complex_rows"]
         return dict(zip(keys, list(a)))
 
     def profile(self, enable: bool):

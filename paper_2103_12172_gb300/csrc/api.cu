@@ -351,8 +351,14 @@ mdp_status mdp_plan_sub_info(const mdp_plan *p, int sub, int *info) {
   const SubDesc &d = hs.d;
   int npiv = 0;
   for (auto v : hs.piv) npiv += v;
-  const int vals[12] = {d.Px, d.Py, d.Nq, d.Nt, d.i0, d.nfirst, d.cplx, d.G, d.R, npiv, d.n_cols, d.Nx};
-  for (int i = 0; i < 12; ++i) info[i] = vals[i];
+  long long creal = 0;  // complex factor rows swept by the forward projection, over all modes
+  for (int q = 0; q < d.Nq; ++q) {
+    const int rlo = std::max(hs.seg[2 * q], d.i0), rhi = std::max(hs.seg[2 * q + 1], rlo);
+    creal += (d.Nt - d.i0) - (rhi - rlo);
+  }
+  const int vals[14] = {d.Px, d.Py, d.Nq, d.Nt, d.i0, d.nfirst, d.cplx, d.G, d.R, npiv, d.n_cols, d.Nx,
+                        d.xsym, (int)creal};
+  for (int i = 0; i < 14; ++i) info[i] = vals[i];
   return MDP_OK;
 }
 

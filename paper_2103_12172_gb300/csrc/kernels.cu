@@ -72,51 +72,11 @@ __global__ void __launch_bounds__(128) k_extend(Batch bt, const SubDesc *subs, c
 }
 
 // ---------------------------------------------------------------- k_residual
-// r(ring node, column) = sum over the 3x3 stencil of the gamma neighbours: w = xi on gamma,
-// 0 elsewhere, so only gamma nodes contribute. Output r[ri][b] (real for basis densities).
-template <bool CIN>
-__global__ void __launch_bounds__(256) k_residual(Batch bt, const SubDesc *subs, const double *tab, double *ws,
-                                                  const double2 *xi_user) {
-  Item it; int local;
-  locate(bt, blockIdx.x, it, local);
-  const SubDesc &d = subs[it.sub];
-  const int cb = (it.ncols + 31) >> 5;
-  const int b = (local % cb) * 32 + threadIdx.x;
-  const int ri = (local / cb) * 8 + threadIdx.y;
-  if (b >= it.ncols || ri >= d.R) return;
-  int n, m;
-  ring_node(d, ri, n, m);
-  cplx acc = cmk(0.0, 0.0);
-#pragma unroll
-  for (int dn = -1; dn <= 1; ++dn) {
-#pragma unroll
-    for (int dm = -1; dm <= 1; ++dm) {
-      const int g = gamma_index(d, n + dn, m + dm);
-      if (g < 0) continue;
-      const int nb = (dn != 0) + (dm != 0);
-      const double c = nb == 0 ? d.c0 : nb == 1 ? d.c1 : d.c2;
-      acc = caxpy(c, density<CIN>(d, it, ws, tab, xi_user, b, g), acc);
-    }
-  }
-  double *r = ws + it.r_off;
-  if (CIN) st2(r + 2 * ((long long)ri * it.ncols + b), acc);
-  else r[(long long)ri * it.ncols + b] = acc.re;
-}
-
-// Gradient pass: r = L w|ring as k_residual, and s = (dL/dk w + L dw/dk)|ring (complex [R][b]),
-// the k-derivative of the ring residual (dw/dk: the extension's own k-dependence, basis only).
-template <bool CIN>
-__global__ void __launch_bounds__(256) k_residual_grad(Batch bt, const SubDesc *subs, const double *tab, double *ws,
-                                                       const double2 *xi_user) {
-  Item it; int local;
-  locate(bt, blockIdx.x, it, local);
-  const SubDesc &d = subs[it.sub];
-  const int cb = (it.ncols + 31) >> 5;
-  const int b = (local % cb) * 32 + threadIdx.x;
-  const int ri = (local / cb) * 8 + threadIdx.y;
-  if (b >= it.ncols || ri >= d.R) return;
-  int n, m;
-  ring_node(d, ri, n, m);
+// r(ring node) = sum over the 3x3 stencil of the gamma neighbours (w = xi on gamma, 0 elsewhere).
+// With GRAD also s = (dL/dk w + L dw/dk)(ring node) (dw/dk: the extension's k-dependence, basis).
+template <bool CIN, bool GRAD>
+__device__ __forceinline__ cplx ring_stencil(const SubDesc &d, const Item &it, const double *ws, const double *tab,
+                                             const double2 *xi_user, int b, int n, int m, cplx *s_out) {
   const int side = col_side(d, it.col0 + b);
   const double *dxi = ws + it.xi_off + (long long)d.G * it.ncols;
   cplx acc = cmk(0.0, 0.0), sacc = cmk(0.0, 0.0);
@@ -128,17 +88,69 @@ __global__ void __launch_bounds__(256) k_residual_grad(Batch bt, const SubDesc *
       if (g < 0) continue;
       const int nb = (dn != 0) + (dm != 0);
       const double c = nb == 0 ? d.c0 : nb == 1 ? d.c1 : d.c2;
-      const double dc = nb == 0 ? d.dc0 : nb == 1 ? d.dc1 : 0.0;
       const cplx v = density<CIN>(d, it, ws, tab, xi_user, b, g);
       acc = caxpy(c, v, acc);
-      sacc = caxpy(dc, v, sacc);
-      if (!CIN && (int)tab[d.geo_off + 4 * g] == side) sacc.re = fma(c, dxi[(long long)g * it.ncols + b], sacc.re);
+      if (GRAD) {
+        const double dc = nb == 0 ? d.dc0 : nb == 1 ? d.dc1 : 0.0;
+        sacc = caxpy(dc, v, sacc);
+        if (!CIN && (int)tab[d.geo_off + 4 * g] == side) sacc.re = fma(c, dxi[(long long)g * it.ncols + b], sacc.re);
+      }
     }
   }
+  if (GRAD) *s_out = sacc;
+  return acc;
+}
+
+// One thread per (ring unit, column). Plain layout: a unit is one ring node, r[ri][b]. Centred
+// subdomains (xsym): a unit is the node pair (m, Nx - m) of a ring row, stored as
+// (r(m) + r(Nx-m), r(m) - r(Nx-m)) -- 4 Ph dense-row units and 2 per middle row -- so that
+// the sine transforms need one product per pair. The gradient's s is stored plain [ri][b].
+template <bool CIN, bool GRAD>
+__global__ void __launch_bounds__(256) k_residual(Batch bt, const SubDesc *subs, const double *tab, double *ws,
+                                                  const double2 *xi_user) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int u = (local / cb) * 8 + threadIdx.y;
+  const int units = d.xsym ? 4 * d.Ph + 2 * (d.Py - 4) : d.R;
+  if (b >= it.ncols || u >= units) return;
   double *r = ws + it.r_off;
-  if (CIN) st2(r + 2 * ((long long)ri * it.ncols + b), acc);
-  else r[(long long)ri * it.ncols + b] = acc.re;
-  st2(ws + it.s_off + 2 * ((long long)ri * it.ncols + b), sacc);
+  double *sb = ws + it.s_off;
+  const long long nc = it.ncols;
+  if (!d.xsym) {
+    int n, m;
+    ring_node(d, u, n, m);
+    cplx sv;
+    const cplx v = ring_stencil<CIN, GRAD>(d, it, ws, tab, xi_user, b, n, m, &sv);
+    if (CIN) st2(r + 2 * (u * nc + b), v); else r[u * nc + b] = v.re;
+    if (GRAD) st2(sb + 2 * (u * nc + b), sv);
+    return;
+  }
+  int n, m1, slot;
+  if (u < 4 * d.Ph) {
+    const int rr = u / d.Ph, k = u % d.Ph;
+    n = rr == 0 ? d.nlo : rr == 1 ? d.nlo + 1 : rr == 2 ? d.nhi - 1 : d.nhi;
+    m1 = d.mlo + k;
+    slot = rr * 2 * d.Ph + 2 * k;
+  } else {
+    const int t = (u - 4 * d.Ph) >> 1, pr = (u - 4 * d.Ph) & 1;
+    n = d.nlo + 2 + t;
+    m1 = d.mlo + pr;
+    slot = 8 * d.Ph + 4 * t + 2 * pr;
+  }
+  const int m2 = d.Nx - m1;
+  cplx s1, s2 = cmk(0.0, 0.0);
+  const cplx v1 = ring_stencil<CIN, GRAD>(d, it, ws, tab, xi_user, b, n, m1, &s1);
+  const cplx v2 = m2 != m1 ? ring_stencil<CIN, GRAD>(d, it, ws, tab, xi_user, b, n, m2, &s2) : cmk(0.0, 0.0);
+  const cplx vp = cadd(v1, v2), vm = csub(v1, v2);
+  if (CIN) { st2(r + 2 * (slot * nc + b), vp); st2(r + 2 * ((slot + 1) * nc + b), vm); }
+  else { r[slot * nc + b] = vp.re; r[(slot + 1) * nc + b] = vm.re; }
+  if (GRAD) {
+    st2(sb + 2 * ((long long)ring_index(d, n, m1) * nc + b), s1);
+    if (m2 != m1) st2(sb + 2 * ((long long)ring_index(d, n, m2) * nc + b), s2);
+  }
 }
 
 // ---------------------------------------------------------------- k_fwd_rows
@@ -159,16 +171,19 @@ __global__ void __launch_bounds__(128) k_fwd_rows(Batch bt, const SubDesc *subs,
   const double *r = ws + it.r_off;
   double *gr = ws + it.gr_off;
   const int q2 = d.Nx - q;
+  const int par = (q & 1) ? 0 : 1;  // xsym: odd modes use r(m) + r(Nx-m), even modes the difference
   for (int rr = 0; rr < 4; ++rr) {
     const int rb = rr == 0 ? 0 : rr == 1 ? P : rr == 2 ? 2 * P + Mr : 3 * P + Mr;
     cplx ao = cmk(0.0, 0.0), ae = cmk(0.0, 0.0);
     int j = (int)(((long long)q * d.mlo) % N2);
-    for (int mm = 0; mm < P; ++mm) {
+    const int cnt = d.xsym ? d.Ph : P;
+    for (int mm = 0; mm < cnt; ++mm) {
       const int m = d.mlo + mm;
       const double sv = S[j];
+      const long long slot = d.xsym ? (long long)rr * 2 * d.Ph + 2 * mm + par : rb + mm;
       cplx v;
-      if (CIN) v = ld2(r + 2 * ((long long)(rb + mm) * it.ncols + b));
-      else v = cmk(r[(long long)(rb + mm) * it.ncols + b], 0.0);
+      if (CIN) v = ld2(r + 2 * (slot * it.ncols + b));
+      else v = cmk(r[slot * it.ncols + b], 0.0);
       if (m & 1) ao = caxpy(sv, v, ao); else ae = caxpy(sv, v, ae);
       j += q;
       if (j >= N2) j -= N2;
@@ -194,6 +209,9 @@ __global__ void __launch_bounds__(128) k_fwd_rows(Batch bt, const SubDesc *subs,
 // nlo-1 .. nhi+1, complex unless neither CF nor CIN (real path).
 // FULL: back substitution down to row 0 and every row stored as y[q-1][i][b] (i = 0..Nt-1),
 // the layout of the gradient pass.
+// Factor rows [rlo, rhi) of a complex AP mode are real to working precision (set by the plan):
+// there the sweeps use real factors, and the forward sweep stays in real arithmetic while the
+// data are still real (real densities, no complex factor row met yet).
 template <bool CF, bool CIN, bool FULL>
 __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const double *tab, const uint8_t *pivtab,
                                          double *ws, int b, int q) {
@@ -202,6 +220,7 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
   const double *S = tab + d.sin_off;
   const double sm0 = S[(q * d.mlo) % N2], sm1 = S[(q * (d.mlo + 1)) % N2];
   const double sm2 = S[(q * (d.mhi - 1)) % N2], sm3 = S[(q * d.mhi) % N2];
+  const int par = (q & 1) ? 0 : 1;
   constexpr int FW = CF ? 8 : 4;
   const double *F = tab + d.fact_off + (long long)(q - 1) * d.Nt * FW;
   const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * d.Nt;
@@ -212,6 +231,12 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
   const int yrows = FULL ? d.Nt : d.NYf, yfirst = FULL ? 0 : d.i0;
   const long long ybase = (long long)(q - 1) * yrows * it.ncols + b;
   const int P = d.Px, nc = it.ncols;
+  int rlo = 0, rhi = d.Nt;  // real factor rows
+  if (CF) {
+    const double *sg = tab + d.seg_off + 2 * (q - 1);
+    rlo = (int)sg[0];
+    rhi = (int)sg[1];
+  }
   auto rhs = [&](int n) -> cplx {
     if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
     int rr = -1;
@@ -219,6 +244,14 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
     if (rr >= 0) {
       const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b;
       return CIN ? ld2(gr + 2 * o) : cmk(gr[o], 0.0);
+    }
+    if (d.xsym) {  // (sum, difference) pairs of columns (mlo, mhi) and (mlo+1, mhi-1)
+      const long long base = 8LL * d.Ph + 4 * (n - d.nlo - 2) + par;
+      if (CIN) {
+        const cplx v0 = ld2(r + 2 * (base * nc + b));
+        return caxpy(sm1, ld2(r + 2 * ((base + 2) * nc + b)), cmk(sm0 * v0.re, sm0 * v0.im));
+      }
+      return cmk(fma(sm1, r[(base + 2) * nc + b], sm0 * r[base * nc + b]), 0.0);
     }
     const long long ri = 2 * P + 4 * (n - d.nlo - 2);
     if (CIN) {
@@ -244,46 +277,79 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
     const long long o = ybase + (long long)(i - yfirst) * ystride;
     return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
   };
-  // forward sweep: cur holds the eliminated value of row i
+  // ---- forward sweep: cur holds the eliminated value of row i
   cplx cur = cmk(0.0, 0.0);
-  for (int i = d.i0; i < d.Nt - 1; ++i) {
-    const cplx g = rhs(i + 1 + d.nfirst);
-    const cplx l = CF ? ld2(F + i * FW) : cmk(F[i * FW], 0.0);
-    cplx yv;
-    if (pv[i]) {
-      yv = g;
-      if constexpr (CF) cur = cfms(cur, l, g);
-      else { cur.re = fma(-l.re, g.re, cur.re); if constexpr (CD) cur.im = fma(-l.re, g.im, cur.im); }
-    } else {
-      yv = cur;
-      if constexpr (CF) cur = cfms(g, l, cur);
-      else { cur.re = fma(-l.re, cur.re, g.re); cur.im = CD ? fma(-l.re, cur.im, g.im) : 0.0; }
+  const int iend = d.Nt - 1;
+  int i = d.i0;
+  if (CF) {  // complex factor rows below the real run
+    const int e = min(max(rlo, d.i0), iend);
+    for (; i < e; ++i) {
+      const cplx g = rhs(i + 1 + d.nfirst);
+      const cplx l = ld2(F + i * FW);
+      cplx yv;
+      if (pv[i]) { yv = g; cur = cfms(cur, l, g); } else { yv = cur; cur = cfms(g, l, cur); }
+      ystore(i, yv);
     }
-    ystore(i, yv);
   }
-  ystore(d.Nt - 1, cur);
-  // back substitution; keep only rows nlo-1 .. nhi+1
-  const int ikeep = d.nhi + 1 - d.nfirst;
-  cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
-  for (int i = d.Nt - 1; i >= (FULL ? 0 : d.i0); --i) {
-    const cplx yi = yload(i);
-    cplx x;
-    if (CF) {
-      const cplx dinv = ld2(F + i * FW + 2), u1 = ld2(F + i * FW + 4);
-      x = cfms(cmul(dinv, yi), u1, x1);
-      if (pv[i]) x = cfms(x, ld2(F + i * FW + 6), x2);
-    } else {
-      const double dinv = F[i * FW + 1], u1 = F[i * FW + 2];
-      x = cmk(fma(-u1, x1.re, dinv * yi.re), CD ? fma(-u1, x1.im, dinv * yi.im) : 0.0);
-      if (pv[i]) {
-        const double u2 = F[i * FW + 3];
-        x.re = fma(-u2, x2.re, x.re);
-        if (CD) x.im = fma(-u2, x2.im, x.im);
+  {
+    const int e = min(max(rhi, i), iend);
+    const bool realdata = !CIN && !(CF && i > d.i0);  // nothing complex has entered cur yet
+    if (realdata) {
+      for (; i < e; ++i) {
+        const double g = rhs(i + 1 + d.nfirst).re;
+        const double l = F[i * FW];
+        double yv;
+        if (pv[i]) { yv = g; cur.re = fma(-l, g, cur.re); } else { yv = cur.re; cur.re = fma(-l, cur.re, g); }
+        ystore(i, cmk(yv, 0.0));
       }
+    } else {
+      for (; i < e; ++i) {
+        const cplx g = rhs(i + 1 + d.nfirst);
+        const double l = F[i * FW];
+        cplx yv;
+        if (pv[i]) { yv = g; cur = caxpy(-l, g, cur); } else { yv = cur; cur = caxpy(-l, cur, g); }
+        ystore(i, yv);
+      }
+    }
+  }
+  if (CF) {  // complex factor rows above the real run
+    for (; i < iend; ++i) {
+      const cplx g = rhs(i + 1 + d.nfirst);
+      const cplx l = ld2(F + i * FW);
+      cplx yv;
+      if (pv[i]) { yv = g; cur = cfms(cur, l, g); } else { yv = cur; cur = cfms(g, l, cur); }
+      ystore(i, yv);
+    }
+  }
+  ystore(iend, cur);
+  // ---- back substitution (keep rows nlo-1 .. nhi+1, or all rows with FULL)
+  const int ikeep = d.nhi + 1 - d.nfirst;
+  const int ilo = FULL ? 0 : d.i0;
+  cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
+  auto back_complex = [&](int i) {
+    const cplx yi = yload(i);
+    const cplx dinv = ld2(F + i * FW + 2), u1 = ld2(F + i * FW + 4);
+    cplx x = cfms(cmul(dinv, yi), u1, x1);
+    if (pv[i]) x = cfms(x, ld2(F + i * FW + 6), x2);
+    if (FULL || i <= ikeep) ystore(i, x);
+    x2 = x1; x1 = x;
+  };
+  auto back_real = [&](int i) {
+    const cplx yi = yload(i);
+    const double dinv = F[i * FW + (CF ? 2 : 1)], u1 = F[i * FW + (CF ? 4 : 2)];
+    cplx x = cmk(fma(-u1, x1.re, dinv * yi.re), CD ? fma(-u1, x1.im, dinv * yi.im) : 0.0);
+    if (pv[i]) {
+      const double u2 = F[i * FW + (CF ? 6 : 3)];
+      x.re = fma(-u2, x2.re, x.re);
+      if (CD) x.im = fma(-u2, x2.im, x.im);
     }
     if (FULL || i <= ikeep) ystore(i, x);
     x2 = x1; x1 = x;
-  }
+  };
+  i = d.Nt - 1;
+  if (CF) for (; i >= max(rhi, ilo); --i) back_complex(i);
+  for (; i >= max(rlo, ilo); --i) back_real(i);
+  if (CF) for (; i >= ilo; --i) back_complex(i);
 }
 
 template <bool CIN, bool FULL>
@@ -309,12 +375,15 @@ __device__ __forceinline__ void write_out(const SubDesc &d, const Item &it, cons
   out[it.io_off + (long long)b * d.G + g] = make_double2(v.re, v.im);
 }
 
-// u(m, n) = (2/Nx) sum_q sin(pi q m/Nx) yhat(q, n) for the 4 full gamma rows
+// u(m, n) = (2/Nx) sum_q sin(pi q m/Nx) yhat(q, n) for the 4 full gamma rows. Centred
+// subdomains: one thread gives u(m) = E + O and u(Nx - m) = E - O from the odd-q (E) and
+// even-q (O) partial sums, since sin(pi q (Nx-m)/Nx) = (-1)^(q+1) sin(pi q m/Nx).
 template <bool CD, bool CIN>
 __device__ __forceinline__ void inv_rows_body(const Item &it, const SubDesc &d, const double *tab, const double *ws,
                                               const double2 *xi_user, double2 *out, int kind, int b, int task) {
-  const int W = d.Px + 2;
-  const int grow = task / W, dm = task % W, m = d.mlo - 1 + dm;
+  const int W = d.Px + 2, Mr = d.Py - 2;
+  const int span = d.xsym ? d.Ph + 1 : W;
+  const int grow = task / span, dm = task % span, m = d.mlo - 1 + dm;
   const int n = grow == 0 ? d.nlo - 1 : grow == 1 ? d.nlo : grow == 2 ? d.nhi : d.nhi + 1;
   const int yrow = n - (d.nlo - 1);
   const double *Si = tab + d.sin_off + 2 * d.Nx;
@@ -322,18 +391,29 @@ __device__ __forceinline__ void inv_rows_body(const Item &it, const SubDesc &d, 
   const double *y = ws + it.y_off;
   const long long qstride = (long long)d.NYf * it.ncols;
   const long long base = (long long)yrow * it.ncols + b;
-  cplx acc = cmk(0.0, 0.0);
-  int j = m % N2;
-  for (int q = 1; q <= d.Nq; ++q) {
+  auto yv = [&](int q) -> cplx {
     const long long o = base + (long long)(q - 1) * qstride;
-    const double sv = Si[j];
-    if (CD) acc = caxpy(sv, ld2(y + 2 * o), acc); else acc.re = fma(sv, y[o], acc.re);
-    j += m;
-    if (j >= N2) j -= N2;
+    return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
+  };
+  cplx e = cmk(0.0, 0.0), o = cmk(0.0, 0.0);
+  int j = m % N2;
+  int q = 1;
+  for (; q + 1 <= d.Nq; q += 2) {  // (odd, even) mode pairs
+    const cplx v1 = yv(q), v2 = yv(q + 1);
+    const double s1 = Si[j];
+    j += m; if (j >= N2) j -= N2;
+    const double s2 = Si[j];
+    j += m; if (j >= N2) j -= N2;
+    if (CD) { e = caxpy(s1, v1, e); o = caxpy(s2, v2, o); }
+    else { e.re = fma(s1, v1.re, e.re); o.re = fma(s2, v2.re, o.re); }
   }
-  const int Mr = d.Py - 2;
-  const int g = grow <= 1 ? grow * W + dm : 2 * W + 4 * Mr + (grow - 2) * W + dm;
-  write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, g, acc);
+  if (q <= d.Nq) {
+    const cplx v1 = yv(q);
+    if (CD) e = caxpy(Si[j], v1, e); else e.re = fma(Si[j], v1.re, e.re);
+  }
+  auto gidx = [&](int mm) { const int k = mm - (d.mlo - 1); return grow <= 1 ? grow * W + k : 2 * W + 4 * Mr + (grow - 2) * W + k; };
+  write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, gidx(m), cadd(e, o));
+  if (d.xsym && d.Nx - m != m) write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, gidx(d.Nx - m), csub(e, o));
 }
 
 template <bool CIN>
@@ -345,27 +425,63 @@ __global__ void __launch_bounds__(256) k_inv_rows(Batch bt, const SubDesc *subs,
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
   const int task = (local / cb) * 8 + threadIdx.y;
-  if (b >= it.ncols || task >= 4 * (d.Px + 2)) return;
+  if (b >= it.ncols || task >= 4 * (d.xsym ? d.Ph + 1 : d.Px + 2)) return;
   if (d.cplx || CIN) inv_rows_body<true, CIN>(it, d, tab, ws, xi_user, out, kind, b, task);
   else inv_rows_body<false, CIN>(it, d, tab, ws, xi_user, out, kind, b, task);
 }
 
-// the 4 gamma columns (mlo-1, mlo, mhi, mhi+1) of the middle rows nlo+1 .. nhi-1
+// the 4 gamma columns (mlo-1, mlo, mhi, mhi+1) of the middle rows nlo+1 .. nhi-1; centred
+// subdomains pair mlo-1 with mhi+1 and mlo with mhi (odd-q / even-q partial sums)
 template <bool CD, bool CIN>
 __device__ __forceinline__ void inv_cols_body(const Item &it, const SubDesc &d, const double *tab, const double *ws,
                                               const double2 *xi_user, double2 *out, int kind, int b, int t) {
   const int yrow = t + 2;  // n = nlo + 1 + t
   const double *Si = tab + d.sin_off + 2 * d.Nx;
   const int N2 = 2 * d.Nx;
-  const int ms[4] = {d.mlo - 1, d.mlo, d.mhi, d.mhi + 1};
-  int j[4] = {ms[0] % N2, ms[1] % N2, ms[2] % N2, ms[3] % N2};
   const double *y = ws + it.y_off;
   const long long qstride = (long long)d.NYf * it.ncols;
   const long long base = (long long)yrow * it.ncols + b;
+  const int W = d.Px + 2;
+  auto yv = [&](int q) -> cplx {
+    const long long o = base + (long long)(q - 1) * qstride;
+    return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
+  };
+  if (d.xsym) {
+    const int m0 = d.mlo - 1, m1 = d.mlo;
+    int j0 = m0 % N2, j1 = m1 % N2;
+    cplx e0 = cmk(0, 0), o0 = cmk(0, 0), e1 = cmk(0, 0), o1 = cmk(0, 0);
+    int q = 1;
+    for (; q + 1 <= d.Nq; q += 2) {
+      const cplx va = yv(q), vb = yv(q + 1);
+      const double a0 = Si[j0], a1 = Si[j1];
+      j0 += m0; if (j0 >= N2) j0 -= N2;
+      j1 += m1; if (j1 >= N2) j1 -= N2;
+      const double b0 = Si[j0], b1 = Si[j1];
+      j0 += m0; if (j0 >= N2) j0 -= N2;
+      j1 += m1; if (j1 >= N2) j1 -= N2;
+      if (CD) { e0 = caxpy(a0, va, e0); e1 = caxpy(a1, va, e1); o0 = caxpy(b0, vb, o0); o1 = caxpy(b1, vb, o1); }
+      else {
+        e0.re = fma(a0, va.re, e0.re); e1.re = fma(a1, va.re, e1.re);
+        o0.re = fma(b0, vb.re, o0.re); o1.re = fma(b1, vb.re, o1.re);
+      }
+    }
+    if (q <= d.Nq) {
+      const cplx va = yv(q);
+      if (CD) { e0 = caxpy(Si[j0], va, e0); e1 = caxpy(Si[j1], va, e1); }
+      else { e0.re = fma(Si[j0], va.re, e0.re); e1.re = fma(Si[j1], va.re, e1.re); }
+    }
+    const int g0 = 2 * W + 4 * t;
+    write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, g0 + 0, cadd(e0, o0));
+    write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, g0 + 1, cadd(e1, o1));
+    write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, g0 + 2, csub(e1, o1));
+    write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, g0 + 3, csub(e0, o0));
+    return;
+  }
+  const int ms[4] = {d.mlo - 1, d.mlo, d.mhi, d.mhi + 1};
+  int j[4] = {ms[0] % N2, ms[1] % N2, ms[2] % N2, ms[3] % N2};
   cplx acc[4] = {cmk(0, 0), cmk(0, 0), cmk(0, 0), cmk(0, 0)};
   for (int q = 1; q <= d.Nq; ++q) {
-    const long long o = base + (long long)(q - 1) * qstride;
-    const cplx v = CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
+    const cplx v = yv(q);
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       const double sv = Si[j[s]];
@@ -374,7 +490,6 @@ __device__ __forceinline__ void inv_cols_body(const Item &it, const SubDesc &d, 
       if (j[s] >= N2) j[s] -= N2;
     }
   }
-  const int W = d.Px + 2;
 #pragma unroll
   for (int s = 0; s < 4; ++s)
     write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, 2 * W + 4 * t + s, acc[s]);
@@ -560,8 +675,8 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
     }                                             \
   } while (0)
   if (basis) MDP_LAUNCH(F_EXT, k_extend<<<grid1(fb[F_EXT].total_blocks), 128, 0, st>>>(fb[F_EXT], ds, tab, ws, 0));
-  if (basis) MDP_LAUNCH(F_RES, k_residual<false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
-  else MDP_LAUNCH(F_RES, k_residual<true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
+  if (basis) MDP_LAUNCH(F_RES, k_residual<false, false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
+  else MDP_LAUNCH(F_RES, k_residual<true, false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
   if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
   else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
   if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
@@ -585,8 +700,8 @@ cudaError_t launch_adjoint(mdp_plan *p, const Batch *fb, int out_kind, const dou
   const dim3 b8(32, 8), b4(32, 4);
   if (grad_k) {  // forward recompute with every mode-space row kept, and the k-derivative sources
     if (basis) MDP_LAUNCH(F_EXT, k_extend<<<grid1(fb[F_EXT].total_blocks), 128, 0, st>>>(fb[F_EXT], ds, tab, ws, 1));
-    if (basis) MDP_LAUNCH(F_RES, k_residual_grad<false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
-    else MDP_LAUNCH(F_RES, k_residual_grad<true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
+    if (basis) MDP_LAUNCH(F_RES, k_residual<false, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
+    else MDP_LAUNCH(F_RES, k_residual<true, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
     if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
     else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
     if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));

@@ -27,6 +27,10 @@ struct SubDesc {
   int n_modes, n_cols;
   int cplx;         // 1: complex factors (Sommerfeld AP), 0: real (Dirichlet AP)
   int ap_bc;
+  int xsym;         // 1: mlo + mhi == Nx (subdomain centred along x): paired ring layout
+  int Ph;           // xsym: pair units per dense ring row, Nx/2 - mlo + 1
+  int R2;           // ring residual slots: R, or 8 Ph + 4 (Py - 4) with xsym
+  int pad1;
   double h, k;
   double x0, x1, y0, y1, ax0, ay0;
   double c0, c1, c2;  // 9-point coefficients: centre, edge, corner (Eq. FD_scheme)
@@ -36,6 +40,7 @@ struct SubDesc {
   long long dT_off;     // doubles: dT_q/dk rows [Nq][Nt][6] (sub, diag, super; complex)
   long long sin_off;    // doubles: sin(pi j / Nx), j = 0 .. 2Nx-1, then (2/Nx) sin(pi j/Nx)
   long long geo_off;    // doubles: gamma geometry [G][4] = (owner, s, rho, side length)
+  long long seg_off;    // doubles: per mode [Nq][2] = (rlo, rhi): factor rows rlo..rhi-1 are real
   long long out_off;    // complex elements: start of the subdomain's output block
 };
 
@@ -74,6 +79,7 @@ struct HostSub {
   std::vector<double> fact;      // [Nq][Nt][FW]
   std::vector<uint8_t> piv;      // [Nq][Nt]
   std::vector<double> dT;        // [Nq][Nt][6]
+  std::vector<int> seg;          // [Nq][2]: real factor rows [rlo, rhi)
 };
 
 struct Wave {
@@ -123,10 +129,10 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
   const int cb = (ncols + 31) / 32;
   switch (f) {
     case F_EXT: return (d.G + 127) / 128;
-    case F_RES: return cb * ((d.R + 7) / 8);
+    case F_RES: return cb * (((d.xsym ? 4 * d.Ph + 2 * (d.Py - 4) : d.R) + 7) / 8);
     case F_FROWS: return cb * ((d.Nx / 2 + 3) / 4);
     case F_TRI: return cb * ((d.Nq + 3) / 4);
-    case F_IROWS: return cb * ((4 * (d.Px + 2) + 7) / 8);
+    case F_IROWS: return cb * (((d.xsym ? 4 * (d.Ph + 1) : 4 * (d.Px + 2)) + 7) / 8);
     case F_ICOLS: return cb * ((d.Py - 2 + 7) / 8);
     case F_AFWD: return cb * ((d.Nx / 2 + 3) / 4);
     case F_ATRI: return cb * ((d.Nq + 3) / 4);

@@ -29,7 +29,7 @@ void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long 
   auto al = [](long long v) { return (v + 31) & ~31LL; };  // 256-byte alignment (in doubles)
   long long off = 0;
   xi = off; off += al((long long)d.G * ncols * (grad ? 2 : 1));
-  r = off;  off += al((long long)d.R * ncols * 2);
+  r = off;  off += al((long long)std::max(d.R, d.R2) * ncols * 2);
   gr = off; off += al(4LL * d.Nq * ncols * 2);
   y = off;  off += al((long long)d.Nq * (grad ? d.Nt : d.NYf) * ncols * 2);
   a = off;  off += grad ? al((long long)d.Nq * d.Nt * ncols * 2) : 0;
@@ -70,6 +70,10 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   if (mlo < 2 || mhi > in.nx - 3 || nlo < 2 || nhi > in.ny - 3 || d.Px < 5 || d.Py < 5) return MDP_ERR_ARG;
   d.G = 4 * (d.Px + d.Py);
   d.R = 4 * d.Px + 4 * (d.Py - 4);
+  // centred along x: the ring pairs m with Nx - m (sin(pi q (Nx-m)/Nx) = (-1)^(q+1) sin(pi q m/Nx))
+  d.xsym = (mlo + mhi == d.Nx) && (d.Nx % 2 == 0);
+  d.Ph = d.xsym ? d.Nx / 2 - mlo + 1 : 0;
+  d.R2 = d.xsym ? 8 * d.Ph + 4 * (d.Py - 4) : d.R;  // (sum, difference) per pair unit
   d.nfirst = d.cplx ? 0 : 1;
   d.Nt = d.cplx ? in.ny : in.ny - 2;
   d.i0 = (nlo - 1) - d.nfirst;
@@ -123,6 +127,7 @@ static mdp_status factor_modes(HostSub &hs) {
   hs.fact.assign((size_t)d.Nq * N * FW, 0.0);
   hs.piv.assign((size_t)d.Nq * N, 0);
   hs.dT.assign((size_t)d.Nq * N * 6, 0.0);
+  hs.seg.assign((size_t)d.Nq * 2, 0);
   const double h = d.h, h2 = h * h, k = d.k, k2 = k * k;
   std::vector<cd> dl(N), dg(N), du(N), du2(N);
   for (int q = 1; q <= d.Nq; ++q) {
@@ -173,12 +178,18 @@ static mdp_status factor_modes(HostSub &hs) {
       }
     }
     double *F = &hs.fact[(size_t)(q - 1) * N * FW];
+    std::vector<uint8_t> isreal(N, 1);
     for (int i = 0; i < N; ++i) {
       if (std::abs(dg[i]) < kSingularTol * scale) return MDP_ERR_SINGULAR;
       const cd dinv = 1.0 / dg[i];
       const cd l = i < N - 1 ? dl[i] : cd(0.0);
       const cd u1 = i < N - 1 ? du[i] * dinv : cd(0.0);
       const cd u2 = i < N - 2 ? du2[i] * dinv : cd(0.0);
+      // a factor entry whose imaginary part is below 2^-60 of its modulus is real to working
+      // precision (the LU of an evanescent mode converges to real values away from the
+      // Sommerfeld rows); such rows are stored exactly real and swept with real factors
+      auto tiny = [](cd v) { return std::fabs(v.imag()) <= 0x1p-60 * std::abs(v); };
+      isreal[i] = tiny(l) && tiny(dinv) && tiny(u1) && tiny(u2);
       if (FW == 8) {
         F[i * 8 + 0] = l.real();    F[i * 8 + 1] = l.imag();
         F[i * 8 + 2] = dinv.real(); F[i * 8 + 3] = dinv.imag();
@@ -188,6 +199,18 @@ static mdp_status factor_modes(HostSub &hs) {
         F[i * 4 + 0] = l.real(); F[i * 4 + 1] = dinv.real(); F[i * 4 + 2] = u1.real(); F[i * 4 + 3] = u2.real();
       }
     }
+    // the longest run of real rows containing the middle row: [rlo, rhi)
+    int rlo = N / 2, rhi = N / 2;
+    if (FW == 8 && isreal[N / 2]) {
+      rlo = N / 2; rhi = N / 2 + 1;
+      while (rlo > 0 && isreal[rlo - 1]) --rlo;
+      while (rhi < N && isreal[rhi]) ++rhi;
+      for (int i = rlo; i < rhi; ++i)
+        for (int w = 0; w < 4; ++w) F[i * 8 + 2 * w + 1] = 0.0;
+    }
+    if (FW == 4) { rlo = 0; rhi = N; }
+    hs.seg[(size_t)(q - 1) * 2 + 0] = rlo;
+    hs.seg[(size_t)(q - 1) * 2 + 1] = rhi;
   }
   return MDP_OK;
 }
@@ -242,6 +265,7 @@ static void layout_tables(mdp_plan *p) {
     d.dT_off = off;   off += al((long long)d.Nq * d.Nt * 6);
     d.sin_off = off;  off += al(4LL * d.Nx);
     d.geo_off = off;  off += al(4LL * d.G);
+    d.seg_off = off;  off += al(2LL * d.Nq);
     d.piv_off = poff; poff += al((long long)d.Nq * d.Nt);
     d.out_off = out;  out += (long long)d.G * d.n_cols;
   }
@@ -261,6 +285,7 @@ static void fill_tables(mdp_plan *p) {
       S[j] = std::sin(M_PI * (double)j / (double)d.Nx);
       S[2 * d.Nx + j] = (2.0 / d.Nx) * S[j];
     }
+    for (int i = 0; i < 2 * d.Nq; ++i) p->host_tables[d.seg_off + i] = hs.seg[i];
     double *g = &p->host_tables[d.geo_off];
     for (int i = 0; i < d.G; ++i) {
       g[4 * i + 0] = hs.owner[i];
