@@ -204,7 +204,9 @@ def run_ours(args, wl):
     dev = torch.device("cuda", local)
 
     subs = list(wl.subdomains)
-    plan = mdp.Plan(subs)
+    from paper_2103_12172_gb300.autotune import tune_tile
+    tile = tune_tile(subs)                     # untimed: columns per work item for this GPU and shape
+    plan = mdp.Plan(subs, tile_cols=tile)
     n_cols = sum(8 * s.n_modes for s in subs)
     out = torch.empty(plan.output_size, dtype=torch.complex128, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -279,6 +281,35 @@ def run_ours(args, wl):
            "d2h_bytes_per_step": int(plan.output_size * 16),
            "what": "update_k (host LU of every mode + table upload) + project + D2H of all columns"}
 
+    # the same step replayed as one CUDA graph (library graph mode)
+    gplan = mdp.Plan(subs, tile_cols=tile, graph=True)
+    gs = torch.cuda.Stream()
+    with torch.cuda.stream(gs):
+        for _ in range(2):
+            gplan.project(out=out)
+        ge0, ge1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ge0.record(gs)
+        for _ in range(args.steps):
+            gplan.project(out=out)
+        ge1.record(gs)
+    gs.synchronize()
+    graph_ms = ge0.elapsed_time(ge1) / args.steps
+    gplan.close()
+
+    # adjoint: dLoss/dk for every subdomain through mdp_ap_adjoint (forward recompute + G^H)
+    cot = out.clone()
+    gk = torch.zeros(len(subs), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        plan.adjoint(cot, grad_xi=False, grad_k=gk)
+    ae0, ae1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ae0.record(stream)
+    for _ in range(args.steps):
+        plan.adjoint(cot, grad_xi=False, grad_k=gk)
+    ae1.record(stream)
+    torch.cuda.synchronize()
+    adj_ms = ae0.elapsed_time(ae1) / args.steps
+
     # per-RHS comparator: the same kernels one column per launch sequence, no batching
     per_rhs_cols = min(64, n_cols)
     one = torch.empty(plan.layout(0)[0], dtype=torch.complex128, device=dev)
@@ -298,6 +329,7 @@ def run_ours(args, wl):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "description": wl.description, "columns_per_step": n_cols,
+                   "tile_cols": tile,
                    "l2": "flushed between timed steps (512 MiB write, untimed)", "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
@@ -306,6 +338,8 @@ def run_ours(args, wl):
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items())},
         "gpu_launches": gpu_launches,
         "per_rhs": {"value": per_rhs, "unit": UNIT, "speedup_batched": value / world / per_rhs},
+        "graph": {"ms_per_step": graph_ms, "launches_per_step": 1, "tile_cols": tile},
+        "adjoint_grad_k": {"value": n_cols / (adj_ms / 1e3), "unit": UNIT, "ms_per_step": adj_ms},
         "e2e": e2e,
         "wall_s_timed": wall,
     }

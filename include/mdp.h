@@ -55,6 +55,14 @@ enum { MDP_OUT_Q = 0, MDP_OUT_P = 1 };
 
 /* Plan flags */
 #define MDP_PLAN_HOST_ONLY 0x1u   /* build host tables only; no CUDA call is made */
+#define MDP_PLAN_GRAPH 0x2u       /* mdp_project_batch replays a CUDA graph of its launches */
+
+/* Plan options (0 selects the default: environment MDP_TILE_COLS / MDP_WS_MB, else 256 columns
+ * per work item and a 4 GiB workspace budget). */
+typedef struct {
+  int tile_cols;              /* columns per work item (the batching tile) */
+  long long workspace_bytes;  /* budget that packs work items into waves */
+} mdp_plan_options;
 
 /* One subdomain Omega_i = (x0, x1) x (y0, y1) and its auxiliary problem
  * (Section 3.2.1: AP on the enclosing rectangle; Section 3.2.4: M* basis functions per side). */
@@ -80,6 +88,14 @@ typedef struct mdp_plan mdp_plan;
  * released with mdp_plan_destroy. With MDP_PLAN_HOST_ONLY the plan holds host tables only
  * (layout and introspection calls work; compute calls return MDP_ERR_STATE). */
 mdp_status mdp_ap_plan(const mdp_subdomain *subs, int n_subs, unsigned flags, mdp_plan **out);
+
+/* mdp_ap_plan with explicit batching options (opt may be NULL). With MDP_PLAN_GRAPH, the first
+ * mdp_project_batch call for a given (xi, out, out_kind, stream) captures all its launches into
+ * a CUDA graph (stream capture), later calls with the same arguments launch that graph: one
+ * launch per call. Calls on the legacy default stream (NULL) are never captured; a plan keeps
+ * up to 8 graphs. Per-kernel profiling (mdp_plan_profile) sees no launches in graph mode. */
+mdp_status mdp_ap_plan_ex(const mdp_subdomain *subs, int n_subs, unsigned flags, const mdp_plan_options *opt,
+                          mdp_plan **out);
 
 /* Replace the wavenumbers (k[n_subs], host array) and refactor in place: same grids, no
  * reallocation. Synchronises the device. */

@@ -18,7 +18,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import MdpError, MDP_OUT_P, MDP_OUT_Q, MDP_PLAN_HOST_ONLY
+from ._lib import MdpError, MDP_OUT_P, MDP_OUT_Q, MDP_PLAN_GRAPH, MDP_PLAN_HOST_ONLY
 
 __all__ = ["Plan", "MdpError", "probe_fp64_gflops", "as_c_subdomains", "solve_noalloc"]
 
@@ -48,13 +48,16 @@ def _ptr(t):
 class Plan:
     """A plan over a list of subdomains (objects with the mdp_subdomain fields)."""
 
-    def __init__(self, subdomains, host_only: bool = False):
+    def __init__(self, subdomains, host_only: bool = False, graph: bool = False, tile_cols: int = 0,
+                 workspace_bytes: int = 0):
         self.L = _lib.lib()
         self.subdomains = list(subdomains)
         self._c_subs = as_c_subdomains(self.subdomains)
         handle = C.c_void_p()
-        flags = MDP_PLAN_HOST_ONLY if host_only else 0
-        _lib.check(self.L.mdp_ap_plan(self._c_subs, len(self.subdomains), flags, C.byref(handle)), "mdp_ap_plan")
+        flags = (MDP_PLAN_HOST_ONLY if host_only else 0) | (MDP_PLAN_GRAPH if graph else 0)
+        opts = _lib.mdp_plan_options(int(tile_cols), int(workspace_bytes))
+        _lib.check(self.L.mdp_ap_plan_ex(self._c_subs, len(self.subdomains), flags, C.byref(opts), C.byref(handle)),
+                   "mdp_ap_plan")
         self.handle = handle
         self.host_only = host_only
         self.n_subs = len(self.subdomains)

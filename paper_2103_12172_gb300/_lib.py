@@ -11,6 +11,7 @@ MDP_OK, MDP_ERR_ARG, MDP_ERR_CUDA, MDP_ERR_NOMEM, MDP_ERR_SINGULAR, MDP_ERR_TIME
 MDP_AP_DIRICHLET4, MDP_AP_DIRX_SOMMY = 0, 1
 MDP_OUT_Q, MDP_OUT_P = 0, 1
 MDP_PLAN_HOST_ONLY = 0x1
+MDP_PLAN_GRAPH = 0x2
 
 EXPORTED = [
     "mdp_ap_plan", "mdp_plan_update_k", "mdp_plan_layout", "mdp_plan_output_size", "mdp_project_batch",
@@ -23,6 +24,10 @@ class mdp_subdomain(C.Structure):
     _fields_ = [("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double), ("y1", C.c_double),
                 ("ax0", C.c_double), ("ay0", C.c_double), ("h", C.c_double),
                 ("nx", C.c_int), ("ny", C.c_int), ("k", C.c_double), ("ap_bc", C.c_int), ("n_modes", C.c_int)]
+
+
+class mdp_plan_options(C.Structure):
+    _fields_ = [("tile_cols", C.c_int), ("workspace_bytes", C.c_longlong)]
 
 
 class MdpError(RuntimeError):
@@ -46,6 +51,7 @@ def lib():
     vp, i, ll, d = C.c_void_p, C.c_int, C.c_longlong, C.c_double
     sig = {
         "mdp_ap_plan": (i, [C.POINTER(mdp_subdomain), i, C.c_uint, C.POINTER(vp)]),
+        "mdp_ap_plan_ex": (i, [C.POINTER(mdp_subdomain), i, C.c_uint, C.POINTER(mdp_plan_options), C.POINTER(vp)]),
         "mdp_plan_update_k": (i, [vp, C.POINTER(d)]),
         "mdp_plan_layout": (i, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(ll), C.POINTER(C.POINTER(i))]),
         "mdp_plan_output_size": (ll, [vp]),

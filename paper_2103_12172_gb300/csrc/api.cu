@@ -166,7 +166,13 @@ const char *mdp_status_string(mdp_status s) {
 }
 
 mdp_status mdp_ap_plan(const mdp_subdomain *subs, int n_subs, unsigned flags, mdp_plan **out) {
+  return mdp_ap_plan_ex(subs, n_subs, flags, nullptr, out);
+}
+
+mdp_status mdp_ap_plan_ex(const mdp_subdomain *subs, int n_subs, unsigned flags, const mdp_plan_options *opt,
+                          mdp_plan **out) {
   if (!subs || n_subs < 1 || !out) return MDP_ERR_ARG;
+  if (opt && (opt->tile_cols < 0 || opt->workspace_bytes < 0)) return MDP_ERR_ARG;
   *out = nullptr;
   mdp_plan *p = new (std::nothrow) mdp_plan();
   if (!p) return MDP_ERR_NOMEM;
@@ -174,6 +180,8 @@ mdp_status mdp_ap_plan(const mdp_subdomain *subs, int n_subs, unsigned flags, md
   p->n_subs = n_subs;
   p->tile_cols = (int)std::max(1LL, env_ll("MDP_TILE_COLS", 256));
   p->ws_budget = env_ll("MDP_WS_MB", 4096) << 20;
+  if (opt && opt->tile_cols > 0) p->tile_cols = opt->tile_cols;
+  if (opt && opt->workspace_bytes > 0) p->ws_budget = opt->workspace_bytes;
   mdp_status st;
   try {
     st = build_host_plan(p, subs, n_subs);
@@ -221,11 +229,46 @@ mdp_status mdp_project_batch(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, int o
   if (xi && (const void *)xi == (const void *)out) return MDP_ERR_ARG;
   CK(cudaSetDevice(p->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  for (size_t w = 0; w < p->waves.size(); ++w) {
-    Batch fb[NFAM];
-    wave_batches(p, w, fb);
-    CK(launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, st));
+  auto launch_all = [&]() -> cudaError_t {
+    for (size_t w = 0; w < p->waves.size(); ++w) {
+      Batch fb[NFAM];
+      wave_batches(p, w, fb);
+      cudaError_t e = launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  if (!(p->flags & MDP_PLAN_GRAPH) || st == nullptr) {
+    CK(launch_all());
+    return MDP_OK;
   }
+  for (auto &g : p->graphs)
+    if (g.xi == (const void *)xi && g.out == (void *)out && g.kind == out_kind && g.st == st) {
+      CK(cudaGraphLaunch(g.exec, st));
+      return MDP_OK;
+    }
+  // capture every launch of this call into one graph
+  const bool prof = p->prof_on;
+  p->prof_on = false;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = launch_all();
+  cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  p->prof_on = prof;
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return MDP_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) return MDP_ERR_CUDA;
+  if (p->graphs.size() >= 8) {
+    cudaGraphExecDestroy(p->graphs.front().exec);
+    p->graphs.erase(p->graphs.begin());
+  }
+  p->graphs.push_back({(const void *)xi, (void *)out, out_kind, st, exec});
+  CK(cudaGraphLaunch(exec, st));
   return MDP_OK;
 }
 
@@ -293,7 +336,12 @@ mdp_status mdp_plan_status(mdp_plan *p) {
 
 void mdp_plan_destroy(mdp_plan *p) {
   if (!p) return;
-  if (device_ok(p)) { destroy_prof(p); free_device(p); }
+  if (device_ok(p)) {
+    for (auto &g : p->graphs) cudaGraphExecDestroy(g.exec);
+    p->graphs.clear();
+    destroy_prof(p);
+    free_device(p);
+  }
   delete p;
 }
 

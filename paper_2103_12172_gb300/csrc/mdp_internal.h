@@ -112,6 +112,9 @@ struct mdp_plan {
   std::vector<mdp::Item *> d_wave_items, d_gwave_items;
   std::vector<int *> d_wave_prefix, d_gwave_prefix;  // [wave] -> device int [NFAM][n_items + 1]
   std::vector<std::vector<int>> h_wave_prefix, h_gwave_prefix;
+  // CUDA graphs of mdp_project_batch, keyed by (xi, out, kind, stream)
+  struct GraphEntry { const void *xi; void *out; int kind; cudaStream_t st; cudaGraphExec_t exec; };
+  std::vector<GraphEntry> graphs;
   // per-kernel event timing (mdp_plan_profile)
   bool prof_on = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[16];
