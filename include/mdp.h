@@ -167,6 +167,30 @@ mdp_status mdp_ap_solve_noalloc(const mdp_subdomain *sub, int nrhs, const mdp_c6
                                 int adjoint, void *cuda_stream);
 long long mdp_ap_solve_noalloc_limit_bytes(void);
 
+/* Receiver rows (for reconstruction of the solution inside subdomains, Section 3.2.2, Eq.
+ * potential_solution_homo: u = P_N+ xi_gamma). rows[i] is the AP grid row n of subdomain i,
+ * nlo+1 <= n <= nhi-1 (strictly inside the gamma ring), or -1 for none (host array of n_subs).
+ * The receivers of subdomain i are the nodes (n, m), m = mlo+1 .. mhi-1 (not on gamma, where
+ * w = 0, so P_N+ xi = -G^(h) L^(h) w there). Uploads a small descriptor array; allocates nothing
+ * and synchronises the device. */
+mdp_status mdp_plan_set_receivers(mdp_plan *p, const int *rows);
+
+/* Receiver layout of subdomain `sub` (host): grid row (or -1), first node m, number of nodes
+ * per column, and the element offset of its block [8M*][count] in the receiver output. */
+mdp_status mdp_plan_receiver_layout(const mdp_plan *p, int sub, int *row, int *m_first, int *count,
+                                    long long *offset);
+long long mdp_plan_receiver_size(const mdp_plan *p);
+
+/* mdp_project_batch that also writes the difference potential P_N+ xi_c at the receivers into
+ * out_rec (device, mdp_plan_receiver_size complex elements; NULL = none). */
+mdp_status mdp_project_batch_rec(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, mdp_c64 *out_rec,
+                                 int out_kind, void *cuda_stream);
+
+/* mdp_ap_adjoint with an additional cotangent on the receiver output (cot_rec, layout of
+ * out_rec; NULL = none): grad_xi and grad_k then include the receivers' contribution. */
+mdp_status mdp_ap_adjoint_rec(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, const mdp_c64 *cot_rec,
+                              mdp_c64 *grad_xi, double *grad_k, int out_kind, void *cuda_stream);
+
 /* Synchronise the plan's device, return and clear the sticky device status word. */
 mdp_status mdp_plan_status(mdp_plan *p);
 

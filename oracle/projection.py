@@ -101,6 +101,21 @@ class APSystem:
         cols = range(8 * self.sub.n_modes) if cols is None else cols
         return np.stack([self.apply(self.basis_density(c), kind) for c in cols])
 
+    def mplus_range(self):
+        """(mlo, mhi, nlo, nhi): the node rectangle of M+."""
+        cols = np.nonzero(self.gs.Mp.any(axis=0))[0]
+        rows = np.nonzero(self.gs.Mp.any(axis=1))[0]
+        return cols[0], cols[-1], rows[0], rows[-1]
+
+    def receivers(self, row, cols=None, xi=None):
+        """Difference potential P_N+ xi (Eq. Potential_def) at the nodes (row, m), m = mlo+1 ..
+        mhi-1, for the basis columns (xi None) or given densities: array [n_cols, Px - 2]."""
+        mlo, mhi, _, _ = self.mplus_range()
+        if xi is None:
+            cols = range(8 * self.sub.n_modes) if cols is None else cols
+            xi = [self.basis_density(c) for c in cols]
+        return np.stack([self.potential(x)[row, mlo + 1:mhi] for x in xi])
+
     def pgamma_matrix(self):
         """Dense P_gamma (|gamma| x |gamma|), one solve per unit density."""
         n = self.n_gamma
@@ -112,8 +127,10 @@ class APSystem:
             P[:, i] = self.apply(e, "P")
         return P
 
-    def adjoint(self, cot, kind="Q", xi=None, cols=None):
-        """(grad_xi, dLoss/dk) for out = columns(cols, kind, xi) and cotangent cot[n_cols, |gamma|]."""
+    def adjoint(self, cot, kind="Q", xi=None, cols=None, cot_rec=None, rec_row=None):
+        """(grad_xi, dLoss/dk) for out = columns(cols, kind, xi) and cotangent cot[n_cols, |gamma|];
+        with cot_rec[n_cols, Px - 2] also the receiver output receivers(rec_row, ...), which is
+        -R_rec G^(h) L^(h) w as well (w = 0 at the receivers), so its cotangent joins Tr^T cot."""
         gs = self.gs
         h, k = self.sub.h, self.k
         dA = assemble(self.sub, k, deriv=True)[0]
@@ -130,6 +147,9 @@ class APSystem:
             c = cot[b]
             y = np.zeros(self.U.shape, dtype=complex)
             y[gs.gamma_n, gs.gamma_m] = c              # Tr^T c
+            if cot_rec is not None:
+                mlo, mhi, _, _ = self.mplus_range()
+                y[rec_row, mlo + 1:mhi] += cot_rec[b]    # R_rec^T c_rec
             mu = self.solve_adjoint(y)                   # A^{-H} Tr^T c (on unknown nodes)
             v = np.where(gs.Mp, mu, 0.0)                 # R^T E^T mu
             g = -apply_L(v, h, k)[gs.gamma_n, gs.gamma_m]  # -W^T L^T R^T E^T mu (L symmetric, real)

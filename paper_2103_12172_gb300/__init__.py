@@ -115,8 +115,10 @@ class Plan:
         if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.numel() < n:
             raise ValueError(f"{name} must be a contiguous complex128 CUDA tensor with >= {n} elements")
 
-    def project(self, xi=None, kind: str = "Q", out=None, stream=None):
-        """Projection columns of all subdomains as a flat complex128 CUDA tensor."""
+    def project(self, xi=None, kind: str = "Q", out=None, stream=None, out_rec=None):
+        """Projection columns of all subdomains as a flat complex128 CUDA tensor. With
+        out_rec (a tensor, or True to allocate one) also the receiver values; returns
+        (out, out_rec) then."""
         import torch
         n = self.output_size
         if out is None:
@@ -124,9 +126,29 @@ class Plan:
         self._check_dev(out, n, "out")
         if xi is not None:
             self._check_dev(xi, n, "xi")
-        _lib.check(self.L.mdp_project_batch(self.handle, _ptr(xi), _ptr(out), _KINDS[kind], _stream_ptr(stream)),
-                   "mdp_project_batch")
-        return out
+        if out_rec is True:
+            out_rec = torch.empty(max(self.receiver_size, 1), dtype=torch.complex128, device="cuda")
+        if out_rec is not None:
+            self._check_dev(out_rec, self.receiver_size, "out_rec")
+        _lib.check(self.L.mdp_project_batch_rec(self.handle, _ptr(xi), _ptr(out), _ptr(out_rec), _KINDS[kind],
+                                                _stream_ptr(stream)), "mdp_project_batch")
+        return out if out_rec is None else (out, out_rec)
+
+    def set_receivers(self, rows):
+        """Receiver grid row per subdomain (-1: none); see mdp_plan_set_receivers."""
+        arr = (C.c_int * self.n_subs)(*[int(r) for r in rows])
+        _lib.check(self.L.mdp_plan_set_receivers(self.handle, arr), "mdp_plan_set_receivers")
+
+    @property
+    def receiver_size(self):
+        return int(self.L.mdp_plan_receiver_size(self.handle))
+
+    def receiver_layout(self, sub):
+        """(row, first m, count, offset) of subdomain `sub`'s receiver block."""
+        r, m0, cnt, off = C.c_int(), C.c_int(), C.c_int(), C.c_longlong()
+        _lib.check(self.L.mdp_plan_receiver_layout(self.handle, sub, C.byref(r), C.byref(m0), C.byref(cnt),
+                                                   C.byref(off)), "mdp_plan_receiver_layout")
+        return r.value, m0.value, cnt.value, off.value
 
     def project_columns(self, sub: int, col0: int, ncols: int, xi=None, kind: str = "Q", out=None, stream=None):
         import torch
@@ -140,18 +162,21 @@ class Plan:
                                               _stream_ptr(stream)), "mdp_project_columns")
         return out
 
-    def adjoint(self, cot, xi=None, kind: str = "Q", grad_xi=True, grad_k=None, stream=None):
-        """(grad_xi or None, grad_k) of a real loss with cotangent `cot` (layout of project())."""
+    def adjoint(self, cot, xi=None, kind: str = "Q", grad_xi=True, grad_k=None, stream=None, cot_rec=None):
+        """(grad_xi or None, grad_k) of a real loss with cotangent `cot` (layout of project())
+        and optionally `cot_rec` on the receiver output."""
         import torch
         n = self.output_size
         self._check_dev(cot, n, "cot")
+        if cot_rec is not None:
+            self._check_dev(cot_rec, self.receiver_size, "cot_rec")
         gx = torch.empty(n, dtype=torch.complex128, device="cuda") if grad_xi else None
         if grad_k is None:
             grad_k = torch.zeros(self.n_subs, dtype=torch.float64, device="cuda")
         elif grad_k is False:
             grad_k = None
-        _lib.check(self.L.mdp_ap_adjoint(self.handle, _ptr(xi), _ptr(cot), _ptr(gx), _ptr(grad_k), _KINDS[kind],
-                                         _stream_ptr(stream)), "mdp_ap_adjoint")
+        _lib.check(self.L.mdp_ap_adjoint_rec(self.handle, _ptr(xi), _ptr(cot), _ptr(cot_rec), _ptr(gx), _ptr(grad_k),
+                                             _KINDS[kind], _stream_ptr(stream)), "mdp_ap_adjoint")
         return gx, grad_k
 
     def solve(self, sub: int, g, adjoint: bool = False, out=None, stream=None):

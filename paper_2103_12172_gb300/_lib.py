@@ -72,6 +72,11 @@ def lib():
         "mdp_plan_sub_info": (i, [vp, i, C.POINTER(i)]),
         "mdp_ap_solve_noalloc": (i, [C.POINTER(mdp_subdomain), i, vp, vp, i, vp]),
         "mdp_ap_solve_noalloc_limit_bytes": (ll, []),
+        "mdp_plan_set_receivers": (i, [vp, C.POINTER(i)]),
+        "mdp_plan_receiver_layout": (i, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(ll)]),
+        "mdp_plan_receiver_size": (ll, [vp]),
+        "mdp_project_batch_rec": (i, [vp, vp, vp, vp, i, vp]),
+        "mdp_ap_adjoint_rec": (i, [vp, vp, vp, vp, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -224,6 +224,11 @@ mdp_status mdp_plan_layout(const mdp_plan *p, int sub, int *gamma_size, int *n_c
 long long mdp_plan_output_size(const mdp_plan *p) { return p ? p->out_size : 0; }
 
 mdp_status mdp_project_batch(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, int out_kind, void *cuda_stream) {
+  return mdp_project_batch_rec(p, xi, out, nullptr, out_kind, cuda_stream);
+}
+
+mdp_status mdp_project_batch_rec(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, mdp_c64 *out_rec, int out_kind,
+                                 void *cuda_stream) {
   if (!p || !out || (out_kind != MDP_OUT_Q && out_kind != MDP_OUT_P)) return MDP_ERR_ARG;
   if (!device_ok(p)) return MDP_ERR_STATE;
   if (xi && (const void *)xi == (const void *)out) return MDP_ERR_ARG;
@@ -233,7 +238,7 @@ mdp_status mdp_project_batch(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, int o
     for (size_t w = 0; w < p->waves.size(); ++w) {
       Batch fb[NFAM];
       wave_batches(p, w, fb);
-      cudaError_t e = launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, st);
+      cudaError_t e = launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, (double2 *)out_rec, st);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -243,7 +248,8 @@ mdp_status mdp_project_batch(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, int o
     return MDP_OK;
   }
   for (auto &g : p->graphs)
-    if (g.xi == (const void *)xi && g.out == (void *)out && g.kind == out_kind && g.st == st) {
+    if (g.xi == (const void *)xi && g.out == (void *)out && g.out_rec == (void *)out_rec && g.kind == out_kind &&
+        g.st == st) {
       CK(cudaGraphLaunch(g.exec, st));
       return MDP_OK;
     }
@@ -267,7 +273,7 @@ mdp_status mdp_project_batch(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, int o
     cudaGraphExecDestroy(p->graphs.front().exec);
     p->graphs.erase(p->graphs.begin());
   }
-  p->graphs.push_back({(const void *)xi, (void *)out, out_kind, st, exec});
+  p->graphs.push_back({(const void *)xi, (void *)out, (void *)out_rec, out_kind, st, exec});
   CK(cudaGraphLaunch(exec, st));
   return MDP_OK;
 }
@@ -290,13 +296,18 @@ mdp_status mdp_project_columns(mdp_plan *p, int sub, int col0, int ncols, const 
     it.io_off = (long long)c * d.G;
     Batch fb[NFAM];
     single_batches(p, it, fb);
-    CK(launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, st));
+    CK(launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, nullptr, st));
   }
   return MDP_OK;
 }
 
 mdp_status mdp_ap_adjoint(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, mdp_c64 *grad_xi, double *grad_k,
                           int out_kind, void *cuda_stream) {
+  return mdp_ap_adjoint_rec(p, xi, cot, nullptr, grad_xi, grad_k, out_kind, cuda_stream);
+}
+
+mdp_status mdp_ap_adjoint_rec(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, const mdp_c64 *cot_rec,
+                              mdp_c64 *grad_xi, double *grad_k, int out_kind, void *cuda_stream) {
   if (!p || !cot || (out_kind != MDP_OUT_Q && out_kind != MDP_OUT_P)) return MDP_ERR_ARG;
   if (!device_ok(p)) return MDP_ERR_STATE;
   if (!grad_xi && !grad_k) return MDP_OK;
@@ -307,7 +318,8 @@ mdp_status mdp_ap_adjoint(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, md
   for (size_t w = 0; w < p->gwaves.size(); ++w) {
     Batch fb[NFAM];
     wave_batches(p, w, fb, true);
-    CK(launch_adjoint(p, fb, out_kind, (const double2 *)xi, (const double2 *)cot, (double2 *)grad_xi, grad_k, st));
+    CK(launch_adjoint(p, fb, out_kind, (const double2 *)xi, (const double2 *)cot, (const double2 *)cot_rec,
+                      (double2 *)grad_xi, grad_k, st));
   }
   return MDP_OK;
 }
@@ -388,6 +400,57 @@ mdp_status mdp_plan_profile_read(mdp_plan *p, int family, double *total_ms, int 
   if (launches) *launches = n;
   return MDP_OK;
 }
+
+mdp_status mdp_plan_set_receivers(mdp_plan *p, const int *rows) {
+  if (!p || !rows) return MDP_ERR_ARG;
+  for (int i = 0; i < p->n_subs; ++i) {
+    const SubDesc &d = p->subs[i].d;
+    if (rows[i] != -1 && (rows[i] < d.nlo + 1 || rows[i] > d.nhi - 1)) return MDP_ERR_ARG;
+  }
+  long long off = 0;
+  for (int i = 0; i < p->n_subs; ++i) {
+    SubDesc &d = p->subs[i].d;
+    d.nrec = rows[i];
+    d.rec_off = off;
+    if (d.nrec >= 0) off += (long long)d.n_cols * (d.Px - 2);
+  }
+  p->rec_size = off;
+  if (!device_ok(p)) return MDP_OK;
+  CK(cudaSetDevice(p->device));
+  CK(cudaDeviceSynchronize());
+  std::vector<SubDesc> ds;
+  for (auto &hs : p->subs) ds.push_back(hs.d);
+  CK(cudaMemcpy(p->d_subs, ds.data(), ds.size() * sizeof(SubDesc), cudaMemcpyHostToDevice));
+  // the receiver kernel's block counts changed: refresh the prefix sums (same sizes)
+  for (int pass = 0; pass < 2; ++pass) {
+    auto &waves = pass ? p->gwaves : p->waves;
+    auto &dpre = pass ? p->d_gwave_prefix : p->d_wave_prefix;
+    auto &hpre = pass ? p->h_gwave_prefix : p->h_wave_prefix;
+    for (size_t w = 0; w < waves.size(); ++w) {
+      const int n = (int)waves[w].items.size();
+      auto &pre = hpre[w];
+      for (int i = 0; i < n; ++i)
+        pre[(size_t)F_IREC * (n + 1) + i + 1] =
+            pre[(size_t)F_IREC * (n + 1) + i] + blocks_for(F_IREC, p->subs[waves[w].items[i].sub].d, waves[w].items[i].ncols);
+      CK(cudaMemcpy(dpre[w], pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+  }
+  for (auto &g : p->graphs) cudaGraphExecDestroy(g.exec);
+  p->graphs.clear();
+  return MDP_OK;
+}
+
+mdp_status mdp_plan_receiver_layout(const mdp_plan *p, int sub, int *row, int *m_first, int *count, long long *offset) {
+  if (!p || sub < 0 || sub >= p->n_subs) return MDP_ERR_ARG;
+  const SubDesc &d = p->subs[sub].d;
+  if (row) *row = d.nrec;
+  if (m_first) *m_first = d.mlo + 1;
+  if (count) *count = d.nrec >= 0 ? d.Px - 2 : 0;
+  if (offset) *offset = d.rec_off;
+  return MDP_OK;
+}
+
+long long mdp_plan_receiver_size(const mdp_plan *p) { return p ? p->rec_size : 0; }
 
 int mdp_kernel_family_count(void) { return NFAM; }
 

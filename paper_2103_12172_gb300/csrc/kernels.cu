@@ -509,6 +509,62 @@ __global__ void __launch_bounds__(256) k_inv_cols(Batch bt, const SubDesc *subs,
   else inv_cols_body<false, CIN>(it, d, tab, ws, xi_user, out, kind, b, t);
 }
 
+// ---------------------------------------------------------------- receivers
+// P_N+ xi at the receiver row nrec, nodes m = mlo+1 .. mhi-1 (not on gamma, so w = 0 there and
+// the difference potential is -G^(h) r): u = -(2/Nx) sum_q sin(pi q m/Nx) yhat(q, nrec).
+// Output out_rec[rec_off + c * (Px - 2) + (m - mlo - 1)]; centred subdomains give m and Nx - m.
+template <bool CD>
+__device__ __forceinline__ void inv_rec_body(const Item &it, const SubDesc &d, const double *tab, const double *ws,
+                                             double2 *out_rec, int b, int task) {
+  const int m = d.mlo + 1 + task;
+  const int yrow = d.nrec - (d.nlo - 1);
+  const double *Si = tab + d.sin_off + 2 * d.Nx;
+  const int N2 = 2 * d.Nx;
+  const double *y = ws + it.y_off;
+  const long long qstride = (long long)d.NYf * it.ncols;
+  const long long base = (long long)yrow * it.ncols + b;
+  auto yv = [&](int q) -> cplx {
+    const long long o = base + (long long)(q - 1) * qstride;
+    return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
+  };
+  cplx e = cmk(0.0, 0.0), o = cmk(0.0, 0.0);
+  int j = m % N2;
+  int q = 1;
+  for (; q + 1 <= d.Nq; q += 2) {
+    const cplx v1 = yv(q), v2 = yv(q + 1);
+    const double s1 = Si[j];
+    j += m; if (j >= N2) j -= N2;
+    const double s2 = Si[j];
+    j += m; if (j >= N2) j -= N2;
+    e = caxpy(s1, v1, e);
+    o = caxpy(s2, v2, o);
+  }
+  if (q <= d.Nq) e = caxpy(Si[j], yv(q), e);
+  const long long col = (long long)(it.col0 + b) * (d.Px - 2);
+  if (d.xsym) {
+    const cplx up = cadd(e, o), um = csub(e, o);
+    out_rec[d.rec_off + col + (m - d.mlo - 1)] = make_double2(-up.re, -up.im);
+    if (d.Nx - m != m) out_rec[d.rec_off + col + (d.Nx - m - d.mlo - 1)] = make_double2(-um.re, -um.im);
+  } else {
+    const cplx u = cadd(e, o);
+    out_rec[d.rec_off + col + (m - d.mlo - 1)] = make_double2(-u.re, -u.im);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_inv_rec(Batch bt, const SubDesc *subs, const double *tab, const double *ws,
+                                                 double2 *out_rec, int cd) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  if (d.nrec < 0) return;
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int task = (local / cb) * 8 + threadIdx.y;
+  if (b >= it.ncols || task >= (d.xsym ? d.Ph - 1 : d.Px - 2)) return;
+  if (d.cplx || cd) inv_rec_body<true>(it, d, tab, ws, out_rec, b, task);
+  else inv_rec_body<false>(it, d, tab, ws, out_rec, b, task);
+}
+
 // ---------------------------------------------------------------- full-grid solves
 // u = G^(h) g or A^{-H} g on the whole grid (test and reconstruction primitive). Mode-space
 // buffer buf[r][q-1][i] (complex), i = matrix row of the y unknowns.
@@ -660,7 +716,7 @@ cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const doub
 static inline dim3 grid1(int n) { return dim3((unsigned)n, 1, 1); }
 
 cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, double2 *out,
-                           cudaStream_t st) {
+                           double2 *out_rec, cudaStream_t st) {
   const bool basis = xi_user == nullptr;
   const SubDesc *ds = p->d_subs;
   const double *tab = p->d_tables;
@@ -688,11 +744,13 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
     MDP_LAUNCH(F_IROWS, k_inv_rows<true><<<grid1(fb[F_IROWS].total_blocks), b8, 0, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
     MDP_LAUNCH(F_ICOLS, k_inv_cols<true><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
   }
+  if (out_rec)
+    MDP_LAUNCH(F_IREC, k_inv_rec<<<grid1(fb[F_IREC].total_blocks), b8, 0, st>>>(fb[F_IREC], ds, tab, ws, out_rec, basis ? 0 : 1));
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, const double2 *cot,
-                           double2 *grad_xi, double *grad_k, cudaStream_t st) {
+                           const double2 *cot_rec, double2 *grad_xi, double *grad_k, cudaStream_t st) {
   const bool basis = xi_user == nullptr;
   const SubDesc *ds = p->d_subs;
   const double *tab = p->d_tables;
@@ -709,7 +767,7 @@ cudaError_t launch_adjoint(mdp_plan *p, const Batch *fb, int out_kind, const dou
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_adjoint_tail(p, fb, out_kind, xi_user, cot, grad_xi, grad_k, st);
+  return launch_adjoint_tail(p, fb, out_kind, xi_user, cot, cot_rec, grad_xi, grad_k, st);
 }
 
 }  // namespace mdp

@@ -18,7 +18,7 @@ static inline dim3 g1(int n) { return dim3((unsigned)n, 1, 1); }
 
 // yhat(q, row) of the 4 full gamma rows of the cotangent (mode pair (q, Nx - q) per thread)
 __global__ void __launch_bounds__(128) k_adj_rows(Batch bt, const SubDesc *subs, const double *tab, double *ws,
-                                                  const double2 *cot) {
+                                                  const double2 *cot, const double2 *cot_rec) {
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
   const SubDesc &d = subs[it.sub];
@@ -46,6 +46,20 @@ __global__ void __launch_bounds__(128) k_adj_rows(Batch bt, const SubDesc *subs,
     st2(gr + 2 * (((long long)rr * d.Nq + (q - 1)) * it.ncols + b), cadd(ao, ae));
     if (q2 != q) st2(gr + 2 * (((long long)rr * d.Nq + (q2 - 1)) * it.ncols + b), csub(ao, ae));
   }
+  if (cot_rec && d.nrec >= 0) {  // fifth row: the receiver cotangent at row nrec, m = mlo+1 .. mhi-1
+    const double2 *cr = cot_rec + d.rec_off + (long long)(it.col0 + b) * (d.Px - 2);
+    cplx ao = cmk(0.0, 0.0), ae = cmk(0.0, 0.0);
+    int j = (int)(((long long)q * (d.mlo + 1)) % N2);
+    for (int mm = 0; mm < d.Px - 2; ++mm) {
+      const int m = d.mlo + 1 + mm;
+      const cplx v = cmk(cr[mm].x, cr[mm].y);
+      if (m & 1) ao = caxpy(S[j], v, ao); else ae = caxpy(S[j], v, ae);
+      j += q;
+      if (j >= N2) j -= N2;
+    }
+    st2(gr + 2 * ((4LL * d.Nq + (q - 1)) * it.ncols + b), cadd(ao, ae));
+    if (q2 != q) st2(gr + 2 * ((4LL * d.Nq + (q2 - 1)) * it.ncols + b), csub(ao, ae));
+  }
 }
 
 // muhat = T_q^{-H} yhat for one (mode, column): U^H forward substitution (rows below the
@@ -54,7 +68,8 @@ __global__ void __launch_bounds__(128) k_adj_rows(Batch bt, const SubDesc *subs,
 // kept on the ring rows nlo..nhi (a buffer, rows in matrix numbering).
 template <bool CF, bool DK>
 __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d, const double *tab,
-                                               const uint8_t *pivtab, double *ws, const double2 *cot, int b, int q) {
+                                               const uint8_t *pivtab, double *ws, const double2 *cot, bool rec,
+                                               int b, int q) {
   constexpr int FW = CF ? 8 : 4;
   const double *F = tab + d.fact_off + (long long)(q - 1) * d.Nt * FW;
   const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * d.Nt;
@@ -74,7 +89,7 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
     const int rr = n == d.nlo - 1 ? 0 : n == d.nlo ? 1 : n == d.nhi ? 2 : n == d.nhi + 1 ? 3 : -1;
     if (rr >= 0) return ld2(gr + 2 * (((long long)rr * d.Nq + (q - 1)) * nc + b));
     const int g0 = 2 * W + 4 * (n - d.nlo - 1);
-    cplx v = cmk(0.0, 0.0);
+    cplx v = (rec && n == d.nrec) ? ld2(gr + 2 * ((4LL * d.Nq + (q - 1)) * nc + b)) : cmk(0.0, 0.0);
     v = caxpy(sg0, cmk(ct[g0].x, ct[g0].y), v);
     v = caxpy(sg1, cmk(ct[g0 + 1].x, ct[g0 + 1].y), v);
     v = caxpy(sg2, cmk(ct[g0 + 2].x, ct[g0 + 2].y), v);
@@ -126,7 +141,7 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
 
 template <bool DK>
 __global__ void __launch_bounds__(128) k_adj_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
-                                                 double *ws, const double2 *cot) {
+                                                 double *ws, const double2 *cot, int has_rec) {
   __shared__ double sh[128];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
@@ -136,8 +151,8 @@ __global__ void __launch_bounds__(128) k_adj_tri(Batch bt, const SubDesc *subs, 
   const int q = (local / cb) * 4 + threadIdx.y + 1;
   double dk = 0.0;
   if (b < it.ncols && q <= d.Nq)
-    dk = d.cplx ? adj_tri_body<true, DK>(it, d, tab, pivtab, ws, cot, b, q)
-                : adj_tri_body<false, DK>(it, d, tab, pivtab, ws, cot, b, q);
+    dk = d.cplx ? adj_tri_body<true, DK>(it, d, tab, pivtab, ws, cot, has_rec && d.nrec >= 0, b, q)
+                : adj_tri_body<false, DK>(it, d, tab, pivtab, ws, cot, has_rec && d.nrec >= 0, b, q);
   if (DK) {
     const double s = block_sum<128>(dk * (2.0 / d.Nx), sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) ws[it.red_off + local] = s;   // slot base 0: k_adj_tri
@@ -314,7 +329,7 @@ __global__ void k_red_subs(const Item *items, int n_items, const SubDesc *subs, 
 }
 
 cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, const double2 *cot,
-                                double2 *grad_xi, double *grad_k, cudaStream_t st) {
+                                const double2 *cot_rec, double2 *grad_xi, double *grad_k, cudaStream_t st) {
   const SubDesc *ds = p->d_subs;
   const double *tab = p->d_tables;
   double *ws = p->d_ws;
@@ -328,9 +343,9 @@ cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, cons
       prof_end(p, fam, st);                       \
     }                                             \
   } while (0)
-  ADJ_LAUNCH(F_AFWD, k_adj_rows<<<g1(fb[F_AFWD].total_blocks), b4, 0, st>>>(fb[F_AFWD], ds, tab, ws, cot));
-  if (dk) ADJ_LAUNCH(F_ATRI, k_adj_tri<true><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot));
-  else ADJ_LAUNCH(F_ATRI, k_adj_tri<false><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot));
+  ADJ_LAUNCH(F_AFWD, k_adj_rows<<<g1(fb[F_AFWD].total_blocks), b4, 0, st>>>(fb[F_AFWD], ds, tab, ws, cot, cot_rec));
+  if (dk) ADJ_LAUNCH(F_ATRI, k_adj_tri<true><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot, cot_rec ? 1 : 0));
+  else ADJ_LAUNCH(F_ATRI, k_adj_tri<false><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot, cot_rec ? 1 : 0));
   if (dk) {
     ADJ_LAUNCH(F_ARING, k_adj_ring_rows<true><<<g1(fb[F_ARING].total_blocks), b8, 0, st>>>(fb[F_ARING], ds, tab, ws));
     ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<true><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));

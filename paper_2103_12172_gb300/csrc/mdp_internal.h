@@ -30,7 +30,7 @@ struct SubDesc {
   int xsym;         // 1: mlo + mhi == Nx (subdomain centred along x): paired ring layout
   int Ph;           // xsym: pair units per dense ring row, Nx/2 - mlo + 1
   int R2;           // ring residual slots: R, or 8 Ph + 4 (Py - 4) with xsym
-  int pad1;
+  int nrec;         // receiver row (nlo+1 .. nhi-1) or -1; receivers m = mlo+1 .. mhi-1
   double h, k;
   double x0, x1, y0, y1, ax0, ay0;
   double c0, c1, c2;  // 9-point coefficients: centre, edge, corner (Eq. FD_scheme)
@@ -42,6 +42,7 @@ struct SubDesc {
   long long geo_off;    // doubles: gamma geometry [G][4] = (owner, s, rho, side length)
   long long seg_off;    // doubles: per mode [Nq][2] = (rlo, rhi): factor rows rlo..rhi-1 are real
   long long out_off;    // complex elements: start of the subdomain's output block
+  long long rec_off;    // complex elements: start of the receiver block [n_cols][Px - 2]
 };
 
 // One batch work item: columns [col0, col0 + ncols) of subdomain `sub`, with its
@@ -97,6 +98,7 @@ struct mdp_plan {
   std::vector<double> host_tables;       // all factor / dT / sine / geometry tables
   std::vector<uint8_t> host_piv;
   long long out_size = 0;
+  long long rec_size = 0;
   int tile_cols = 256;                   // columns per work item
   long long ws_budget = 0;               // bytes of workspace
   std::vector<mdp::Wave> waves;          // batch schedule of mdp_project_batch
@@ -113,7 +115,7 @@ struct mdp_plan {
   std::vector<int *> d_wave_prefix, d_gwave_prefix;  // [wave] -> device int [NFAM][n_items + 1]
   std::vector<std::vector<int>> h_wave_prefix, h_gwave_prefix;
   // CUDA graphs of mdp_project_batch, keyed by (xi, out, kind, stream)
-  struct GraphEntry { const void *xi; void *out; int kind; cudaStream_t st; cudaGraphExec_t exec; };
+  struct GraphEntry { const void *xi; void *out; void *out_rec; int kind; cudaStream_t st; cudaGraphExec_t exec; };
   std::vector<GraphEntry> graphs;
   // per-kernel event timing (mdp_plan_profile)
   bool prof_on = false;
@@ -124,7 +126,8 @@ struct mdp_plan {
 namespace mdp {
 
 // kernel families (each has its own block decomposition of an item); F_A* are the adjoint's
-enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_ARINGC, F_AGAM, NFAM };
+enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_ARINGC, F_AGAM, F_IREC,
+           NFAM };
 
 // Blocks of kernel family f for an item of ncols columns: 32 columns (x) times BY tasks (y).
 // The same function numbers the blocks on the host (prefix sums) and in the kernels.
@@ -142,6 +145,7 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
     case F_ARING: return cb * ((4 * d.Px + 7) / 8);
     case F_ARINGC: return cb * ((d.Py - 4 + 7) / 8);
     case F_AGAM: return cb * ((d.G + 7) / 8);
+    case F_IREC: return d.nrec < 0 ? 0 : cb * (((d.xsym ? d.Ph - 1 : d.Px - 2) + 7) / 8);
     default: return 0;
   }
 }
@@ -167,12 +171,13 @@ void host_mode_solve(const HostSub &hs, int q, int adjoint, const double *b, dou
 // kernel launchers (kernels.cu)
 enum { PASS_FWD = 0, PASS_GRAD = 1 };
 cudaError_t launch_project(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,
-                           double2 *out, cudaStream_t st);
+                           double2 *out, double2 *out_rec, cudaStream_t st);
 cudaError_t launch_adjoint(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,
-                           const double2 *cot, double2 *grad_xi, double *grad_k, cudaStream_t st);
+                           const double2 *cot, const double2 *cot_rec, double2 *grad_xi, double *grad_k,
+                           cudaStream_t st);
 // the adjoint's own kernels (kernels_adj.cu), after the forward recompute of the gradient pass
 cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, const double2 *cot,
-                                double2 *grad_xi, double *grad_k, cudaStream_t st);
+                                const double2 *cot_rec, double2 *grad_xi, double *grad_k, cudaStream_t st);
 
 cudaError_t launch_solve(const mdp_plan *p, int sub, int nrhs, const double2 *g, double2 *u, int adjoint,
                          cudaStream_t st);

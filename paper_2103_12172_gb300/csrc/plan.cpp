@@ -20,7 +20,8 @@ static const double kSingularTol = 1e-13; // pivot below this x max|T| -> singul
 
 const char *fam_name(int f) {
   static const char *names[NFAM] = {"k_extend", "k_residual", "k_fwd_rows", "k_tri", "k_inv_rows", "k_inv_cols",
-                                    "k_adj_rows", "k_adj_tri", "k_adj_ring_rows", "k_adj_ring_cols", "k_adj_gamma"};
+                                    "k_adj_rows", "k_adj_tri", "k_adj_ring_rows", "k_adj_ring_cols", "k_adj_gamma",
+                                    "k_inv_rec"};
   return (f >= 0 && f < NFAM) ? names[f] : "?";
 }
 
@@ -30,7 +31,7 @@ void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long 
   long long off = 0;
   xi = off; off += al((long long)d.G * ncols * (grad ? 2 : 1));
   r = off;  off += al((long long)std::max(d.R, d.R2) * ncols * 2);
-  gr = off; off += al(4LL * d.Nq * ncols * 2);
+  gr = off; off += al(5LL * d.Nq * ncols * 2);  // 4 dense rows (+ the receiver row in the adjoint)
   y = off;  off += al((long long)d.Nq * (grad ? d.Nt : d.NYf) * ncols * 2);
   a = off;  off += grad ? al((long long)d.Nq * d.Nt * ncols * 2) : 0;
   s = off;  off += grad ? al((long long)d.R * ncols * 2) : 0;
@@ -74,6 +75,7 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   d.xsym = (mlo + mhi == d.Nx) && (d.Nx % 2 == 0);
   d.Ph = d.xsym ? d.Nx / 2 - mlo + 1 : 0;
   d.R2 = d.xsym ? 8 * d.Ph + 4 * (d.Py - 4) : d.R;  // (sum, difference) per pair unit
+  d.nrec = -1;
   d.nfirst = d.cplx ? 0 : 1;
   d.Nt = d.cplx ? in.ny : in.ny - 2;
   d.i0 = (nlo - 1) - d.nfirst;
