@@ -1,0 +1,191 @@
+"""Layered strip: domain-decomposition coupling on top of the batched projection columns, and
+its gradient with respect to the per-layer wavenumbers.
+
+Subdomains Omega_j = [j, j+1] x [0, 1] (a duct, Section 4) with wavenumbers k_j. Per layer the
+library computes Q_j = (P_gamma - I) Ex Psi (Section 3.2.5) and the difference potential of
+every basis column at a receiver row (Eq. potential_solution_homo) in one batched pass. The
+coupling follows Sections 3.3-3.5: outer sides carry alpha u + beta du/dn = phi expanded in the
+Chebyshev basis (Eq. BC_coefficients), interfaces carry c^(0) continuous and c^(1) opposite
+(Section 3.3.2); the BC and interface equations are eliminated (Section 3.3.3) and the stacked
+system is solved in the least-squares sense by QR (steps 2(b)-(c)). The loss is the squared
+misfit of the reconstructed solution at the receivers.
+
+The coupling is small dense linear algebra (hundreds of unknowns) written with torch so that
+autograd carries the chain rule; the AP solves, the projection columns, the receiver values and
+their wavenumber derivatives run in libmdp (forward: mdp_project_batch_rec; backward:
+mdp_ap_adjoint_rec).
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import Plan
+
+
+class ProjectWithReceivers(torch.autograd.Function):
+    """(Q, receiver values) of the basis columns of every subdomain as functions of k."""
+
+    @staticmethod
+    def forward(ctx, k, plan):
+        ks = [float(v) for v in k.detach().cpu().tolist()]
+        if getattr(plan, "_k_current", None) != ks:
+            plan.update_k(ks)
+            plan._k_current = ks
+        out, rec = plan.project(out_rec=True)
+        ctx.plan, ctx.ks = plan, ks
+        ctx.k_meta = (k.dtype, k.device)
+        return out, rec
+
+    @staticmethod
+    def backward(ctx, g_out, g_rec):
+        plan = ctx.plan
+        if getattr(plan, "_k_current", None) != ctx.ks:
+            plan.update_k(ctx.ks)
+            plan._k_current = ctx.ks
+        g_out = torch.zeros(plan.output_size, dtype=torch.complex128, device="cuda") if g_out is None else g_out
+        g_rec = None if g_rec is None else g_rec.contiguous()
+        _, gk = plan.adjoint(g_out.contiguous(), grad_xi=False, cot_rec=g_rec)
+        dtype, device = ctx.k_meta
+        return gk.to(dtype=dtype, device=device), None
+
+
+def cheb_coeffs(fvals, n):
+    """Chebyshev coefficients of the degree n-1 interpolant from values at the n first-kind
+    Chebyshev points x_i = cos(pi (i + 1/2) / n) (i = 0..n-1): c_m = (2/n) sum_i f(x_i) T_m(x_i),
+    c_0 halved. fvals [..., n] complex."""
+    i = torch.arange(n, dtype=torch.float64, device=fvals.device)
+    m = torch.arange(n, dtype=torch.float64, device=fvals.device)
+    T = torch.cos(m[:, None] * math.pi * (i[None, :] + 0.5) / n)   # T_m(x_i)
+    c = (2.0 / n) * (fvals @ T.T.to(fvals.dtype))
+    c[..., 0] = c[..., 0] / 2
+    return c
+
+
+def cheb_points(n, device):
+    i = torch.arange(n, dtype=torch.float64, device=device)
+    return torch.cos(math.pi * (i + 0.5) / n)
+
+
+class LayeredStrip:
+    """The strip of `subdomains` (unit squares side by side along x) with outer boundary data
+    bc(j, side, k_j, x, y) -> (alpha, beta, phi values) (torch, differentiable in k_j) and a
+    receiver row per layer."""
+
+    def __init__(self, subdomains, bc, receiver_rows, tile_cols=0):
+        self.subs = list(subdomains)
+        self.N = len(self.subs)
+        self.M = self.subs[0].n_modes
+        self.bc = bc
+        self.plan = Plan(self.subs, tile_cols=tile_cols)
+        self.plan.set_receivers(receiver_rows)
+        self.layout = [self.plan.layout(j) for j in range(self.N)]
+        self.rlayout = [self.plan.receiver_layout(j) for j in range(self.N)]
+
+    def outer(self, j, side):
+        return not ((side == 4 and j < self.N - 1) or (side == 3 and j > 0))
+
+    def _side_xy(self, j, side, s):
+        sb = self.subs[j]
+        if side in (1, 2):
+            return sb.x0 + (s + 1) / 2 * (sb.x1 - sb.x0), torch.full_like(s, sb.y0 if side == 1 else sb.y1)
+        return torch.full_like(s, sb.x0 if side == 3 else sb.x1), sb.y0 + (s + 1) / 2 * (sb.y1 - sb.y0)
+
+    def receivers(self, k):
+        """Solution at the receivers of every layer (list of complex tensors), differentiable in k."""
+        M, N = self.M, self.N
+        out, rec = ProjectWithReceivers.apply(k, self.plan)
+        s = cheb_points(M, out.device)
+        # unknowns: one block per outer side, two per interface
+        idx, n = {}, 0
+        for j in range(N):
+            for side in (1, 2, 3, 4):
+                if self.outer(j, side):
+                    idx[(j, side)] = n
+                    n += M
+            if j < N - 1:
+                idx[("if", j)] = n
+                n += 2 * M
+        A_rows, b_rows, coef = [], [], []
+        for j in range(N):
+            G, nc, off, _ = self.layout[j]
+            Q = out[off:off + G * nc].view(nc, G).transpose(0, 1)          # [G, 8M]
+            A = torch.zeros(G, n, dtype=torch.complex128, device=out.device)
+            b = torch.zeros(G, dtype=torch.complex128, device=out.device)
+            cj = []
+            for side in (1, 2, 3, 4):
+                Q0 = Q[:, (side - 1) * M: side * M]
+                Q1 = Q[:, 4 * M + (side - 1) * M: 4 * M + side * M]
+                if self.outer(j, side):
+                    x, y = self._side_xy(j, side, s)
+                    alpha, beta, phi = self.bc(j, side, k[j], x, y)
+                    d = cheb_coeffs(phi, M)
+                    c = idx[(j, side)]
+                    pad_l, pad_r = c, n - c - M
+                    if beta != 0:
+                        blk = Q0 - (alpha / beta) * Q1
+                        b = b - Q1 @ (d / beta)
+                        cj.append(("robin", c, d, alpha, beta))
+                    else:
+                        blk = Q1
+                        b = b - Q0 @ (d / alpha)
+                        cj.append(("dirichlet", c, d, alpha, beta))
+                    A = A + torch.nn.functional.pad(blk, (pad_l, pad_r))
+                else:
+                    jj = j if side == 4 else j - 1
+                    c = idx[("if", jj)]
+                    sgn = 1.0 if side == 4 else -1.0
+                    blk = torch.cat([Q0, sgn * Q1], dim=1)
+                    A = A + torch.nn.functional.pad(blk, (c, n - c - 2 * M))
+                    cj.append(("if", c, sgn))
+            A_rows.append(A)
+            b_rows.append(b)
+            coef.append(cj)
+        A = torch.cat(A_rows)
+        b = torch.cat(b_rows)
+        # columns scaled to unit norm (same minimiser, better-conditioned QR), x = D y
+        D = 1.0 / torch.linalg.vector_norm(A, dim=0)
+        Qf, R = torch.linalg.qr(A * D)
+        xsol = D * torch.linalg.solve_triangular(R, (Qf.conj().transpose(0, 1) @ b)[:, None], upper=True)[:, 0]
+        res = []
+        for j in range(N):
+            parts0, parts1 = [], []
+            for side, spec in zip((1, 2, 3, 4), coef[j]):
+                if spec[0] == "robin":
+                    _, c, d, alpha, beta = spec
+                    u0 = xsol[c:c + M]
+                    parts0.append(u0)
+                    parts1.append((d - alpha * u0) / beta)
+                elif spec[0] == "dirichlet":
+                    _, c, d, alpha, beta = spec
+                    parts0.append(d / alpha)
+                    parts1.append(xsol[c:c + M])
+                else:
+                    _, c, sgn = spec
+                    parts0.append(xsol[c:c + M])
+                    parts1.append(sgn * xsol[c + M:c + 2 * M])
+            cvec = torch.cat(parts0 + parts1)
+            row, m0, cnt, roff = self.rlayout[j]
+            nc = self.layout[j][1]
+            K = rec[roff:roff + nc * cnt].view(nc, cnt).transpose(0, 1)    # [cnt, 8M]
+            res.append(K @ cvec)
+        return res
+
+
+def incident_impedance_bc(theta):
+    """Outer data of config `strip4x1`: impedance sides du/dn + i k_j u = phi with phi from the
+    plane wave exp(i k_j (x cos theta + y sin theta)) of the layer's own wavenumber."""
+    def bc(j, side, kj, x, y):
+        kx, ky = kj * math.cos(theta), kj * math.sin(theta)
+        u = torch.exp(1j * (kx * x + ky * y))
+        dn = {1: -1j * ky, 2: 1j * ky, 3: -1j * kx, 4: 1j * kx}[side] * u
+        return 1j * kj, 1.0, dn + 1j * kj * u
+    return bc
+
+
+def receiver_row(sub, y_target=0.9):
+    """Grid row whose y is nearest y_target (within M+)."""
+    import numpy as np
+    y = sub.ay0 + np.arange(sub.ny) * sub.h
+    return int(np.argmin(np.abs(y - y_target)))

@@ -144,3 +144,26 @@ def test_checkerboard_workload_sampled(dev):
         cols = sorted(rng.choice(8 * sub.n_modes, 12, replace=False).tolist())
         ref = APSystem(sub).columns(cols=cols)
         assert rel_col_err(blocks[i].cpu().numpy()[cols], ref) < TOL, i
+
+
+@pytest.mark.slow
+def test_dd8x8_workload_sampled(dev):
+    """The 8 x 8 decomposition at full size (64 subdomains, 257^2 / 513^2 / 1025^2 grids, 32768
+    columns) in one batched pass; one subdomain per grid class is checked against the oracle on
+    4 sampled columns (the 1025^2 SuperLU factorisation alone takes about a minute)."""
+    wl = W.dd8x8_mixed()
+    subs = list(wl.subdomains)
+    plan = dev.Plan(subs)
+    out = plan.project()
+    torch.cuda.synchronize()
+    plan.status()
+    blocks = plan.blocks(out)
+    seen = set()
+    for i, s in enumerate(subs):
+        if s.nx in seen:
+            continue
+        seen.add(s.nx)
+        cols = [0, 129, 300, 511]
+        ref = APSystem(s).columns(cols=cols)
+        assert rel_col_err(blocks[i].cpu().numpy()[cols], ref) < TOL, (i, s.nx)
+    assert seen == {257, 513, 1025}

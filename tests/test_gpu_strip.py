@@ -1,0 +1,124 @@
+"""Layered strip: the GPU DD pipeline against the oracle's DD solve, and the
+wavenumber gradient of the receiver misfit (autograd through the coupling, libmdp's adjoint for
+the AP solves) against central differences."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.dd import Strip
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+THETA = 0.3
+
+
+def oracle_bc(ks):
+    def bc(j, side):
+        kx, ky = ks[j] * math.cos(THETA), ks[j] * math.sin(THETA)
+        sgn = {1: -1j * ky, 2: 1j * ky, 3: -1j * kx, 4: 1j * kx}[side]
+
+        def phi(s, j=j, side=side):
+            from oracle.dd import side_points
+            x, y = side_points(subs_holder[0][j], side, s)
+            u = np.exp(1j * (kx * x + ky * y))
+            return sgn * u + 1j * ks[j] * u
+        return 1j * ks[j], 1.0, phi
+    return bc
+
+
+subs_holder = [None]
+
+
+def build(n, ks, M):
+    from paper_2103_12172_gb300.strip import LayeredStrip, incident_impedance_bc, receiver_row
+    subs = [W.unit_subdomain(j, 0, n, k, W.AP_DIRX_SOMMY, M) for j, k in enumerate(ks)]
+    rows = [receiver_row(s) for s in subs]
+    return subs, rows, LayeredStrip(subs, incident_impedance_bc(THETA), rows)
+
+
+def test_strip_receivers_match_oracle_dd(mdp):
+    ks = [12.0, 15.0, 18.0, 14.0]
+    subs, rows, strip = build(65, ks, 8)
+    k = torch.tensor(ks, dtype=torch.float64)
+    got = [u.detach().cpu().numpy() for u in strip.receivers(k)]
+    subs_holder[0] = subs
+    _, ref, _ = Strip(subs, oracle_bc(ks)).solve(rows)
+    for g, r in zip(got, ref):
+        assert np.abs(g - r).max() < 1e-8 * np.abs(r).max()
+
+
+def loss_fn(strip, k, targets):
+    return sum(torch.sum(torch.abs(u - t) ** 2) for u, t in zip(strip.receivers(k), targets))
+
+
+def test_layered_strip_gradient_matches_central_differences(mdp):
+    """The 4 x 1 strip of 129^2 grids, 24 modes per side, k_j = 40 against targets at k drawn
+    from default_rng(3): dLoss/dk_j by the adjoint vs 4th-order central differences."""
+    wl = W.strip4x1()
+    subs = list(wl.subdomains)
+    from paper_2103_12172_gb300.strip import LayeredStrip, incident_impedance_bc, receiver_row
+    rows = [receiver_row(s) for s in subs]
+    strip = LayeredStrip(subs, incident_impedance_bc(THETA), rows)
+    with torch.no_grad():
+        targets = [u.clone() for u in strip.receivers(torch.tensor(W.strip_targets(), dtype=torch.float64))]
+    k0 = [s.k for s in subs]
+    k = torch.tensor(k0, dtype=torch.float64, requires_grad=True)
+    L = loss_fn(strip, k, targets)
+    L.backward()
+    g = k.grad.numpy()
+    for j in range(4):
+        d = 1e-4 * k0[j]
+
+        def f(delta):
+            kk = list(k0)
+            kk[j] += delta
+            with torch.no_grad():
+                return float(loss_fn(strip, torch.tensor(kk, dtype=torch.float64), targets))
+
+        fd = (8 * (f(d) - f(-d)) - (f(2 * d) - f(-2 * d))) / (12 * d)
+        assert abs(g[j] - fd) < 1e-6 * abs(fd), (j, g[j], fd)
+
+
+@pytest.mark.slow
+def test_layered_strip_workload_matches_oracle(mdp):
+    """Receiver values of the 4 x 1 strip at k_j = 40 (4 x 129^2, 768 columns) against the oracle."""
+    wl = W.strip4x1()
+    subs = list(wl.subdomains)
+    ks = [s.k for s in subs]
+    _, rows, strip = build(129, ks, subs[0].n_modes)
+    got = [u.detach().cpu().numpy() for u in strip.receivers(torch.tensor(ks, dtype=torch.float64))]
+    subs_holder[0] = subs
+    _, ref, _ = Strip(subs, oracle_bc(ks)).solve(rows)
+    for g, r in zip(got, ref):
+        assert np.abs(g - r).max() < 1e-8 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+def test_receiver_output_and_its_adjoint_match_oracle(mdp, ap):
+    from oracle.projection import APSystem
+    sub = W.small_subdomain(65, 13.0, ap, 2)
+    plan = mdp.Plan([sub], tile_cols=8)
+    S = APSystem(sub)
+    row = 40
+    plan.set_receivers([row])
+    G, nc, _, _ = plan.layout(0)
+    _, _, cnt, _ = plan.receiver_layout(0)
+    out, rec = plan.project(out_rec=True)
+    ref = S.receivers(row)
+    got = rec.cpu().numpy().reshape(nc, cnt)
+    assert (np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)).max() < 1e-10
+    cot = W.random_complex((nc, G), seed=31)
+    crec = W.random_complex((nc, cnt), seed=32)
+    _, gk = plan.adjoint(torch.from_numpy(cot.ravel()).cuda(), grad_xi=False,
+                         cot_rec=torch.from_numpy(crec.ravel()).cuda())
+    _, gref = S.adjoint(cot, cot_rec=crec, rec_row=row)
+    assert abs(gk.item() - gref) < 1e-9 * abs(gref)
+    xi = W.random_complex((nc, G), seed=33)
+    gx, _ = plan.adjoint(torch.from_numpy(cot.ravel()).cuda(), xi=torch.from_numpy(xi.ravel()).cuda(),
+                         cot_rec=torch.from_numpy(crec.ravel()).cuda())
+    gxr, _ = S.adjoint(cot, xi=xi, cot_rec=crec, rec_row=row)
+    gx = gx.cpu().numpy().reshape(nc, G)
+    assert (np.abs(gx - gxr).max(axis=1) / np.abs(gxr).max(axis=1)).max() < 1e-10
