@@ -150,6 +150,26 @@ def kernel_flops(plan, items):
     return tot
 
 
+# ------------------------------------------------------------------ ncu traffic record
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels_common.cuh", "mdp_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2103_12172_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from profiles/traffic.json (an ncu
+    capture), or None when absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[workload][kernel]
+    except (OSError, ValueError, KeyError):
+        return None
+    return rec["dram_bytes_per_launch"] if rec.get("source_sha256") == kernel_source_sha() else None
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
@@ -332,7 +352,7 @@ def run_ours(args, wl):
                    "tile_cols": tile,
                    "l2": "flushed between timed steps (512 MiB write, untimed)", "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": recorded_traffic(dom, wl.name),
                      "peak_note": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA rate per SM measured)",
                      "fp64_probe_tflops": fp64_probe / 1e3},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items())},
