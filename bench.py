@@ -134,13 +134,17 @@ def kernel_flops(plan, items):
         g = plan.sub_info(sub)
         Px, Py, Nq, Nt, i0, cx, R, Nx = g["Px"], g["Py"], g["Nq"], g["Nt"], g["i0"], g["cplx"], g["R"], g["Nx"]
         xs = g["xsym"]
-        nf, nb, nmid = Nt - 1 - i0, Nt - i0, Py - 4
+        # the projection sweeps rows i0 .. nhi+1 (rows above are condensed into the last pivot),
+        # pivot-scaled: forward = scaled right-hand side + recurrence, back = x - u1 x' (no 1/d)
+        nb = Py + 2
+        nf = nb - 1
         if cx:
-            f = g["complex_rows"] / float(Nq * (Nt - i0))
-            tri = nf * (8 * f + 4 * (1 - f)) + nmid * (3 if xs else 8) + nb * (14 * f + 6 * (1 - f))
+            f = g["complex_rows"] / float(Nq * nb)
+            fwd = f * (6 + 8) + (1 - f) * ((3 if xs else 8) + 4)
+            tri = nf * fwd + nb * (8 * f + 4 * (1 - f))
             inv = 4
         else:
-            tri = nf * 2 + nmid * (3 if xs else 8) + nb * 3
+            tri = nf * ((3 if xs else 8) + 2) + nb * 2
             inv = 2
         add("k_tri", nc * Nq * tri)
         add("k_inv_cols", nc * (Py - 2) * Nq * (2 if xs else 4) * inv)
@@ -295,8 +299,7 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     plan.update_k(ks)
-    table_bytes = sum(8 * (pi["Nq"] * pi["Nt"] * (14 if pi["cplx"] else 10)) for pi in
-                      (plan.sub_info(s) for s in range(len(subs))))
+    table_bytes = int(plan.L.mdp_plan_table_bytes(plan.handle))
     e2e = {"value": world * n_cols * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(table_bytes),
            "d2h_bytes_per_step": int(plan.output_size * 16),
            "what": "update_k (host LU of every mode + table upload) + project + D2H of all columns"}

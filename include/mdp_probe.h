@@ -33,6 +33,10 @@ const char *mdp_kernel_family_name(int family);
  * number of factor rows with complex entries swept by the projection, over all modes. */
 mdp_status mdp_plan_sub_info(const mdp_plan *p, int sub, int *info14);
 
+/* Bytes of the plan's host tables that mdp_plan_update_k uploads (factors, sweep tables, sines,
+ * geometry, pivot flags). */
+long long mdp_plan_table_bytes(const mdp_plan *p);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,7 @@ def _nvcc():
 
 def _flags():
     return ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+                   "-Xcompiler", "-fcx-fortran-rules",
                    "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 
 

@@ -75,6 +75,7 @@ def lib():
         "mdp_plan_set_receivers": (i, [vp, C.POINTER(i)]),
         "mdp_plan_receiver_layout": (i, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(ll)]),
         "mdp_plan_receiver_size": (ll, [vp]),
+        "mdp_plan_table_bytes": (ll, [vp]),
         "mdp_project_batch_rec": (i, [vp, vp, vp, vp, i, vp]),
         "mdp_ap_adjoint_rec": (i, [vp, vp, vp, vp, vp, vp, i, vp]),
     }

@@ -452,6 +452,10 @@ mdp_status mdp_plan_receiver_layout(const mdp_plan *p, int sub, int *row, int *m
 
 long long mdp_plan_receiver_size(const mdp_plan *p) { return p ? p->rec_size : 0; }
 
+long long mdp_plan_table_bytes(const mdp_plan *p) {
+  return p ? (long long)(p->host_tables.size() * sizeof(double) + p->host_piv.size()) : 0;
+}
+
 int mdp_kernel_family_count(void) { return NFAM; }
 
 const char *mdp_kernel_family_name(int family) { return fam_name(family); }
@@ -461,11 +465,12 @@ mdp_status mdp_plan_sub_info(const mdp_plan *p, int sub, int *info) {
   const HostSub &hs = p->subs[sub];
   const SubDesc &d = hs.d;
   int npiv = 0;
-  for (auto v : hs.piv) npiv += v;
+  for (long long i = 0; i < (long long)d.Nq * d.Nt; ++i) npiv += hs.piv[i];
   long long creal = 0;  // complex factor rows swept by the forward projection, over all modes
   for (int q = 0; q < d.Nq; ++q) {
-    const int rlo = std::max(hs.seg[2 * q], d.i0), rhi = std::max(hs.seg[2 * q + 1], rlo);
-    creal += (d.Nt - d.i0) - (rhi - rlo);
+    const int itop = hs.seg[5 * q + 4];
+    const int rlo = std::max(hs.seg[5 * q + 2], d.i0), rhi = std::min(std::max(hs.seg[5 * q + 3], rlo), itop);
+    creal += (itop - d.i0 + 1) - (rhi - rlo);
   }
   const int vals[14] = {d.Px, d.Py, d.Nq, d.Nt, d.i0, d.nfirst, d.cplx, d.G, d.R, npiv, d.n_cols, d.Nx,
                         d.xsym, (int)creal};

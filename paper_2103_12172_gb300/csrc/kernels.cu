@@ -233,7 +233,7 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
   const int P = d.Px, nc = it.ncols;
   int rlo = 0, rhi = d.Nt;  // real factor rows
   if (CF) {
-    const double *sg = tab + d.seg_off + 2 * (q - 1);
+    const double *sg = tab + d.seg_off + 5 * (q - 1);
     rlo = (int)sg[0];
     rhi = (int)sg[1];
   }
@@ -352,6 +352,173 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
   if (CF) for (; i >= ilo; --i) back_complex(i);
 }
 
+// The projection's sweep over the condensed, pivot-scaled table (plan: build_fs): rows
+// i0 .. itop, y~ = y / d stored, so the back substitution is x = y~ - u1 x' - u2 x''. The rows
+// with real entries [frlo, frhi) use real coefficients; while no complex value has entered the
+// sweep (real densities and the run starts at i0) the forward recurrence is real.
+// CD: complex mode-space data (complex AP or complex densities).
+template <bool CD, bool CIN>
+__device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, const double *tab, double *ws, int b,
+                                            int q) {
+  const double *T = tab + d.fs_off + (long long)(q - 1) * d.NYf * FSW;
+  const double *sg = tab + d.seg_off + 5 * (q - 1);
+  const int frlo = (int)sg[2], frhi = (int)sg[3], itop = (int)sg[4];
+  const int N2 = 2 * d.Nx;
+  const double *S = tab + d.sin_off;
+  const double sm0 = S[(q * d.mlo) % N2], sm1 = S[(q * (d.mlo + 1)) % N2];
+  const double sm2 = S[(q * (d.mhi - 1)) % N2], sm3 = S[(q * d.mhi) % N2];
+  const int par = (q & 1) ? 0 : 1;
+  const double *r = ws + it.r_off;
+  const double *gr = ws + it.gr_off;
+  double *y = ws + it.y_off;
+  const int nc = it.ncols, P = d.Px;
+  const long long ybase = (long long)(q - 1) * d.NYf * nc + b;
+  auto ystore = [&](int i, cplx v) {
+    const long long o = ybase + (long long)(i - d.i0) * nc;
+    if (CD) st2(y + 2 * o, v); else y[o] = v.re;
+  };
+  auto yload = [&](int i) -> cplx {
+    const long long o = ybase + (long long)(i - d.i0) * nc;
+    return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
+  };
+  // ring data of grid row n: dense rows give gr (complex if CIN); middle rows give the slot values
+  auto dense = [&](int n) -> int {
+    return n == d.nlo ? 0 : n == d.nlo + 1 ? 1 : n == d.nhi - 1 ? 2 : n == d.nhi ? 3 : -1;
+  };
+  auto rv = [&](long long slot) -> cplx { return CIN ? ld2(r + 2 * (slot * nc + b)) : cmk(r[slot * nc + b], 0.0); };
+  // raw right-hand side of grid row n (swapped steps)
+  auto graw = [&](int n) -> cplx {
+    if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
+    const int rr = dense(n);
+    if (rr >= 0) {
+      const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b;
+      return CIN ? ld2(gr + 2 * o) : cmk(gr[o], 0.0);
+    }
+    if (d.xsym) {
+      const long long base = 8LL * d.Ph + 4 * (n - d.nlo - 2) + par;
+      return caxpy(sm1, rv(base + 2), cmk(sm0 * rv(base).re, sm0 * rv(base).im));
+    }
+    const long long ri = 2 * P + 4 * (n - d.nlo - 2);
+    cplx v = cmk(0.0, 0.0);
+    v = caxpy(sm0, rv(ri), v); v = caxpy(sm1, rv(ri + 1), v); v = caxpy(sm2, rv(ri + 2), v); v = caxpy(sm3, rv(ri + 3), v);
+    return v;
+  };
+  // scaled right-hand side g / d_{i+1} of grid row n from table row `row` (complex coefficients)
+  auto ghat_c = [&](const double *row, int n) -> cplx {
+    if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
+    const int rr = dense(n);
+    const cplx sc = ld2(row + 8);
+    if (rr >= 0) {
+      const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b;
+      if (CIN) return cmul(sc, ld2(gr + 2 * o));
+      const double g = gr[o];
+      return cmk(sc.re * g, sc.im * g);
+    }
+    if (d.xsym) {
+      const long long base = 8LL * d.Ph + 4 * (n - d.nlo - 2) + par;
+      if (CIN) return cadd(cmul(ld2(row + 10), rv(base)), cmul(ld2(row + 12), rv(base + 2)));
+      const double a0 = r[base * nc + b], a1 = r[(base + 2) * nc + b];
+      const cplx c0 = ld2(row + 10), c1 = ld2(row + 12);
+      return cmk(fma(c1.re, a1, c0.re * a0), fma(c1.im, a1, c0.im * a0));
+    }
+    const long long ri = 2 * P + 4 * (n - d.nlo - 2);
+    cplx v = cmk(0.0, 0.0);
+    for (int s_ = 0; s_ < 4; ++s_) v = cadd(v, cmul(ld2(row + 10 + 2 * s_), rv(ri + s_)));
+    return v;
+  };
+  // the same with real coefficients (rows of the real run)
+  auto ghat_r = [&](const double *row, int n) -> cplx {
+    if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
+    const int rr = dense(n);
+    const double sc = row[8];
+    if (rr >= 0) {
+      const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b;
+      if (CIN) { const cplx g = ld2(gr + 2 * o); return cmk(sc * g.re, sc * g.im); }
+      return cmk(sc * gr[o], 0.0);
+    }
+    if (d.xsym) {
+      const long long base = 8LL * d.Ph + 4 * (n - d.nlo - 2) + par;
+      const cplx a0 = rv(base);
+      return caxpy(row[12], rv(base + 2), cmk(row[10] * a0.re, row[10] * a0.im));
+    }
+    const long long ri = 2 * P + 4 * (n - d.nlo - 2);
+    cplx v = cmk(0.0, 0.0);
+    for (int s_ = 0; s_ < 4; ++s_) v = caxpy(row[10 + 2 * s_], rv(ri + s_), v);
+    return v;
+  };
+  // ---- forward sweep
+  cplx ct = cmk(0.0, 0.0);
+  int i = d.i0;
+  if (CD) {
+    for (; i < min(frlo, itop); ++i) {
+      const double *row = T + (long long)(i - d.i0) * FSW;
+      const int n = i + 1 + d.nfirst;
+      if (row[22] == 0.0) { ystore(i, ct); ct = cfms(ghat_c(row, n), ld2(row), ct); }
+      else {
+        const cplx g = graw(n);
+        ystore(i, cmul(ld2(row + 6), g));
+        ct = cfms(cmul(ld2(row + 2), ct), ld2(row + 4), g);
+      }
+    }
+  }
+  {
+    const int e = min(max(frhi, i), itop);
+    if (!CIN && i == d.i0) {     // real data so far: real recurrence
+      for (; i < e; ++i) {
+        const double *row = T + (long long)(i - d.i0) * FSW;
+        const int n = i + 1 + d.nfirst;
+        if (row[22] == 0.0) { ystore(i, ct); ct.re = fma(-row[0], ct.re, ghat_r(row, n).re); }
+        else {
+          const double g = graw(n).re;
+          ystore(i, cmk(row[6] * g, 0.0));
+          ct.re = fma(-row[4], g, row[2] * ct.re);
+        }
+      }
+    } else {
+      for (; i < e; ++i) {
+        const double *row = T + (long long)(i - d.i0) * FSW;
+        const int n = i + 1 + d.nfirst;
+        if (row[22] == 0.0) { ystore(i, ct); ct = caxpy(-row[0], ct, ghat_r(row, n)); }
+        else {
+          const cplx g = graw(n);
+          ystore(i, cmk(row[6] * g.re, row[6] * g.im));
+          ct = caxpy(-row[4], g, cmk(row[2] * ct.re, row[2] * ct.im));
+        }
+      }
+    }
+  }
+  if (CD) {
+    for (; i < itop; ++i) {
+      const double *row = T + (long long)(i - d.i0) * FSW;
+      const int n = i + 1 + d.nfirst;
+      if (row[22] == 0.0) { ystore(i, ct); ct = cfms(ghat_c(row, n), ld2(row), ct); }
+      else {
+        const cplx g = graw(n);
+        ystore(i, cmul(ld2(row + 6), g));
+        ct = cfms(cmul(ld2(row + 2), ct), ld2(row + 4), g);
+      }
+    }
+  }
+  ystore(itop, ct);
+  // ---- back substitution (rows nlo-1 .. nhi+1 are kept)
+  const int ikeep = d.nhi + 1 - d.nfirst;
+  cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
+  for (i = itop; i >= d.i0; --i) {
+    const double *row = T + (long long)(i - d.i0) * FSW;
+    const cplx yi = yload(i);
+    cplx x;
+    if (!CD || (i >= frlo && i < frhi)) {
+      x = cmk(fma(-row[18], x1.re, yi.re), CD ? fma(-row[18], x1.im, yi.im) : 0.0);
+      if (row[22] != 0.0) { x.re = fma(-row[20], x2.re, x.re); if (CD) x.im = fma(-row[20], x2.im, x.im); }
+    } else {
+      x = cfms(yi, ld2(row + 18), x1);
+      if (row[22] != 0.0) x = cfms(x, ld2(row + 20), x2);
+    }
+    if (i <= ikeep) ystore(i, x);
+    x2 = x1; x1 = x;
+  }
+}
+
 template <bool CIN, bool FULL>
 __global__ void __launch_bounds__(128) k_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
                                              double *ws) {
@@ -362,8 +529,13 @@ __global__ void __launch_bounds__(128) k_tri(Batch bt, const SubDesc *subs, cons
   const int b = (local % cb) * 32 + threadIdx.x;
   const int q = (local / cb) * 4 + threadIdx.y + 1;
   if (b >= it.ncols || q > d.Nq) return;
-  if (d.cplx) tri_body<true, CIN, FULL>(it, d, tab, pivtab, ws, b, q);
-  else tri_body<false, CIN, FULL>(it, d, tab, pivtab, ws, b, q);
+  if (FULL) {
+    if (d.cplx) tri_body<true, CIN, true>(it, d, tab, pivtab, ws, b, q);
+    else tri_body<false, CIN, true>(it, d, tab, pivtab, ws, b, q);
+  } else {
+    if (d.cplx || CIN) tri_fs_body<true, CIN>(it, d, tab, ws, b, q);
+    else tri_fs_body<false, CIN>(it, d, tab, ws, b, q);
+  }
 }
 
 // ---------------------------------------------------------------- inverse transforms on gamma

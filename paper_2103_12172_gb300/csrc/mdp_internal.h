@@ -3,6 +3,9 @@
 #include <cstdint>
 #include <vector>
 #include <string>
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <cuda_runtime.h>
 #include "mdp.h"
 
@@ -40,7 +43,9 @@ struct SubDesc {
   long long dT_off;     // doubles: dT_q/dk rows [Nq][Nt][6] (sub, diag, super; complex)
   long long sin_off;    // doubles: sin(pi j / Nx), j = 0 .. 2Nx-1, then (2/Nx) sin(pi j/Nx)
   long long geo_off;    // doubles: gamma geometry [G][4] = (owner, s, rho, side length)
-  long long seg_off;    // doubles: per mode [Nq][2] = (rlo, rhi): factor rows rlo..rhi-1 are real
+  long long seg_off;    // doubles: per mode [Nq][5] = (rlo, rhi, frlo, frhi, itop): real rows of the
+                        // factor table, real rows of the forward-sweep table, last swept row
+  long long fs_off;     // doubles: projection forward-sweep table [Nq][NYf][FSW] (rows i0..)
   long long out_off;    // complex elements: start of the subdomain's output block
   long long rec_off;    // complex elements: start of the receiver block [n_cols][Px - 2]
 };
@@ -71,16 +76,52 @@ struct Batch {
   Item one;
 };
 
+constexpr int FSW = 24;  // doubles per forward-sweep table row
+
+// Host buffer of the plan's tables: page-locked (cudaMallocHost) for plans with a device, so
+// that uploads (plan creation, mdp_plan_update_k) run at full link speed; plain heap memory for
+// host-only plans, which make no CUDA call. Zero-filled on allocation.
+template <class T>
+struct HostBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  bool pinned = false;
+  HostBuf() = default;
+  HostBuf(const HostBuf &) = delete;
+  HostBuf &operator=(const HostBuf &) = delete;
+  ~HostBuf() { release(); }
+  void release() {
+    if (p) { if (pinned) cudaFreeHost(p); else std::free(p); }
+    p = nullptr; n = 0; pinned = false;
+  }
+  bool alloc(size_t count, bool want_pinned) {
+    release();
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (want_pinned && cudaMallocHost((void **)&p, bytes) == cudaSuccess) pinned = true;
+    else { p = (T *)std::malloc(bytes); pinned = false; }
+    if (!p) return false;
+    std::memset((void *)p, 0, bytes);
+    n = count;
+    return true;
+  }
+  T *data() { return p; }
+  const T *data() const { return p; }
+  size_t size() const { return n; }
+  T &operator[](size_t i) { return p[i]; }
+  const T &operator[](size_t i) const { return p[i]; }
+};
+
 struct HostSub {
   SubDesc d;
   std::vector<int> gamma_nm;     // 2*G: (n, m) pairs, row-major order
   std::vector<int> owner;        // G
   std::vector<double> rho, s, L; // G
-  // tridiagonal factors (host copy, for introspection)
-  std::vector<double> fact;      // [Nq][Nt][FW]
-  std::vector<uint8_t> piv;      // [Nq][Nt]
-  std::vector<double> dT;        // [Nq][Nt][6]
-  std::vector<int> seg;          // [Nq][2]: real factor rows [rlo, rhi)
+  // this subdomain's slices of the plan's host tables (written in place by the factorisation)
+  double *fact = nullptr;        // [Nq][Nt][FW]
+  uint8_t *piv = nullptr;        // [Nq][Nt]
+  double *dT = nullptr;          // [Nq][Nt][6]
+  double *fs = nullptr;          // [Nq][NYf][FSW]: projection forward-sweep table
+  std::vector<int> seg;          // [Nq][5]: see SubDesc::seg_off
 };
 
 struct Wave {
@@ -95,8 +136,8 @@ struct mdp_plan {
   int n_subs = 0;
   int device = -1;
   std::vector<mdp::HostSub> subs;
-  std::vector<double> host_tables;       // all factor / dT / sine / geometry tables
-  std::vector<uint8_t> host_piv;
+  mdp::HostBuf<double> host_tables;      // all factor / dT / sweep / sine / geometry tables
+  mdp::HostBuf<uint8_t> host_piv;
   long long out_size = 0;
   long long rec_size = 0;
   int tile_cols = 256;                   // columns per work item

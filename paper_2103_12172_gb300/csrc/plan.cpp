@@ -9,7 +9,9 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <atomic>
 #include <cstring>
+#include <thread>
 
 namespace mdp {
 
@@ -123,98 +125,224 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
 //   and the mirror image at n = 0.
 // Factorisation: Gaussian elimination with partial pivoting on the band (row swaps create
 // one extra super-diagonal), the textbook algorithm for banded LU.
-static mdp_status factor_modes(HostSub &hs) {
-  SubDesc &d = hs.d;
-  const int N = d.Nt, FW = d.cplx ? 8 : 4;
-  hs.fact.assign((size_t)d.Nq * N * FW, 0.0);
-  hs.piv.assign((size_t)d.Nq * N, 0);
-  hs.dT.assign((size_t)d.Nq * N * 6, 0.0);
-  hs.seg.assign((size_t)d.Nq * 2, 0);
+// The tridiagonal T_q of sine mode q (rows 0..Nt-1) and, when dT != nullptr, its k-derivative
+// rows (sub, diag, super; complex). dl[i] = T[i+1][i], dg[i] = T[i][i], du[i] = T[i][i+1].
+static void mode_matrix(const SubDesc &d, int q, cd *dl, cd *dg, cd *du, double *dT) {
+  const int N = d.Nt;
   const double h = d.h, h2 = h * h, k = d.k, k2 = k * k;
-  std::vector<cd> dl(N), dg(N), du(N), du2(N);
-  for (int q = 1; q <= d.Nq; ++q) {
-    const double sq = std::sin(M_PI * q / (2.0 * d.Nx));
-    const double lam = -4.0 * sq * sq;
-    const double a = 1.0 / h2 + lam / (6.0 * h2) + k2 / 12.0;
-    const double dd = -2.0 * a + lam / h2 + k2 + k2 * lam / 12.0;
-    const double da = k / 6.0;
-    const double ddd = -2.0 * da + 2.0 * k + 2.0 * k * lam / 12.0;
-    const cd alpha((1.0 + k2 * h2 / 24.0 + lam / 24.0) / h2, 0.0);
-    const cd beta(0.0, k * (1.0 + k2 * h2 / 8.0 + lam / 8.0) / h);
-    const cd dalpha(k / 12.0, 0.0);
-    const cd dbeta(0.0, (1.0 + 3.0 * k2 * h2 / 8.0 + lam / 8.0) / h);
-    double *dT = &hs.dT[(size_t)(q - 1) * N * 6];
-    for (int i = 0; i < N; ++i) {
-      dl[i] = a; dg[i] = dd; du[i] = a; du2[i] = 0.0;
-      cd tsub = da, tdg = ddd, tsup = da;
-      if (d.cplx && i == 0) { dg[i] = alpha + 0.5 * beta; du[i] = -alpha + 0.5 * beta; tdg = dalpha + 0.5 * dbeta; tsup = -dalpha + 0.5 * dbeta; tsub = 0.0; }
-      if (d.cplx && i == N - 1) { dg[i] = alpha + 0.5 * beta; tdg = dalpha + 0.5 * dbeta; tsub = -dalpha + 0.5 * dbeta; tsup = 0.0; }
-      if (i == 0) tsub = 0.0;
-      if (i == N - 1) tsup = 0.0;
+  const double sq = std::sin(M_PI * q / (2.0 * d.Nx));
+  const double lam = -4.0 * sq * sq;
+  const double a = 1.0 / h2 + lam / (6.0 * h2) + k2 / 12.0;
+  const double dd = -2.0 * a + lam / h2 + k2 + k2 * lam / 12.0;
+  const double da = k / 6.0;
+  const double ddd = -2.0 * da + 2.0 * k + 2.0 * k * lam / 12.0;
+  const cd alpha((1.0 + k2 * h2 / 24.0 + lam / 24.0) / h2, 0.0);
+  const cd beta(0.0, k * (1.0 + k2 * h2 / 8.0 + lam / 8.0) / h);
+  const cd dalpha(k / 12.0, 0.0);
+  const cd dbeta(0.0, (1.0 + 3.0 * k2 * h2 / 8.0 + lam / 8.0) / h);
+  for (int i = 0; i < N; ++i) {
+    dl[i] = a; dg[i] = dd; du[i] = a;
+    cd tsub = da, tdg = ddd, tsup = da;
+    if (d.cplx && i == 0) { dg[i] = alpha + 0.5 * beta; du[i] = -alpha + 0.5 * beta; tdg = dalpha + 0.5 * dbeta; tsup = -dalpha + 0.5 * dbeta; tsub = 0.0; }
+    if (d.cplx && i == N - 1) { dg[i] = alpha + 0.5 * beta; tdg = dalpha + 0.5 * dbeta; tsub = -dalpha + 0.5 * dbeta; tsup = 0.0; }
+    if (i == 0) tsub = 0.0;
+    if (i == N - 1) tsup = 0.0;
+    if (dT) {
       dT[i * 6 + 0] = tsub.real(); dT[i * 6 + 1] = tsub.imag();
       dT[i * 6 + 2] = tdg.real();  dT[i * 6 + 3] = tdg.imag();
       dT[i * 6 + 4] = tsup.real(); dT[i * 6 + 5] = tsup.imag();
     }
-    // dl[i] is T[i+1][i]; the top Sommerfeld row's sub-diagonal entry is T[N-1][N-2]
-    if (d.cplx) dl[N - 2] = -alpha + 0.5 * beta;
+  }
+  // the top Sommerfeld row's sub-diagonal entry is T[N-1][N-2] = dl[N-2]
+  if (d.cplx) dl[N - 2] = -alpha + 0.5 * beta;
+}
+
+// Banded LU with partial pivoting of rows 0..N-1 in place: on return dl holds the multipliers,
+// dg the pivots, du / du2 the first / second super-diagonal of U, pv the row swaps.
+static bool band_lu(int N, cd *dl, cd *dg, cd *du, cd *du2, uint8_t *pv) {
+  for (int i = 0; i < N; ++i) du2[i] = 0.0;
+  for (int i = 0; i < N - 1; ++i) {
+    if (std::abs(dg[i]) >= std::abs(dl[i])) {
+      if (dg[i] == 0.0) return false;
+      const cd f = dl[i] / dg[i];
+      dl[i] = f;
+      dg[i + 1] -= f * du[i];
+      du2[i] = 0.0;
+      pv[i] = 0;
+    } else {
+      const cd f = dg[i] / dl[i];
+      dg[i] = dl[i];
+      dl[i] = f;
+      const cd tmp = du[i];
+      du[i] = dg[i + 1];
+      dg[i + 1] = tmp - f * dg[i + 1];
+      if (i < N - 2) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
+      pv[i] = 1;
+    }
+  }
+  pv[N - 1] = 0;
+  return true;
+}
+
+static bool tiny_imag(cd v) { return std::fabs(v.imag()) <= 0x1p-60 * std::abs(v); }
+
+// The projection's forward-sweep table (rows i0 .. Nt-1 of each mode, FSW doubles per row).
+// (1) Top condensation: rows above itop = nhi + 1 - nfirst carry zero right-hand side in the
+//     projection, so they are eliminated into the last pivot by their Schur complement
+//     T[itop][itop] -= T[itop][itop+1] T[itop+1][itop] / s_{itop+1}, s computed from the top row
+//     down (s_{N-1} = T[N-1][N-1], s_i = T[i][i] - T[i][i+1] T[i+1][i] / s_{i+1}); the condensed
+//     system (rows 0..itop) is factored with the same pivoted band LU. A mode whose s is tiny
+//     relative to the matrix (a resonance of the rows above) keeps all rows (itop = Nt-1).
+// (2) Pivot-scaled sweep: with y~_i = y_i / d_i stored, the back substitution is
+//     x_i = y~_i - (du_i/d_i) x_{i+1} - (du2_i/d_i) x_{i+2}; the forward sweep carries
+//     c~ = cur / d at each position: unswapped step c~' = g^_{i+1} - m_i c~ with
+//     m_i = l_i d_i / d_{i+1}, g^ = g / d_{i+1}; swapped step y~_i = g / d_i and
+//     c~' = (d_i / d_{i+1}) c~ - (l_i / d_{i+1}) g.
+// Row layout (complex pairs): m, p = d_i/d_{i+1}, mq = l_i/d_{i+1}, qd = 1/d_i, sc = 1/d_{i+1},
+// c0..c3 = sc * sin(pi q m_s / Nx) for the ring columns m_s = mlo, mlo+1, mhi-1, mhi, u1, u2,
+// then the swap flag and a pad. seg[2], seg[3]: rows with real entries [frlo, frhi); seg[4] = itop.
+static mdp_status build_fs_mode(HostSub &hs, int q) {
+  SubDesc &d = hs.d;
+  const int N = d.Nt, R = d.NYf;
+  std::vector<cd> dl(N), dg(N), du(N), du2(N), T_dl(N), T_dg(N), T_du(N);
+  std::vector<uint8_t> pv(N);
+  const int ih = d.nhi + 1 - d.nfirst;
+  {
+    mode_matrix(d, q, T_dl.data(), T_dg.data(), T_du.data(), nullptr);
     double scale = 0.0;
-    for (int i = 0; i < N; ++i) scale = std::max({scale, std::abs(dg[i]), std::abs(du[i]), std::abs(dl[i])});
-    uint8_t *pv = &hs.piv[(size_t)(q - 1) * N];
-    for (int i = 0; i < N - 1; ++i) {
-      if (std::abs(dg[i]) >= std::abs(dl[i])) {
-        if (dg[i] == 0.0) return MDP_ERR_SINGULAR;
-        const cd f = dl[i] / dg[i];
-        dl[i] = f;
-        dg[i + 1] -= f * du[i];
-        du2[i] = 0.0;
-        pv[i] = 0;
-      } else {
-        const cd f = dg[i] / dl[i];
-        dg[i] = dl[i];
-        dl[i] = f;
-        const cd tmp = du[i];
-        du[i] = dg[i + 1];
-        dg[i + 1] = tmp - f * dg[i + 1];
-        if (i < N - 2) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
-        pv[i] = 1;
+    for (int i = 0; i < N; ++i) scale = std::max({scale, std::abs(T_dg[i]), std::abs(T_du[i]), std::abs(T_dl[i])});
+    int itop = N - 1;
+    cd sigma = 0.0;
+    if (ih < N - 1) {
+      cd sv = T_dg[N - 1];
+      bool ok = std::abs(sv) > 1e-8 * scale;
+      for (int i = N - 2; i >= ih + 1 && ok; --i) {
+        sv = T_dg[i] - T_du[i] * T_dl[i] / sv;
+        ok = std::abs(sv) > 1e-8 * scale;
       }
+      if (ok) { itop = ih; sigma = T_du[ih] * T_dl[ih] / sv; }
     }
-    double *F = &hs.fact[(size_t)(q - 1) * N * FW];
-    std::vector<uint8_t> isreal(N, 1);
-    for (int i = 0; i < N; ++i) {
+    const int n = itop + 1;
+    for (int i = 0; i < n; ++i) { dl[i] = T_dl[i]; dg[i] = T_dg[i]; du[i] = T_du[i]; }
+    dg[itop] -= sigma;
+    if (!band_lu(n, dl.data(), dg.data(), du.data(), du2.data(), pv.data())) return MDP_ERR_SINGULAR;
+    for (int i = 0; i < n; ++i)
       if (std::abs(dg[i]) < kSingularTol * scale) return MDP_ERR_SINGULAR;
+    const int N2 = 2 * d.Nx;
+    const int ms[4] = {d.mlo, d.mlo + 1, d.mhi - 1, d.mhi};
+    double sines[4];
+    for (int s_ = 0; s_ < 4; ++s_) sines[s_] = std::sin(M_PI * (double)((q * ms[s_]) % N2) / (double)d.Nx);
+    double *F = hs.fs + (size_t)(q - 1) * R * FSW;
+    std::vector<uint8_t> isreal(R, 1);
+    for (int i = d.i0; i <= itop; ++i) {
+      double *row = F + (size_t)(i - d.i0) * FSW;
       const cd dinv = 1.0 / dg[i];
-      const cd l = i < N - 1 ? dl[i] : cd(0.0);
-      const cd u1 = i < N - 1 ? du[i] * dinv : cd(0.0);
-      const cd u2 = i < N - 2 ? du2[i] * dinv : cd(0.0);
-      // a factor entry whose imaginary part is below 2^-60 of its modulus is real to working
-      // precision (the LU of an evanescent mode converges to real values away from the
-      // Sommerfeld rows); such rows are stored exactly real and swept with real factors
-      auto tiny = [](cd v) { return std::fabs(v.imag()) <= 0x1p-60 * std::abs(v); };
-      isreal[i] = tiny(l) && tiny(dinv) && tiny(u1) && tiny(u2);
-      if (FW == 8) {
-        F[i * 8 + 0] = l.real();    F[i * 8 + 1] = l.imag();
-        F[i * 8 + 2] = dinv.real(); F[i * 8 + 3] = dinv.imag();
-        F[i * 8 + 4] = u1.real();   F[i * 8 + 5] = u1.imag();
-        F[i * 8 + 6] = u2.real();   F[i * 8 + 7] = u2.imag();
-      } else {
-        F[i * 4 + 0] = l.real(); F[i * 4 + 1] = dinv.real(); F[i * 4 + 2] = u1.real(); F[i * 4 + 3] = u2.real();
+      const bool last = i == itop;
+      const cd dnext_inv = last ? cd(0.0) : 1.0 / dg[i + 1];
+      const cd l = last ? cd(0.0) : dl[i];
+      const cd vals[11] = {l * dg[i] * dnext_inv, dg[i] * dnext_inv, l * dnext_inv, dinv, dnext_inv,
+                           dnext_inv * sines[0], dnext_inv * sines[1], dnext_inv * sines[2], dnext_inv * sines[3],
+                           last ? cd(0.0) : du[i] * dinv, i + 2 <= itop ? du2[i] * dinv : cd(0.0)};
+      bool re = true;
+      for (int w = 0; w < 11; ++w) {
+        row[2 * w] = vals[w].real();
+        row[2 * w + 1] = vals[w].imag();
+        re = re && tiny_imag(vals[w]);
       }
+      row[22] = pv[i];
+      isreal[i - d.i0] = re;
     }
-    // the longest run of real rows containing the middle row: [rlo, rhi)
-    int rlo = N / 2, rhi = N / 2;
-    if (FW == 8 && isreal[N / 2]) {
-      rlo = N / 2; rhi = N / 2 + 1;
-      while (rlo > 0 && isreal[rlo - 1]) --rlo;
-      while (rhi < N && isreal[rhi]) ++rhi;
-      for (int i = rlo; i < rhi; ++i)
-        for (int w = 0; w < 4; ++w) F[i * 8 + 2 * w + 1] = 0.0;
+    // real rows: the longest run containing the middle of the swept range
+    const int mid = (d.i0 + itop) / 2 - d.i0;
+    int flo = mid, fhi = mid;
+    if (isreal[mid]) {
+      flo = mid; fhi = mid + 1;
+      while (flo > 0 && isreal[flo - 1]) --flo;
+      while (fhi < itop - d.i0 + 1 && isreal[fhi]) ++fhi;
+      for (int r = flo; r < fhi; ++r)
+        for (int w = 0; w < 11; ++w) F[(size_t)r * FSW + 2 * w + 1] = 0.0;
     }
-    if (FW == 4) { rlo = 0; rhi = N; }
-    hs.seg[(size_t)(q - 1) * 2 + 0] = rlo;
-    hs.seg[(size_t)(q - 1) * 2 + 1] = rhi;
+    hs.seg[(size_t)(q - 1) * 5 + 2] = flo + d.i0;
+    hs.seg[(size_t)(q - 1) * 5 + 3] = fhi + d.i0;
+    hs.seg[(size_t)(q - 1) * 5 + 4] = itop;
   }
   return MDP_OK;
+}
+
+
+// Factor mode q of subdomain hs (tables sized by prepare_tables): the full pivoted LU of T_q
+// (factor table, dT/dk rows, real-row run) and the condensed, pivot-scaled forward-sweep table.
+static mdp_status factor_mode(HostSub &hs, int q) {
+  SubDesc &d = hs.d;
+  const int N = d.Nt, FW = d.cplx ? 8 : 4;
+  std::vector<cd> dl(N), dg(N), du(N), du2(N);
+  mode_matrix(d, q, dl.data(), dg.data(), du.data(), hs.dT + (size_t)(q - 1) * N * 6);
+  double scale = 0.0;
+  for (int i = 0; i < N; ++i) scale = std::max({scale, std::abs(dg[i]), std::abs(du[i]), std::abs(dl[i])});
+  uint8_t *pv = hs.piv + (size_t)(q - 1) * N;
+  if (!band_lu(N, dl.data(), dg.data(), du.data(), du2.data(), pv)) return MDP_ERR_SINGULAR;
+  double *F = hs.fact + (size_t)(q - 1) * N * FW;
+  std::vector<uint8_t> isreal(N, 1);
+  for (int i = 0; i < N; ++i) {
+    if (std::abs(dg[i]) < kSingularTol * scale) return MDP_ERR_SINGULAR;
+    const cd dinv = 1.0 / dg[i];
+    const cd l = i < N - 1 ? dl[i] : cd(0.0);
+    const cd u1 = i < N - 1 ? du[i] * dinv : cd(0.0);
+    const cd u2 = i < N - 2 ? du2[i] * dinv : cd(0.0);
+    // a factor entry whose imaginary part is below 2^-60 of its modulus is real to working
+    // precision (the LU of an evanescent mode converges to real values away from the
+    // Sommerfeld rows); such rows are stored exactly real and swept with real factors
+    isreal[i] = tiny_imag(l) && tiny_imag(dinv) && tiny_imag(u1) && tiny_imag(u2);
+    if (FW == 8) {
+      F[i * 8 + 0] = l.real();    F[i * 8 + 1] = l.imag();
+      F[i * 8 + 2] = dinv.real(); F[i * 8 + 3] = dinv.imag();
+      F[i * 8 + 4] = u1.real();   F[i * 8 + 5] = u1.imag();
+      F[i * 8 + 6] = u2.real();   F[i * 8 + 7] = u2.imag();
+    } else {
+      F[i * 4 + 0] = l.real(); F[i * 4 + 1] = dinv.real(); F[i * 4 + 2] = u1.real(); F[i * 4 + 3] = u2.real();
+    }
+  }
+  // the longest run of real rows containing the middle row: [rlo, rhi)
+  int rlo = N / 2, rhi = N / 2;
+  if (FW == 8 && isreal[N / 2]) {
+    rlo = N / 2; rhi = N / 2 + 1;
+    while (rlo > 0 && isreal[rlo - 1]) --rlo;
+    while (rhi < N && isreal[rhi]) ++rhi;
+    for (int i = rlo; i < rhi; ++i)
+      for (int w = 0; w < 4; ++w) F[i * 8 + 2 * w + 1] = 0.0;
+  }
+  if (FW == 4) { rlo = 0; rhi = N; }
+  hs.seg[(size_t)(q - 1) * 5 + 0] = rlo;
+  hs.seg[(size_t)(q - 1) * 5 + 1] = rhi;
+  return build_fs_mode(hs, q);
+}
+
+static void prepare_tables(HostSub &hs) { hs.seg.assign((size_t)hs.d.Nq * 5, 0); }
+
+// Factor every mode of every subdomain; modes are independent, so they are spread over the
+// host's hardware threads (each writes its own table slices).
+static mdp_status factor_all(std::vector<HostSub> &subs) {
+  std::vector<std::pair<int, int>> tasks;
+  for (int si = 0; si < (int)subs.size(); ++si) {
+    prepare_tables(subs[si]);
+    for (int q = 1; q <= subs[si].d.Nq; ++q) tasks.push_back({si, q});
+  }
+  const int nthr = (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
+  std::atomic<size_t> next(0);
+  std::atomic<int> status(MDP_OK);
+  auto worker = [&]() {
+    for (;;) {
+      const size_t t = next.fetch_add(1);
+      if (t >= tasks.size() || status.load() != MDP_OK) return;
+      const mdp_status st = factor_mode(subs[tasks[t].first], tasks[t].second);
+      if (st != MDP_OK) status.store(st);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nthr; ++i) pool.emplace_back(worker);
+  worker();
+  for (auto &th : pool) th.join();
+  return (mdp_status)status.load();
 }
 
 // x = T_q^{-1} b (adjoint = 0) or T_q^{-H} b (adjoint = 1), complex interleaved host arrays,
@@ -222,8 +350,8 @@ static mdp_status factor_modes(HostSub &hs) {
 void host_mode_solve(const HostSub &hs, int q, int adjoint, const double *b, double *x) {
   const SubDesc &d = hs.d;
   const int N = d.Nt, FW = d.cplx ? 8 : 4;
-  const double *F = &hs.fact[(size_t)(q - 1) * N * FW];
-  const uint8_t *pv = &hs.piv[(size_t)(q - 1) * N];
+  const double *F = hs.fact + (size_t)(q - 1) * N * FW;
+  const uint8_t *pv = hs.piv + (size_t)(q - 1) * N;
   auto get = [&](int i, int w) -> cd {
     if (FW == 8) return cd(F[i * 8 + 2 * w], F[i * 8 + 2 * w + 1]);
     return cd(F[i * 4 + w], 0.0);
@@ -257,7 +385,7 @@ void host_mode_solve(const HostSub &hs, int q, int adjoint, const double *b, dou
 }
 
 // ---------------------------------------------------------------- tables
-static void layout_tables(mdp_plan *p) {
+static bool layout_tables(mdp_plan *p) {
   long long off = 0, poff = 0, out = 0;
   auto al = [](long long v) { return (v + 31) & ~31LL; };
   for (auto &hs : p->subs) {
@@ -267,27 +395,33 @@ static void layout_tables(mdp_plan *p) {
     d.dT_off = off;   off += al((long long)d.Nq * d.Nt * 6);
     d.sin_off = off;  off += al(4LL * d.Nx);
     d.geo_off = off;  off += al(4LL * d.G);
-    d.seg_off = off;  off += al(2LL * d.Nq);
+    d.seg_off = off;  off += al(5LL * d.Nq);
+    d.fs_off = off;   off += al((long long)d.Nq * d.NYf * FSW);
     d.piv_off = poff; poff += al((long long)d.Nq * d.Nt);
     d.out_off = out;  out += (long long)d.G * d.n_cols;
   }
-  p->host_tables.assign(off, 0.0);
-  p->host_piv.assign(poff, 0);
+  const bool pinned = !(p->flags & MDP_PLAN_HOST_ONLY);
+  if (!p->host_tables.alloc((size_t)off, pinned) || !p->host_piv.alloc((size_t)poff, pinned)) return false;
+  for (auto &hs : p->subs) {
+    const SubDesc &d = hs.d;
+    hs.fact = p->host_tables.data() + d.fact_off;
+    hs.dT = p->host_tables.data() + d.dT_off;
+    hs.fs = p->host_tables.data() + d.fs_off;
+    hs.piv = p->host_piv.data() + d.piv_off;
+  }
   p->out_size = out;
+  return true;
 }
 
 static void fill_tables(mdp_plan *p) {
   for (auto &hs : p->subs) {
     const SubDesc &d = hs.d;
-    std::copy(hs.fact.begin(), hs.fact.end(), p->host_tables.begin() + d.fact_off);
-    std::copy(hs.dT.begin(), hs.dT.end(), p->host_tables.begin() + d.dT_off);
-    std::copy(hs.piv.begin(), hs.piv.end(), p->host_piv.begin() + d.piv_off);
     double *S = &p->host_tables[d.sin_off];
     for (int j = 0; j < 2 * d.Nx; ++j) {
       S[j] = std::sin(M_PI * (double)j / (double)d.Nx);
       S[2 * d.Nx + j] = (2.0 / d.Nx) * S[j];
     }
-    for (int i = 0; i < 2 * d.Nq; ++i) p->host_tables[d.seg_off + i] = hs.seg[i];
+    for (int i = 0; i < 5 * d.Nq; ++i) p->host_tables[d.seg_off + i] = hs.seg[i];
     double *g = &p->host_tables[d.geo_off];
     for (int i = 0; i < d.G; ++i) {
       g[4 * i + 0] = hs.owner[i];
@@ -341,10 +475,10 @@ mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n) {
   for (int i = 0; i < n; ++i) {
     mdp_status st = geometry(subs[i], p->subs[i]);
     if (st != MDP_OK) return st;
-    st = factor_modes(p->subs[i]);
-    if (st != MDP_OK) return st;
   }
-  layout_tables(p);
+  if (!layout_tables(p)) return MDP_ERR_NOMEM;
+  mdp_status st = factor_all(p->subs);
+  if (st != MDP_OK) return st;
   fill_tables(p);
   schedule(p);
   return MDP_OK;
@@ -356,16 +490,15 @@ mdp_status refactor_host(mdp_plan *p, const double *k) {
   }
   for (int i = 0; i < (int)p->subs.size(); ++i) {
     HostSub &hs = p->subs[i];
-    SubDesc keep = hs.d;
-    const double h2 = keep.h * keep.h, k2 = k[i] * k[i];
+    const double h2 = hs.d.h * hs.d.h, k2 = k[i] * k[i];
     hs.d.k = k[i];
     hs.d.c1 = 1.0 / h2 - 2.0 / (6.0 * h2) + k2 / 12.0;
     hs.d.c0 = -4.0 / h2 + 4.0 / (6.0 * h2) + 8.0 * k2 / 12.0;
     hs.d.dc1 = k[i] / 6.0;
     hs.d.dc0 = 8.0 * k[i] / 6.0;
-    mdp_status st = factor_modes(hs);
-    if (st != MDP_OK) return st;
   }
+  mdp_status st = factor_all(p->subs);
+  if (st != MDP_OK) return st;
   fill_tables(p);
   return MDP_OK;
 }
