@@ -588,12 +588,79 @@ __device__ __forceinline__ void inv_rows_body(const Item &it, const SubDesc &d, 
   if (d.xsym && d.Nx - m != m) write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, gidx(d.Nx - m), csub(e, o));
 }
 
+// The same rows by FFT: u(m) = (2/Nx) sum_q yhat(q) sin(pi q m/Nx) = (i/Nx) V[m], where V is the
+// length-2Nx DFT of the odd extension x~ = (0, yhat_1 .. yhat_{Nx-1}, 0, -yhat_{Nx-1} .. -yhat_1)
+// (V[m] = -2i sum_q yhat_q sin(pi q m/Nx)). Radix-2 decimation in time in shared memory: inputs
+// stored bit-reversed, log2(2Nx) butterfly stages, output in natural order. One block: one
+// gamma row and fpb = 4096/(2Nx) columns (64 KiB of complex values). Twiddles e^{-i pi j/Nx}
+// come from the sine table (cos(pi j/Nx) = sin(pi (j + Nx/2)/Nx)).
+template <bool CD, bool CIN>
+__device__ __forceinline__ void inv_rows_fft_body(const Item &it, const SubDesc &d, const double *tab,
+                                                  const double *ws, const double2 *xi_user, double2 *out, int kind,
+                                                  int local, double2 *sm) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int grow = local & 3, cblk = local >> 2;
+  const int b0 = cblk * d.fpb, nf = min(d.fpb, it.ncols - b0);
+  const int L = 2 * d.Nx, Nx = d.Nx;
+  int lg = 0;
+  while ((1 << lg) < L) ++lg;
+  const int n = grow == 0 ? d.nlo - 1 : grow == 1 ? d.nlo : grow == 2 ? d.nhi : d.nhi + 1;
+  const int yrow = n - (d.nlo - 1);
+  const double *y = ws + it.y_off;
+  const long long qstride = (long long)d.NYf * it.ncols;
+  auto brev = [&](int j) { return (int)(__brev((unsigned)j) >> (32 - lg)); };
+  // load the odd extension, bit-reversed
+  for (int idx = tid; idx < d.fpb * (Nx + 1); idx += nt) {
+    const int f = idx % d.fpb, q = idx / d.fpb;       // q = 0 .. Nx
+    double2 v = make_double2(0.0, 0.0);
+    if (q >= 1 && q <= Nx - 1 && f < nf) {
+      const long long o = (long long)(q - 1) * qstride + (long long)yrow * it.ncols + b0 + f;
+      v = CD ? *reinterpret_cast<const double2 *>(y + 2 * o) : make_double2(y[o], 0.0);
+    }
+    double2 *S = sm + (long long)f * L;
+    S[brev(q)] = v;
+    if (q >= 1 && q <= Nx - 1) S[brev(L - q)] = make_double2(-v.x, -v.y);
+  }
+  __syncthreads();
+  const double *sn = tab + d.sin_off;
+  for (int st = 0; st < lg; ++st) {
+    const int half = 1 << st, span = Nx / half;    // twiddle e^{-i pi j / half} = e^{-i pi (j span) / Nx}
+    for (int t = tid; t < d.fpb * (L / 2); t += nt) {
+      const int f = t / (L / 2), k = t % (L / 2);
+      const int j = k & (half - 1), i1 = ((k >> st) << (st + 1)) + j, i2 = i1 + half;
+      double2 *S = sm + (long long)f * L;
+      const int jj = j * span;
+      const double wr = sn[jj + Nx / 2], wi = -sn[jj];
+      const double2 a = S[i1], c = S[i2];
+      const double br = fma(wr, c.x, -wi * c.y), bi = fma(wr, c.y, wi * c.x);
+      S[i1] = make_double2(a.x + br, a.y + bi);
+      S[i2] = make_double2(a.x - br, a.y - bi);
+    }
+    __syncthreads();
+  }
+  const int W = d.Px + 2, Mr = d.Py - 2;
+  const double sc = 1.0 / Nx;
+  for (int idx = tid; idx < nf * W; idx += nt) {
+    const int f = idx / W, dm = idx % W, m = d.mlo - 1 + dm;
+    const double2 V = sm[(long long)f * L + m];
+    const cplx u = cmk(-V.y * sc, V.x * sc);   // (i/Nx) V
+    const int g = grow <= 1 ? grow * W + dm : 2 * W + 4 * Mr + (grow - 2) * W + dm;
+    write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b0 + f, g, u);
+  }
+}
+
 template <bool CIN>
 __global__ void __launch_bounds__(256) k_inv_rows(Batch bt, const SubDesc *subs, const double *tab, const double *ws,
                                                   const double2 *xi_user, double2 *out, int kind) {
+  extern __shared__ double2 fft_sm[];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
   const SubDesc &d = subs[it.sub];
+  if (d.rows_fft) {
+    if (d.cplx || CIN) inv_rows_fft_body<true, CIN>(it, d, tab, ws, xi_user, out, kind, local, fft_sm);
+    else inv_rows_fft_body<false, CIN>(it, d, tab, ws, xi_user, out, kind, local, fft_sm);
+    return;
+  }
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
   const int task = (local / cb) * 8 + threadIdx.y;
@@ -886,6 +953,14 @@ cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const doub
 
 // ---------------------------------------------------------------- launchers
 static inline dim3 grid1(int n) { return dim3((unsigned)n, 1, 1); }
+static constexpr int FFT_SMEM = 4096 * 16;  // bytes: fpb x 2Nx complex values
+
+// Dynamic shared memory above 48 KiB must be opted into per kernel on the current device.
+cudaError_t set_kernel_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_inv_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+  return e;
+}
 
 cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, double2 *out,
                            double2 *out_rec, cudaStream_t st) {
@@ -910,10 +985,10 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
   if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   else MDP_LAUNCH(F_TRI, k_tri<true, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   if (basis) {
-    MDP_LAUNCH(F_IROWS, k_inv_rows<false><<<grid1(fb[F_IROWS].total_blocks), b8, 0, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
+    MDP_LAUNCH(F_IROWS, k_inv_rows<false><<<grid1(fb[F_IROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
     MDP_LAUNCH(F_ICOLS, k_inv_cols<false><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
   } else {
-    MDP_LAUNCH(F_IROWS, k_inv_rows<true><<<grid1(fb[F_IROWS].total_blocks), b8, 0, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
+    MDP_LAUNCH(F_IROWS, k_inv_rows<true><<<grid1(fb[F_IROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
     MDP_LAUNCH(F_ICOLS, k_inv_cols<true><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
   }
   if (out_rec)

@@ -34,6 +34,9 @@ struct SubDesc {
   int Ph;           // xsym: pair units per dense ring row, Nx/2 - mlo + 1
   int R2;           // ring residual slots: R, or 8 Ph + 4 (Py - 4) with xsym
   int nrec;         // receiver row (nlo+1 .. nhi-1) or -1; receivers m = mlo+1 .. mhi-1
+  int rows_fft;     // inverse transform of the gamma rows by FFT (Nx a power of 2, 2Nx <= 4096)
+  int fpb;          // FFTs (columns) per block of that kernel: 4096 / (2 Nx)
+  int pad2;
   double h, k;
   double x0, x1, y0, y1, ax0, ay0;
   double c0, c1, c2;  // 9-point coefficients: centre, edge, corner (Eq. FD_scheme)
@@ -179,7 +182,9 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
     case F_RES: return cb * (((d.xsym ? 4 * d.Ph + 2 * (d.Py - 4) : d.R) + 7) / 8);
     case F_FROWS: return cb * ((d.Nx / 2 + 3) / 4);
     case F_TRI: return cb * ((d.Nq + 3) / 4);
-    case F_IROWS: return cb * (((d.xsym ? 4 * (d.Ph + 1) : 4 * (d.Px + 2)) + 7) / 8);
+    case F_IROWS:
+      if (d.rows_fft) return 4 * ((ncols + d.fpb - 1) / d.fpb);
+      return cb * (((d.xsym ? 4 * (d.Ph + 1) : 4 * (d.Px + 2)) + 7) / 8);
     case F_ICOLS: return cb * ((d.Py - 2 + 7) / 8);
     case F_AFWD: return cb * ((d.Nx / 2 + 3) / 4);
     case F_ATRI: return cb * ((d.Nq + 3) / 4);
@@ -211,6 +216,7 @@ void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long 
 void host_mode_solve(const HostSub &hs, int q, int adjoint, const double *b, double *x);
 // kernel launchers (kernels.cu)
 enum { PASS_FWD = 0, PASS_GRAD = 1 };
+cudaError_t set_kernel_attributes();
 cudaError_t launch_project(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,
                            double2 *out, double2 *out_rec, cudaStream_t st);
 cudaError_t launch_adjoint(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,

@@ -78,6 +78,8 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   d.Ph = d.xsym ? d.Nx / 2 - mlo + 1 : 0;
   d.R2 = d.xsym ? 8 * d.Ph + 4 * (d.Py - 4) : d.R;  // (sum, difference) per pair unit
   d.nrec = -1;
+  d.rows_fft = (d.Nx & (d.Nx - 1)) == 0 && 2 * d.Nx <= 4096 && d.Nx >= 8;
+  d.fpb = d.rows_fft ? 4096 / (2 * d.Nx) : 0;
   d.nfirst = d.cplx ? 0 : 1;
   d.Nt = d.cplx ? in.ny : in.ny - 2;
   d.i0 = (nlo - 1) - d.nfirst;
