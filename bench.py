@@ -148,7 +148,14 @@ def kernel_flops(plan, items):
             inv = 2
         add("k_tri", nc * Nq * tri)
         add("k_inv_cols", nc * (Py - 2) * Nq * (2 if xs else 4) * inv)
-        add("k_inv_rows", nc * 4 * ((Px // 2 + 2) if xs else (Px + 2)) * Nq * inv)
+        if (Nx & (Nx - 1)) == 0 and 8 <= Nx <= 2048:
+            # radix-2 FFT of length L = 2 Nx per dense row: two multiply-free stages (4 L flops),
+            # log2(L) - 2 stages of L/2 butterflies (complex multiply 6 + two complex adds 4)
+            L = 2 * Nx
+            lg = L.bit_length() - 1
+            add("k_inv_rows", nc * 4 * (4 * L + 5 * L * (lg - 2) + 2 * (Px + 2)))
+        else:
+            add("k_inv_rows", nc * 4 * ((Px // 2 + 2) if xs else (Px + 2)) * Nq * inv)
         add("k_fwd_rows", nc * (Nx // 2) * 4 * ((Px + 1) // 2 if xs else Px) * 2)
         add("k_residual", nc * R * 9 * 2)
     return tot
@@ -285,11 +292,14 @@ def run_ours(args, wl):
     peak = NOMINAL_FP64_GFLOPS / 1e3
     gpu_launches = sum(n for (_, n) in prof.values())
 
-    # end to end through the public API with host buffers: new wavenumbers from pinned host
-    # memory (host refactorisation + table upload), all columns, result read back to pinned host
+    # end to end through the public API with host buffers: new wavenumbers from host memory
+    # (every mode refactored on the GPU), all columns, result read back to pinned host memory
     host_out = torch.empty(plan.output_size, dtype=torch.complex128, pin_memory=True)
     ks = [s.k for s in subs]
     e2e_steps = max(3, min(args.steps, 10))
+    plan.update_k([k * (1.0 + 1e-9) for k in ks])    # untimed warm-up of the same step
+    plan.project(out=out)
+    host_out.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
@@ -299,10 +309,11 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     plan.update_k(ks)
-    table_bytes = int(plan.L.mdp_plan_table_bytes(plan.handle))
-    e2e = {"value": world * n_cols * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(table_bytes),
+    update_bytes = int(plan.L.mdp_plan_update_bytes(plan.handle))
+    e2e = {"value": world * n_cols * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": update_bytes,
            "d2h_bytes_per_step": int(plan.output_size * 16),
-           "what": "update_k (host LU of every mode + table upload) + project + D2H of all columns"}
+           "what": "update_k (new k up, every mode refactored on the GPU) + project + D2H of all columns "
+                   "to pinned host memory"}
 
     # the same step replayed as one CUDA graph (library graph mode)
     gplan = mdp.Plan(subs, tile_cols=tile, graph=True)

@@ -97,9 +97,16 @@ mdp_status mdp_ap_plan(const mdp_subdomain *subs, int n_subs, unsigned flags, md
 mdp_status mdp_ap_plan_ex(const mdp_subdomain *subs, int n_subs, unsigned flags, const mdp_plan_options *opt,
                           mdp_plan **out);
 
-/* Replace the wavenumbers (k[n_subs], host array) and refactor in place: same grids, no
- * reallocation. Synchronises the device. */
+/* Replace the wavenumbers (k[n_subs], host array, each > 0 and finite, else MDP_ERR_ARG) and
+ * refactor every sine mode in place (Section 3.2.1: the per-mode tridiagonal systems of the
+ * separable AP; same grids, no reallocation). On a device plan the factorisation runs on the
+ * GPU, on cuda_stream (NULL: the legacy default stream): the pivoted LU of each mode, its
+ * dT/dk rows and the projection's condensed sweep table are rebuilt in the device tables. The
+ * call returns when they are done; MDP_ERR_SINGULAR if a mode of the new k is singular (the
+ * tables are then unusable until a successful update). Host-only plans factor on the host.
+ * mdp_plan_update_k is mdp_plan_update_k_stream on the legacy default stream. */
 mdp_status mdp_plan_update_k(mdp_plan *p, const double *k);
+mdp_status mdp_plan_update_k_stream(mdp_plan *p, const double *k, void *cuda_stream);
 
 /* Layout of subdomain `sub` (host values): |gamma|, its 8*M* columns, the element offset
  * of its block in the output of mdp_project_batch, and a host pointer (owned by the plan,

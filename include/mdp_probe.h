@@ -33,9 +33,29 @@ const char *mdp_kernel_family_name(int family);
  * number of factor rows with complex entries swept by the projection, over all modes. */
 mdp_status mdp_plan_sub_info(const mdp_plan *p, int sub, int *info14);
 
-/* Bytes of the plan's host tables that mdp_plan_update_k uploads (factors, sweep tables, sines,
- * geometry, pivot flags). */
+/* Bytes of the plan's tables (factors, sweep tables, sines, geometry, pivot flags), uploaded at
+ * plan creation and rebuilt on the device by mdp_plan_update_k. */
 long long mdp_plan_table_bytes(const mdp_plan *p);
+
+/* Bytes that mdp_plan_update_k copies host -> device on a device plan (the subdomain
+ * descriptors with the new wavenumbers; the tables themselves are rebuilt on the device). */
+long long mdp_plan_update_bytes(const mdp_plan *p);
+
+/* Sizes of the plan's tables: doubles (factor, dT/dk, sine, segment, sweep and geometry tables)
+ * and pivot-flag bytes. */
+mdp_status mdp_plan_table_sizes(const mdp_plan *p, long long *n_doubles, long long *n_piv);
+
+/* Copy the tables into caller-owned host buffers of mdp_plan_table_sizes elements: the device
+ * copy (device_side = 1; MDP_ERR_STATE on a host-only plan) or the host copy (device_side = 0,
+ * rebuilt on the host for the current wavenumbers if the device has refactored since). Used to
+ * check the device factorisation against the host one. */
+mdp_status mdp_plan_read_tables(const mdp_plan *p, int device_side, double *tables, unsigned char *piv);
+
+/* Offsets of subdomain `sub`'s tables (7 values): in doubles into the tables, the factor rows
+ * [Nq][Nt][8 complex | 4 real AP], dT/dk rows [Nq][Nt][6], sines [4 Nx], segments [Nq][5],
+ * sweep rows [Nq][rows from i0][24], gamma geometry [|gamma|][4]; then in bytes into the pivot
+ * flags [Nq][Nt]. */
+mdp_status mdp_plan_table_offsets(const mdp_plan *p, int sub, long long *off7);
 
 #ifdef __cplusplus
 }

@@ -192,9 +192,28 @@ class Plan:
                                              _stream_ptr(stream)), "mdp_ap_solve_batch")
         return out
 
-    def update_k(self, ks):
+    def update_k(self, ks, stream=None):
+        """New wavenumbers: every mode is refactored (on the GPU for device plans, on `stream`,
+        default the current torch stream; the call returns when the tables are rebuilt)."""
         arr = (C.c_double * self.n_subs)(*[float(k) for k in ks])
-        _lib.check(self.L.mdp_plan_update_k(self.handle, arr), "mdp_plan_update_k")
+        st = None if self.host_only else _stream_ptr(stream)
+        _lib.check(self.L.mdp_plan_update_k_stream(self.handle, arr, st), "mdp_plan_update_k_stream")
+
+    def table_offsets(self, sub: int) -> dict:
+        a = (C.c_longlong * 7)()
+        _lib.check(self.L.mdp_plan_table_offsets(self.handle, sub, a), "mdp_plan_table_offsets")
+        return dict(zip(["fact", "dT", "sin", "seg", "fs", "geo", "piv"], list(a)))
+
+    def read_tables(self, device_side: bool):
+        """(tables float64, pivot flags uint8) numpy copies of the device or host tables."""
+        import numpy as np
+        nd, npv = C.c_longlong(), C.c_longlong()
+        _lib.check(self.L.mdp_plan_table_sizes(self.handle, C.byref(nd), C.byref(npv)), "mdp_plan_table_sizes")
+        tab = np.empty(nd.value, dtype=np.float64)
+        piv = np.empty(npv.value, dtype=np.uint8)
+        _lib.check(self.L.mdp_plan_read_tables(self.handle, int(device_side), tab.ctypes.data_as(C.c_void_p),
+                                               piv.ctypes.data_as(C.c_void_p)), "mdp_plan_read_tables")
+        return tab, piv
 
     def sub_info(self, sub: int) -> dict:
         a = (C.c_int * 14)()

@@ -53,6 +53,11 @@ def lib():
         "mdp_ap_plan": (i, [C.POINTER(mdp_subdomain), i, C.c_uint, C.POINTER(vp)]),
         "mdp_ap_plan_ex": (i, [C.POINTER(mdp_subdomain), i, C.c_uint, C.POINTER(mdp_plan_options), C.POINTER(vp)]),
         "mdp_plan_update_k": (i, [vp, C.POINTER(d)]),
+        "mdp_plan_update_k_stream": (i, [vp, C.POINTER(d), vp]),
+        "mdp_plan_table_sizes": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
+        "mdp_plan_update_bytes": (ll, [vp]),
+        "mdp_plan_read_tables": (i, [vp, i, vp, vp]),
+        "mdp_plan_table_offsets": (i, [vp, i, C.POINTER(ll)]),
         "mdp_plan_layout": (i, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(ll), C.POINTER(C.POINTER(i))]),
         "mdp_plan_output_size": (ll, [vp]),
         "mdp_project_batch": (i, [vp, vp, vp, i, vp]),

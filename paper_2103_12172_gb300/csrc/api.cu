@@ -33,6 +33,10 @@ void free_device(mdp_plan *p) {
   cudaFree(p->d_piv);
   cudaFree(p->d_ws);
   cudaFree(p->d_status);
+  cudaFree(p->d_fstatus);
+  p->d_fstatus = nullptr;
+  p->sub_stage.release();
+  p->h_fstatus.release();
   for (auto x : p->d_wave_items) cudaFree(x);
   for (auto x : p->d_wave_prefix) cudaFree(x);
   for (auto x : p->d_gwave_items) cudaFree(x);
@@ -61,9 +65,11 @@ mdp_status alloc_device(mdp_plan *p) {
   if (!al((void **)&p->d_subs, p->subs.size() * sizeof(SubDesc)) ||
       !al((void **)&p->d_tables, p->host_tables.size() * sizeof(double)) ||
       !al((void **)&p->d_piv, p->host_piv.size()) || !al((void **)&p->d_ws, (size_t)p->ws_doubles * 8) ||
-      !al((void **)&p->d_status, sizeof(int)))
+      !al((void **)&p->d_status, sizeof(int)) || !al((void **)&p->d_fstatus, sizeof(int)) ||
+      !p->sub_stage.alloc(p->subs.size(), true) || !p->h_fstatus.alloc(1, true))
     return MDP_ERR_NOMEM;
   CK(cudaMemset(p->d_status, 0, sizeof(int)));
+  CK(cudaMemset(p->d_fstatus, 0, sizeof(int)));
   mdp_status st = upload_subs_tables(p);
   if (st != MDP_OK) return st;
   for (int pass = 0; pass < 2; ++pass) {
@@ -199,15 +205,72 @@ mdp_status mdp_ap_plan_ex(const mdp_subdomain *subs, int n_subs, unsigned flags,
   return MDP_OK;
 }
 
-mdp_status mdp_plan_update_k(mdp_plan *p, const double *k) {
+mdp_status mdp_plan_update_k(mdp_plan *p, const double *k) { return mdp_plan_update_k_stream(p, k, nullptr); }
+
+// Device plans factor on the GPU: the descriptors (new k, stencil coefficients) go up through a
+// pinned stage, then one kernel rebuilds every factor, dT/dk and sweep table in place. The host
+// copies of the tables are refreshed only when host introspection asks for them.
+mdp_status mdp_plan_update_k_stream(mdp_plan *p, const double *k, void *cuda_stream) {
   if (!p || !k) return MDP_ERR_ARG;
-  mdp_status st = refactor_host(p, k);
+  if (!device_ok(p)) return refactor_host(p, k);
+  mdp_status st = set_k_fields(p, k);
   if (st != MDP_OK) return st;
-  if (device_ok(p)) {
+  CK(cudaSetDevice(p->device));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  CK(cudaStreamSynchronize(s));   // the stage may still feed an upload of an earlier call
+  for (size_t i = 0; i < p->subs.size(); ++i) p->sub_stage[i] = p->subs[i].d;
+  CK(cudaMemcpyAsync(p->d_subs, p->sub_stage.data(), p->subs.size() * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(p->d_fstatus, 0, sizeof(int), s));
+  CK(launch_factor(p, p->d_fstatus, s));
+  CK(cudaMemcpyAsync(p->h_fstatus.data(), p->d_fstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  p->host_stale = true;
+  return (mdp_status)p->h_fstatus[0];
+}
+
+// The host tables are a cache of the device ones for introspection: rebuilt for the current
+// wavenumbers after a device refactor.
+static mdp_status ensure_host_tables(const mdp_plan *cp) {
+  mdp_plan *p = const_cast<mdp_plan *>(cp);
+  if (!p->host_stale) return MDP_OK;
+  std::vector<double> k;
+  for (auto &hs : p->subs) k.push_back(hs.d.k);
+  const mdp_status st = refactor_host(p, k.data());
+  if (st == MDP_OK) p->host_stale = false;
+  return st;
+}
+
+long long mdp_plan_update_bytes(const mdp_plan *p) { return p ? (long long)(p->subs.size() * sizeof(SubDesc)) : 0; }
+
+mdp_status mdp_plan_table_sizes(const mdp_plan *p, long long *n_doubles, long long *n_piv) {
+  if (!p) return MDP_ERR_ARG;
+  if (n_doubles) *n_doubles = (long long)p->host_tables.size();
+  if (n_piv) *n_piv = (long long)p->host_piv.size();
+  return MDP_OK;
+}
+
+mdp_status mdp_plan_table_offsets(const mdp_plan *p, int sub, long long *off) {
+  if (!p || !off || sub < 0 || sub >= p->n_subs) return MDP_ERR_ARG;
+  const SubDesc &d = p->subs[sub].d;
+  off[0] = d.fact_off; off[1] = d.dT_off; off[2] = d.sin_off; off[3] = d.seg_off;
+  off[4] = d.fs_off; off[5] = d.geo_off; off[6] = d.piv_off;
+  return MDP_OK;
+}
+
+mdp_status mdp_plan_read_tables(const mdp_plan *p, int device_side, double *tables, unsigned char *piv) {
+  if (!p || !tables || !piv || (device_side != 0 && device_side != 1)) return MDP_ERR_ARG;
+  if (device_side) {
+    if (!device_ok(p)) return MDP_ERR_STATE;
     CK(cudaSetDevice(p->device));
     CK(cudaDeviceSynchronize());
-    return upload_subs_tables(p);
+    CK(cudaMemcpy(tables, p->d_tables, p->host_tables.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(piv, p->d_piv, p->host_piv.size(), cudaMemcpyDeviceToHost));
+    return MDP_OK;
   }
+  const mdp_status st = ensure_host_tables(p);
+  if (st != MDP_OK) return st;
+  std::memcpy(tables, p->host_tables.data(), p->host_tables.size() * sizeof(double));
+  std::memcpy(piv, p->host_piv.data(), p->host_piv.size());
   return MDP_OK;
 }
 
@@ -373,6 +436,8 @@ mdp_status mdp_host_mode_solve(const mdp_plan *p, int sub, int q, int adjoint, c
   if (!p || sub < 0 || sub >= p->n_subs || !b || !x || (adjoint != 0 && adjoint != 1)) return MDP_ERR_ARG;
   const HostSub &hs = p->subs[sub];
   if (q < 1 || q > hs.d.Nq) return MDP_ERR_ARG;
+  const mdp_status st = ensure_host_tables(p);
+  if (st != MDP_OK) return st;
   host_mode_solve(hs, q, adjoint, (const double *)b, (double *)x);
   return MDP_OK;
 }
@@ -463,6 +528,8 @@ const char *mdp_kernel_family_name(int family) { return fam_name(family); }
 
 mdp_status mdp_plan_sub_info(const mdp_plan *p, int sub, int *info) {
   if (!p || !info || sub < 0 || sub >= p->n_subs) return MDP_ERR_ARG;
+  const mdp_status st = ensure_host_tables(p);
+  if (st != MDP_OK) return st;
   const HostSub &hs = p->subs[sub];
   const SubDesc &d = hs.d;
   int npiv = 0;

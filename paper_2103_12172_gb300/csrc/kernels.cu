@@ -446,6 +446,8 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
     for (int s_ = 0; s_ < 4; ++s_) v = caxpy(row[10 + 2 * s_], rv(ri + s_), v);
     return v;
   };
+  // the swap flag (0.0 or 1.0) tested on its bits: an integer compare, not an FP64-pipe DSETP
+  auto swapped = [](const double *row) { return __double_as_longlong(row[22]) != 0; };
   // ---- forward sweep
   cplx ct = cmk(0.0, 0.0);
   int i = d.i0;
@@ -453,7 +455,7 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
     for (; i < min(frlo, itop); ++i) {
       const double *row = T + (long long)(i - d.i0) * FSW;
       const int n = i + 1 + d.nfirst;
-      if (row[22] == 0.0) { ystore(i, ct); ct = cfms(ghat_c(row, n), ld2(row), ct); }
+      if (!swapped(row)) { ystore(i, ct); ct = cfms(ghat_c(row, n), ld2(row), ct); }
       else {
         const cplx g = graw(n);
         ystore(i, cmul(ld2(row + 6), g));
@@ -467,7 +469,7 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
       for (; i < e; ++i) {
         const double *row = T + (long long)(i - d.i0) * FSW;
         const int n = i + 1 + d.nfirst;
-        if (row[22] == 0.0) { ystore(i, ct); ct.re = fma(-row[0], ct.re, ghat_r(row, n).re); }
+        if (!swapped(row)) { ystore(i, ct); ct.re = fma(-row[0], ct.re, ghat_r(row, n).re); }
         else {
           const double g = graw(n).re;
           ystore(i, cmk(row[6] * g, 0.0));
@@ -478,7 +480,7 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
       for (; i < e; ++i) {
         const double *row = T + (long long)(i - d.i0) * FSW;
         const int n = i + 1 + d.nfirst;
-        if (row[22] == 0.0) { ystore(i, ct); ct = caxpy(-row[0], ct, ghat_r(row, n)); }
+        if (!swapped(row)) { ystore(i, ct); ct = caxpy(-row[0], ct, ghat_r(row, n)); }
         else {
           const cplx g = graw(n);
           ystore(i, cmk(row[6] * g.re, row[6] * g.im));
@@ -491,7 +493,7 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
     for (; i < itop; ++i) {
       const double *row = T + (long long)(i - d.i0) * FSW;
       const int n = i + 1 + d.nfirst;
-      if (row[22] == 0.0) { ystore(i, ct); ct = cfms(ghat_c(row, n), ld2(row), ct); }
+      if (!swapped(row)) { ystore(i, ct); ct = cfms(ghat_c(row, n), ld2(row), ct); }
       else {
         const cplx g = graw(n);
         ystore(i, cmul(ld2(row + 6), g));
@@ -509,10 +511,10 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
     cplx x;
     if (!CD || (i >= frlo && i < frhi)) {
       x = cmk(fma(-row[18], x1.re, yi.re), CD ? fma(-row[18], x1.im, yi.im) : 0.0);
-      if (row[22] != 0.0) { x.re = fma(-row[20], x2.re, x.re); if (CD) x.im = fma(-row[20], x2.im, x.im); }
+      if (swapped(row)) { x.re = fma(-row[20], x2.re, x.re); if (CD) x.im = fma(-row[20], x2.im, x.im); }
     } else {
       x = cfms(yi, ld2(row + 18), x1);
-      if (row[22] != 0.0) x = cfms(x, ld2(row + 20), x2);
+      if (swapped(row)) x = cfms(x, ld2(row + 20), x2);
     }
     if (i <= ikeep) ystore(i, x);
     x2 = x1; x1 = x;
@@ -520,7 +522,7 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
 }
 
 template <bool CIN, bool FULL>
-__global__ void __launch_bounds__(128) k_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
+__global__ void __launch_bounds__(128, 8) k_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
                                              double *ws) {
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
@@ -608,7 +610,7 @@ __device__ __forceinline__ void inv_rows_fft_body(const Item &it, const SubDesc 
   const int yrow = n - (d.nlo - 1);
   const double *y = ws + it.y_off;
   const long long qstride = (long long)d.NYf * it.ncols;
-  auto brev = [&](int j) { return (int)(__brev((unsigned)j) >> (32 - lg)); };
+  auto brev = [&](int j) { return brev_lg(j, lg); };
   // load the odd extension, bit-reversed
   for (int idx = tid; idx < d.fpb * (Nx + 1); idx += nt) {
     const int f = idx % d.fpb, q = idx / d.fpb;       // q = 0 .. Nx
@@ -622,22 +624,7 @@ __device__ __forceinline__ void inv_rows_fft_body(const Item &it, const SubDesc 
     if (q >= 1 && q <= Nx - 1) S[brev(L - q)] = make_double2(-v.x, -v.y);
   }
   __syncthreads();
-  const double *sn = tab + d.sin_off;
-  for (int st = 0; st < lg; ++st) {
-    const int half = 1 << st, span = Nx / half;    // twiddle e^{-i pi j / half} = e^{-i pi (j span) / Nx}
-    for (int t = tid; t < d.fpb * (L / 2); t += nt) {
-      const int f = t / (L / 2), k = t % (L / 2);
-      const int j = k & (half - 1), i1 = ((k >> st) << (st + 1)) + j, i2 = i1 + half;
-      double2 *S = sm + (long long)f * L;
-      const int jj = j * span;
-      const double wr = sn[jj + Nx / 2], wi = -sn[jj];
-      const double2 a = S[i1], c = S[i2];
-      const double br = fma(wr, c.x, -wi * c.y), bi = fma(wr, c.y, wi * c.x);
-      S[i1] = make_double2(a.x + br, a.y + bi);
-      S[i2] = make_double2(a.x - br, a.y - bi);
-    }
-    __syncthreads();
-  }
+  fft_r2_stages(sm, d.fpb, Nx, lg, tab + d.sin_off);
   const int W = d.Px + 2, Mr = d.Py - 2;
   const double sc = 1.0 / Nx;
   for (int idx = tid; idx < nf * W; idx += nt) {
@@ -953,12 +940,13 @@ cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const doub
 
 // ---------------------------------------------------------------- launchers
 static inline dim3 grid1(int n) { return dim3((unsigned)n, 1, 1); }
-static constexpr int FFT_SMEM = 4096 * 16;  // bytes: fpb x 2Nx complex values
+static constexpr int FFT_SMEM = FFT_POINTS * 16;  // bytes: fpb x 2Nx complex values
 
 // Dynamic shared memory above 48 KiB must be opted into per kernel on the current device.
 cudaError_t set_kernel_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_inv_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+  if (e == cudaSuccess) e = set_adj_kernel_attributes();
   return e;
 }
 

@@ -15,16 +15,62 @@
 namespace mdp {
 
 static inline dim3 g1(int n) { return dim3((unsigned)n, 1, 1); }
+static constexpr int FFT_SMEM_ADJ = FFT_POINTS * 16;  // bytes of dynamic shared memory of the FFT kernels
 
-// yhat(q, row) of the 4 full gamma rows of the cotangent (mode pair (q, Nx - q) per thread)
-__global__ void __launch_bounds__(128) k_adj_rows(Batch bt, const SubDesc *subs, const double *tab, double *ws,
+
+// yhat(q, row) = sum_m c(m) sin(pi q m / Nx) of the 4 full gamma rows of the cotangent (and
+// the receiver row): by FFT where the plan allows it (Nx a power of 2), else a direct sum.
+//
+// FFT form: with the odd extension x~(m) = c(m), x~(2Nx - m) = -c(m) (zero at 0 and Nx), the
+// length-2Nx DFT is V[q] = -2i sum_m c(m) sin(pi q m / Nx), so yhat(q) = (i/2) V[q]. One block:
+// one row and fpb columns.
+__device__ __forceinline__ void adj_rows_fft(const Item &it, const SubDesc &d, const double *tab, double *ws,
+                                             const double2 *cot, const double2 *cot_rec, int local, double2 *sm) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int rr = local % 5, cblk = local / 5;
+  if (rr == 4 && !(cot_rec && d.nrec >= 0)) return;   // uniform over the block
+  const int b0 = cblk * d.fpb, nf = min(d.fpb, it.ncols - b0);
+  const int Nx = d.Nx, L = 2 * Nx;
+  int lg = 0;
+  while ((1 << lg) < L) ++lg;
+  const int W = d.Px + 2, M4 = 4 * (d.Py - 2);
+  // the row's values c(m) for m in [m0, m0 + cnt), column f at src(f) + (m - m0)
+  const int m0 = rr == 4 ? d.mlo + 1 : d.mlo - 1, cnt = rr == 4 ? d.Px - 2 : W;
+  const int g0 = rr == 0 ? 0 : rr == 1 ? W : rr == 2 ? 2 * W + M4 : 3 * W + M4;
+  auto src = [&](int f) -> const double2 * {
+    return rr == 4 ? cot_rec + d.rec_off + (long long)(it.col0 + b0 + f) * (d.Px - 2)
+                   : cot + it.io_off + (long long)(b0 + f) * d.G + g0;
+  };
+  for (int idx = tid; idx < d.fpb * L; idx += nt) {
+    const int f = idx >> lg, n = idx & (L - 1);
+    double2 v = make_double2(0.0, 0.0);
+    if (f < nf) {
+      if (n >= m0 && n < m0 + cnt) v = src(f)[n - m0];
+      else if (L - n >= m0 && L - n < m0 + cnt) { const double2 w = src(f)[L - n - m0]; v = make_double2(-w.x, -w.y); }
+    }
+    sm[(f << lg) + brev_lg(n, lg)] = v;
+  }
+  __syncthreads();
+  fft_r2_stages(sm, d.fpb, Nx, lg, tab + d.sin_off);
+  double *gr = ws + it.gr_off;
+  for (int idx = tid; idx < nf * d.Nq; idx += nt) {
+    const int f = idx % nf, q = idx / nf + 1;
+    const double2 V = sm[(f << lg) + q];
+    st2(gr + 2 * (((long long)rr * d.Nq + (q - 1)) * it.ncols + b0 + f), cmk(-0.5 * V.y, 0.5 * V.x));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_adj_rows(Batch bt, const SubDesc *subs, const double *tab, double *ws,
                                                   const double2 *cot, const double2 *cot_rec) {
+  extern __shared__ double2 fft_sm[];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
   const SubDesc &d = subs[it.sub];
+  if (d.rows_fft) { adj_rows_fft(it, d, tab, ws, cot, cot_rec, local, fft_sm); return; }
+  // direct: mode pair (q, Nx - q) per thread
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
-  const int q = (local / cb) * 4 + threadIdx.y + 1;
+  const int q = (local / cb) * 8 + threadIdx.y + 1;
   if (b >= it.ncols || q > d.Nx / 2) return;
   const double *S = tab + d.sin_off;
   const int N2 = 2 * d.Nx, W = d.Px + 2, M4 = 4 * (d.Py - 2);
@@ -96,14 +142,37 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
     v = caxpy(sg3, cmk(ct[g0 + 3].x, ct[g0 + 3].y), v);
     return v;
   };
+  // Factor rows [rlo, rhi) of a complex mode are exactly real (plan: factor_mode); there the
+  // products with the factors are real x complex.
+  int rlo = 0, rhi = d.Nt;
+  if (CF) {
+    const double *sg = tab + d.seg_off + 5 * (q - 1);
+    rlo = (int)sg[0];
+    rhi = (int)sg[1];
+  }
+  auto fr = [&](int i, int w) -> double { return F[i * FW + (CF ? 2 * w : w)]; };
   // U^H zt = yhat, zt_i = conj(d_i) z_i, from the first nonzero row (i0) up
   cplx t1 = cmk(0.0, 0.0), t2 = cmk(0.0, 0.0);
-  for (int i = d.i0; i < d.Nt; ++i) {
+  auto fstep_c = [&](int i) {
     cplx v = rhs(i + d.nfirst);
     if (i - 1 >= d.i0) v = cfms(v, cconj(fl(i - 1, 2)), t1);
     if (i - 2 >= d.i0 && pv[i - 2]) v = cfms(v, cconj(fl(i - 2, 3)), t2);
     st2(aptr(i), cmul(cconj(fl(i, 1)), v));
     t2 = t1; t1 = v;
+  };
+  auto fstep_r = [&](int i) {   // rows i-2, i-1, i real
+    cplx v = rhs(i + d.nfirst);
+    if (i - 1 >= d.i0) v = caxpy(-fr(i - 1, 2), t1, v);
+    if (i - 2 >= d.i0 && pv[i - 2]) v = caxpy(-fr(i - 2, 3), t2, v);
+    const double di = fr(i, 1);
+    st2(aptr(i), cmk(di * v.re, di * v.im));
+    t2 = t1; t1 = v;
+  };
+  {
+    int i = d.i0;
+    if (CF) for (const int e = min(max(rlo + 2, i), d.Nt); i < e; ++i) fstep_c(i);
+    for (const int e = CF ? max(rhi, i) : d.Nt; i < e; ++i) fstep_r(i);
+    for (; i < d.Nt; ++i) fstep_c(i);
   }
   // z = P_0 E_0^H ... P_{N-2} E_{N-2}^H z; position i+1 is final after step i
   const double *dT = tab + d.dT_off + (long long)(q - 1) * d.Nt * 6;
@@ -113,34 +182,56 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
     if (i < 0 || i >= d.Nt) return cmk(0.0, 0.0);
     return ld2(y + 2 * (ybase + (long long)i * nc));
   };
-  double dk = 0.0;
+  // Re <muhat, T_q' uhat>: T_q' is (da, ddk, da) with real constants on rows 1 .. Nt-2 (the
+  // k-derivatives of the interior coefficients), so those rows accumulate
+  // s_off = sum Re conj(mu_j)(u_{j-1} + u_{j+1}) and s_dg = sum Re conj(mu_j) u_j; the two end
+  // rows (Sommerfeld or Dirichlet) take their tabulated entries.
+  double dk = 0.0, s_off = 0.0, s_dg = 0.0;
   cplx uj1 = cmk(0.0, 0.0), uj = DK ? uhat(d.Nt - 1) : cmk(0.0, 0.0);
   const int jlo = d.nlo - d.nfirst, jhi = d.nhi - d.nfirst;
   auto emit = [&](int j, cplx mu) {
     if (DK) {
       const cplx ujm = uhat(j - 1);
-      const double *t = dT + 6 * j;
-      cplx v = cmul(ld2(t), ujm);
-      v = cadd(v, cmul(ld2(t + 2), uj));
-      v = cadd(v, cmul(ld2(t + 4), uj1));
-      dk = fma(mu.re, v.re, fma(mu.im, v.im, dk));
+      if (j == 0 || j == d.Nt - 1) {
+        const double *t = dT + 6 * j;
+        cplx v = cmul(ld2(t), ujm);
+        v = cadd(v, cmul(ld2(t + 2), uj));
+        v = cadd(v, cmul(ld2(t + 4), uj1));
+        dk = fma(mu.re, v.re, fma(mu.im, v.im, dk));
+      } else {
+        s_off = fma(mu.re, ujm.re + uj1.re, fma(mu.im, ujm.im + uj1.im, s_off));
+        s_dg = fma(mu.re, uj.re, fma(mu.im, uj.im, s_dg));
+      }
       uj1 = uj; uj = ujm;
     }
     if (j >= jlo && j <= jhi) st2(aptr(j), mu);
   };
   cplx up = ld2(aptr(d.Nt - 1));
-  for (int i = d.Nt - 2; i >= 0; --i) {
+  auto bstep_c = [&](int i) {
     const cplx zi0 = i >= d.i0 ? ld2(aptr(i)) : cmk(0.0, 0.0);
     const cplx zi = cfms(zi0, cconj(fl(i, 0)), up);
     if (pv[i]) emit(i + 1, zi);
     else { emit(i + 1, up); up = zi; }
+  };
+  auto bstep_r = [&](int i) {
+    const cplx zi0 = i >= d.i0 ? ld2(aptr(i)) : cmk(0.0, 0.0);
+    const cplx zi = caxpy(-fr(i, 0), up, zi0);
+    if (pv[i]) emit(i + 1, zi);
+    else { emit(i + 1, up); up = zi; }
+  };
+  {
+    int i = d.Nt - 2;
+    if (CF) for (; i >= rhi; --i) bstep_c(i);
+    for (const int e = CF ? rlo : 0; i >= e; --i) bstep_r(i);
+    for (; i >= 0; --i) bstep_c(i);
   }
   emit(0, up);
+  if (DK && d.Nt >= 3) dk = fma(dT[6 + 0], s_off, fma(dT[6 + 2], s_dg, dk));
   return dk;
 }
 
 template <bool DK>
-__global__ void __launch_bounds__(128) k_adj_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
+__global__ void __launch_bounds__(128, 7) k_adj_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
                                                  double *ws, const double2 *cot, int has_rec) {
   __shared__ double sh[128];
   Item it; int local;
@@ -159,40 +250,90 @@ __global__ void __launch_bounds__(128) k_adj_tri(Batch bt, const SubDesc *subs, 
   }
 }
 
-// mu on the 4 full ring rows (into the r buffer, complex [R][b]); DK: -Re <mu, s>
+// mu on the 4 full ring rows (into the r buffer, complex [R][b]); DK: -Re <mu, s>.
+// FFT form (as for the forward path's gamma rows): mu(m) = (2/Nx) sum_q muhat_q sin(pi q m/Nx)
+// = (i/Nx) V[m], V the length-2Nx DFT of the odd extension of muhat. One block: one ring row and
+// fpb columns.
+template <bool DK>
+__device__ __forceinline__ double adj_ring_rows_fft(const Item &it, const SubDesc &d, const double *tab, double *ws,
+                                                    int local, double2 *sm) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int rr = local & 3, cblk = local >> 2;
+  const int b0 = cblk * d.fpb, nf = min(d.fpb, it.ncols - b0);
+  const int Nx = d.Nx, L = 2 * Nx;
+  int lg = 0;
+  while ((1 << lg) < L) ++lg;
+  const int P = d.Px, Mr = 4 * (d.Py - 4);
+  const int n = rr == 0 ? d.nlo : rr == 1 ? d.nlo + 1 : rr == 2 ? d.nhi - 1 : d.nhi;
+  const int j = n - d.nfirst;
+  const double *a = ws + it.a_off;
+  const long long qstride = (long long)d.Nt * it.ncols;
+  for (int idx = tid; idx < d.fpb * (Nx + 1); idx += nt) {
+    const int f = idx % d.fpb, q = idx / d.fpb;   // q = 0 .. Nx
+    double2 v = make_double2(0.0, 0.0);
+    if (q >= 1 && q <= Nx - 1 && f < nf)
+      v = *reinterpret_cast<const double2 *>(a + 2 * ((long long)(q - 1) * qstride + (long long)j * it.ncols + b0 + f));
+    double2 *S = sm + (f << lg);
+    S[brev_lg(q, lg)] = v;
+    if (q >= 1 && q <= Nx - 1) S[brev_lg(L - q, lg)] = make_double2(-v.x, -v.y);
+  }
+  __syncthreads();
+  fft_r2_stages(sm, d.fpb, Nx, lg, tab + d.sin_off);
+  const int rb = rr == 0 ? 0 : rr == 1 ? P : rr == 2 ? 2 * P + Mr : 3 * P + Mr;
+  const double sc = 1.0 / Nx;
+  double dk = 0.0;
+  for (int idx = tid; idx < nf * P; idx += nt) {
+    const int f = idx % nf, dm = idx / nf;
+    const double2 V = sm[(f << lg) + d.mlo + dm];
+    const cplx acc = cmk(-V.y * sc, V.x * sc);
+    const long long o = (long long)(rb + dm) * it.ncols + b0 + f;
+    st2(ws + it.r_off + 2 * o, acc);
+    if (DK) {
+      const cplx s = ld2(ws + it.s_off + 2 * o);
+      dk -= acc.re * s.re + acc.im * s.im;
+    }
+  }
+  return dk;
+}
+
 template <bool DK>
 __global__ void __launch_bounds__(256) k_adj_ring_rows(Batch bt, const SubDesc *subs, const double *tab, double *ws) {
+  extern __shared__ double2 fft_sm[];
   __shared__ double sh[256];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
   const SubDesc &d = subs[it.sub];
-  const int cb = (it.ncols + 31) >> 5;
-  const int b = (local % cb) * 32 + threadIdx.x;
-  const int task = (local / cb) * 8 + threadIdx.y;
-  const int P = d.Px, Mr = 4 * (d.Py - 4);
   double dk = 0.0;
-  if (b < it.ncols && task < 4 * P) {
-    const int rr = task / P, m = d.mlo + task % P;
-    const int n = rr == 0 ? d.nlo : rr == 1 ? d.nlo + 1 : rr == 2 ? d.nhi - 1 : d.nhi;
-    const int j = n - d.nfirst;
-    const double *Si = tab + d.sin_off + 2 * d.Nx;
-    const int N2 = 2 * d.Nx;
-    const double *a = ws + it.a_off;
-    const long long qstride = (long long)d.Nt * it.ncols;
-    const long long base = (long long)j * it.ncols + b;
-    cplx acc = cmk(0.0, 0.0);
-    int jj = m % N2;
-    for (int q = 1; q <= d.Nq; ++q) {
-      acc = caxpy(Si[jj], ld2(a + 2 * (base + (long long)(q - 1) * qstride)), acc);
-      jj += m;
-      if (jj >= N2) jj -= N2;
-    }
-    const int rb = rr == 0 ? 0 : rr == 1 ? P : rr == 2 ? 2 * P + Mr : 3 * P + Mr;
-    const long long o = (long long)(rb + m - d.mlo) * it.ncols + b;
-    st2(ws + it.r_off + 2 * o, acc);
-    if (DK) {
-      const cplx s = ld2(ws + it.s_off + 2 * o);
-      dk = -(acc.re * s.re + acc.im * s.im);
+  if (d.rows_fft) {
+    dk = adj_ring_rows_fft<DK>(it, d, tab, ws, local, fft_sm);
+  } else {
+    const int cb = (it.ncols + 31) >> 5;
+    const int b = (local % cb) * 32 + threadIdx.x;
+    const int task = (local / cb) * 8 + threadIdx.y;
+    const int P = d.Px, Mr = 4 * (d.Py - 4);
+    if (b < it.ncols && task < 4 * P) {
+      const int rr = task / P, m = d.mlo + task % P;
+      const int n = rr == 0 ? d.nlo : rr == 1 ? d.nlo + 1 : rr == 2 ? d.nhi - 1 : d.nhi;
+      const int j = n - d.nfirst;
+      const double *Si = tab + d.sin_off + 2 * d.Nx;
+      const int N2 = 2 * d.Nx;
+      const double *a = ws + it.a_off;
+      const long long qstride = (long long)d.Nt * it.ncols;
+      const long long base = (long long)j * it.ncols + b;
+      cplx acc = cmk(0.0, 0.0);
+      int jj = m % N2;
+      for (int q = 1; q <= d.Nq; ++q) {
+        acc = caxpy(Si[jj], ld2(a + 2 * (base + (long long)(q - 1) * qstride)), acc);
+        jj += m;
+        if (jj >= N2) jj -= N2;
+      }
+      const int rb = rr == 0 ? 0 : rr == 1 ? P : rr == 2 ? 2 * P + Mr : 3 * P + Mr;
+      const long long o = (long long)(rb + m - d.mlo) * it.ncols + b;
+      st2(ws + it.r_off + 2 * o, acc);
+      if (DK) {
+        const cplx s = ld2(ws + it.s_off + 2 * o);
+        dk = -(acc.re * s.re + acc.im * s.im);
+      }
     }
   }
   if (DK) {
@@ -224,13 +365,36 @@ __global__ void __launch_bounds__(256) k_adj_ring_cols(Batch bt, const SubDesc *
     const long long qstride = (long long)d.Nt * it.ncols;
     const long long base = (long long)j * it.ncols + b;
     cplx acc[4] = {cmk(0, 0), cmk(0, 0), cmk(0, 0), cmk(0, 0)};
-    for (int q = 1; q <= d.Nq; ++q) {
-      const cplx v = ld2(a + 2 * (base + (long long)(q - 1) * qstride));
+    if (d.xsym) {
+      // mhi = Nx - mlo: sin(pi q (Nx - m)/Nx) = sin(pi q m/Nx) for odd q and its negative for
+      // even q, so odd-q and even-q partial sums at mlo, mlo+1 give all four columns
+      cplx e0 = cmk(0, 0), o0 = cmk(0, 0), e1 = cmk(0, 0), o1 = cmk(0, 0);
+      int q = 1;
+      for (; q + 1 <= d.Nq; q += 2) {
+        const cplx va = ld2(a + 2 * (base + (long long)(q - 1) * qstride));
+        const cplx vb = ld2(a + 2 * (base + (long long)q * qstride));
+        e0 = caxpy(Si[jj[0]], va, e0); e1 = caxpy(Si[jj[1]], va, e1);
+        jj[0] += ms[0]; if (jj[0] >= N2) jj[0] -= N2;
+        jj[1] += ms[1]; if (jj[1] >= N2) jj[1] -= N2;
+        o0 = caxpy(Si[jj[0]], vb, o0); o1 = caxpy(Si[jj[1]], vb, o1);
+        jj[0] += ms[0]; if (jj[0] >= N2) jj[0] -= N2;
+        jj[1] += ms[1]; if (jj[1] >= N2) jj[1] -= N2;
+      }
+      if (q <= d.Nq) {
+        const cplx va = ld2(a + 2 * (base + (long long)(q - 1) * qstride));
+        e0 = caxpy(Si[jj[0]], va, e0); e1 = caxpy(Si[jj[1]], va, e1);
+      }
+      acc[0] = cadd(e0, o0); acc[3] = csub(e0, o0);
+      acc[1] = cadd(e1, o1); acc[2] = csub(e1, o1);
+    } else {
+      for (int q = 1; q <= d.Nq; ++q) {
+        const cplx v = ld2(a + 2 * (base + (long long)(q - 1) * qstride));
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        acc[s] = caxpy(Si[jj[s]], v, acc[s]);
-        jj[s] += ms[s];
-        if (jj[s] >= N2) jj[s] -= N2;
+        for (int s = 0; s < 4; ++s) {
+          acc[s] = caxpy(Si[jj[s]], v, acc[s]);
+          jj[s] += ms[s];
+          if (jj[s] >= N2) jj[s] -= N2;
+        }
       }
     }
 #pragma unroll
@@ -328,6 +492,13 @@ __global__ void k_red_subs(const Item *items, int n_items, const SubDesc *subs, 
   }
 }
 
+cudaError_t set_adj_kernel_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_adj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM_ADJ);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_ring_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM_ADJ);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_ring_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM_ADJ);
+  return e;
+}
+
 cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, const double2 *cot,
                                 const double2 *cot_rec, double2 *grad_xi, double *grad_k, cudaStream_t st) {
   const SubDesc *ds = p->d_subs;
@@ -343,14 +514,14 @@ cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, cons
       prof_end(p, fam, st);                       \
     }                                             \
   } while (0)
-  ADJ_LAUNCH(F_AFWD, k_adj_rows<<<g1(fb[F_AFWD].total_blocks), b4, 0, st>>>(fb[F_AFWD], ds, tab, ws, cot, cot_rec));
+  ADJ_LAUNCH(F_AFWD, k_adj_rows<<<g1(fb[F_AFWD].total_blocks), b8, FFT_SMEM_ADJ, st>>>(fb[F_AFWD], ds, tab, ws, cot, cot_rec));
   if (dk) ADJ_LAUNCH(F_ATRI, k_adj_tri<true><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot, cot_rec ? 1 : 0));
   else ADJ_LAUNCH(F_ATRI, k_adj_tri<false><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot, cot_rec ? 1 : 0));
   if (dk) {
-    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<true><<<g1(fb[F_ARING].total_blocks), b8, 0, st>>>(fb[F_ARING], ds, tab, ws));
+    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<true><<<g1(fb[F_ARING].total_blocks), b8, FFT_SMEM_ADJ, st>>>(fb[F_ARING], ds, tab, ws));
     ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<true><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));
   } else {
-    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<false><<<g1(fb[F_ARING].total_blocks), b8, 0, st>>>(fb[F_ARING], ds, tab, ws));
+    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<false><<<g1(fb[F_ARING].total_blocks), b8, FFT_SMEM_ADJ, st>>>(fb[F_ARING], ds, tab, ws));
     ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<false><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));
   }
   if (dk && basis)

@@ -128,4 +128,47 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   return sh[0];
 }
 
+// Bit reversal of the lg low bits of j.
+__device__ __forceinline__ int brev_lg(int j, int lg) { return (int)(__brev((unsigned)j) >> (32 - lg)); }
+
+// Radix-2 decimation-in-time FFT with the forward sign, V[k] = sum_n x[n] e^{-2 pi i n k / L},
+// of nf sequences of length L = 2 Nx = 2^lg (lg >= 2) stored one after another in shared memory
+// with their inputs in bit-reversed order; the output is in natural order. Twiddles come from
+// the sine table sn[j] = sin(pi j / Nx), j < 2 Nx (cos(pi j / Nx) = sn[j + Nx/2]). The first
+// two stages (twiddles 1 and -i) take no multiplies. Called by every thread of the block.
+__device__ __forceinline__ void fft_r2_stages(double2 *sm, int nf, int Nx, int lg, const double *sn) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int hl = lg - 1, nb = nf << hl;  // butterflies per stage
+  for (int t = tid; t < nb; t += nt) {   // stage 0: pairs (2k, 2k+1)
+    double2 *S = sm + ((t >> hl) << lg) + 2 * (t & ((1 << hl) - 1));
+    const double2 a = S[0], c = S[1];
+    S[0] = make_double2(a.x + c.x, a.y + c.y);
+    S[1] = make_double2(a.x - c.x, a.y - c.y);
+  }
+  __syncthreads();
+  for (int t = tid; t < nb; t += nt) {   // stage 1: twiddles 1, -i
+    const int k = t & ((1 << hl) - 1), j = k & 1;
+    double2 *S = sm + ((t >> hl) << lg) + ((k >> 1) << 2) + j;
+    const double2 a = S[0], c = S[2];
+    const double2 bb = j ? make_double2(c.y, -c.x) : c;
+    S[0] = make_double2(a.x + bb.x, a.y + bb.y);
+    S[2] = make_double2(a.x - bb.x, a.y - bb.y);
+  }
+  __syncthreads();
+  for (int st = 2; st < lg; ++st) {
+    const int half = 1 << st, span = Nx >> st;  // twiddle e^{-i pi j / half} = e^{-i pi (j span) / Nx}
+    for (int t = tid; t < nb; t += nt) {
+      const int k = t & ((1 << hl) - 1), j = k & (half - 1);
+      double2 *S = sm + ((t >> hl) << lg) + ((k >> st) << (st + 1)) + j;
+      const int jj = j * span;
+      const double wr = sn[jj + (Nx >> 1)], wi = -sn[jj];
+      const double2 a = S[0], c = S[half];
+      const double br = fma(wr, c.x, -wi * c.y), bi = fma(wr, c.y, wi * c.x);
+      S[0] = make_double2(a.x + br, a.y + bi);
+      S[half] = make_double2(a.x - br, a.y - bi);
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace mdp

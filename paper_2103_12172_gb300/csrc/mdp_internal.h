@@ -80,6 +80,7 @@ struct Batch {
 };
 
 constexpr int FSW = 24;  // doubles per forward-sweep table row
+constexpr int FFT_POINTS = 4096;  // complex values per block of the dense-row FFT kernels (64 KiB)
 
 // Host buffer of the plan's tables: page-locked (cudaMallocHost) for plans with a device, so
 // that uploads (plan creation, mdp_plan_update_k) run at full link speed; plain heap memory for
@@ -154,6 +155,10 @@ struct mdp_plan {
   double *d_ws = nullptr;
   long long ws_doubles = 0;
   int *d_status = nullptr;
+  int *d_fstatus = nullptr;               // status word of the device factorisation
+  mdp::HostBuf<mdp::SubDesc> sub_stage;  // pinned copy of the subdomain descriptors (async upload)
+  mdp::HostBuf<int> h_fstatus;           // pinned read-back of d_fstatus
+  bool host_stale = false;               // device tables refactored since the host tables were built
   // per wave: device items and prefix arrays (one prefix array per kernel family)
   std::vector<mdp::Item *> d_wave_items, d_gwave_items;
   std::vector<int *> d_wave_prefix, d_gwave_prefix;  // [wave] -> device int [NFAM][n_items + 1]
@@ -186,9 +191,13 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
       if (d.rows_fft) return 4 * ((ncols + d.fpb - 1) / d.fpb);
       return cb * (((d.xsym ? 4 * (d.Ph + 1) : 4 * (d.Px + 2)) + 7) / 8);
     case F_ICOLS: return cb * ((d.Py - 2 + 7) / 8);
-    case F_AFWD: return cb * ((d.Nx / 2 + 3) / 4);
+    case F_AFWD:
+      if (d.rows_fft) return 5 * ((ncols + d.fpb - 1) / d.fpb);
+      return cb * ((d.Nx / 2 + 7) / 8);
     case F_ATRI: return cb * ((d.Nq + 3) / 4);
-    case F_ARING: return cb * ((4 * d.Px + 7) / 8);
+    case F_ARING:
+      if (d.rows_fft) return 4 * ((ncols + d.fpb - 1) / d.fpb);
+      return cb * ((4 * d.Px + 7) / 8);
     case F_ARINGC: return cb * ((d.Py - 4 + 7) / 8);
     case F_AGAM: return cb * ((d.G + 7) / 8);
     case F_IREC: return d.nrec < 0 ? 0 : cb * (((d.xsym ? d.Ph - 1 : d.Px - 2) + 7) / 8);
@@ -211,12 +220,15 @@ void prof_end(mdp_plan *p, int fam, cudaStream_t st);
 // plan construction (host)
 mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n);
 mdp_status refactor_host(mdp_plan *p, const double *k);
+mdp_status set_k_fields(mdp_plan *p, const double *k);   // validate k, update the k-dependent SubDesc fields
+cudaError_t launch_factor(const mdp_plan *p, int *status, cudaStream_t st);   // factor.cu
 void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long long &r, long long &gr,
                     long long &y, long long &a, long long &s, long long &red, long long &total);
 void host_mode_solve(const HostSub &hs, int q, int adjoint, const double *b, double *x);
 // kernel launchers (kernels.cu)
 enum { PASS_FWD = 0, PASS_GRAD = 1 };
-cudaError_t set_kernel_attributes();
+cudaError_t set_kernel_attributes();      // kernels.cu: opt-in shared memory of the FFT kernels
+cudaError_t set_adj_kernel_attributes();  // kernels_adj.cu
 cudaError_t launch_project(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,
                            double2 *out, double2 *out_rec, cudaStream_t st);
 cudaError_t launch_adjoint(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,

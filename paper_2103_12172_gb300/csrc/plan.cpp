@@ -78,8 +78,8 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   d.Ph = d.xsym ? d.Nx / 2 - mlo + 1 : 0;
   d.R2 = d.xsym ? 8 * d.Ph + 4 * (d.Py - 4) : d.R;  // (sum, difference) per pair unit
   d.nrec = -1;
-  d.rows_fft = (d.Nx & (d.Nx - 1)) == 0 && 2 * d.Nx <= 4096 && d.Nx >= 8;
-  d.fpb = d.rows_fft ? 4096 / (2 * d.Nx) : 0;
+  d.rows_fft = (d.Nx & (d.Nx - 1)) == 0 && 2 * d.Nx <= FFT_POINTS && d.Nx >= 8;
+  d.fpb = d.rows_fft ? FFT_POINTS / (2 * d.Nx) : 0;
   d.nfirst = d.cplx ? 0 : 1;
   d.Nt = d.cplx ? in.ny : in.ny - 2;
   d.i0 = (nlo - 1) - d.nfirst;
@@ -486,7 +486,7 @@ mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n) {
   return MDP_OK;
 }
 
-mdp_status refactor_host(mdp_plan *p, const double *k) {
+mdp_status set_k_fields(mdp_plan *p, const double *k) {
   for (int i = 0; i < (int)p->subs.size(); ++i) {
     if (!(k[i] > 0) || !std::isfinite(k[i])) return MDP_ERR_ARG;
   }
@@ -499,7 +499,13 @@ mdp_status refactor_host(mdp_plan *p, const double *k) {
     hs.d.dc1 = k[i] / 6.0;
     hs.d.dc0 = 8.0 * k[i] / 6.0;
   }
-  mdp_status st = factor_all(p->subs);
+  return MDP_OK;
+}
+
+mdp_status refactor_host(mdp_plan *p, const double *k) {
+  mdp_status st = set_k_fields(p, k);
+  if (st != MDP_OK) return st;
+  st = factor_all(p->subs);
   if (st != MDP_OK) return st;
   fill_tables(p);
   return MDP_OK;

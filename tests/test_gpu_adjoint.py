@@ -34,7 +34,10 @@ def rel_col_err(got, ref):
 
 CASES = [("dir4_n65", W.small_subdomain(65, 9.0, W.AP_DIRICHLET4, 2), 8),
          ("somm_n65", W.small_subdomain(65, 11.0, W.AP_DIRX_SOMMY, 2), 8),
-         ("somm_n129", W.small_subdomain(129, 20.0, W.AP_DIRX_SOMMY, 3), None)]
+         ("somm_n129", W.small_subdomain(129, 20.0, W.AP_DIRX_SOMMY, 3), None),
+         # Nx not a power of 2: direct dense-row sums in the adjoint
+         ("somm_n61_direct", W.small_subdomain(61, 10.0, W.AP_DIRX_SOMMY, 2), 8),
+         ("dir4_n50_direct_oddNx", W.small_subdomain(50, 8.0, W.AP_DIRICHLET4, 2), None)]
 
 
 @pytest.mark.parametrize("name,sub,tile", CASES, ids=[c[0] for c in CASES])

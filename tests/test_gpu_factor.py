@@ -1,0 +1,101 @@
+"""Factorisation on the GPU (mdp_plan_update_k on a device plan) against the host plan's
+factorisation of the same wavenumbers, table by table, and the projection after a device
+refactor against the oracle at the new k."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.projection import APSystem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [("somm_n65", W.small_subdomain(65, 11.0, W.AP_DIRX_SOMMY, 3), 14.5),
+         ("dir4_n65", W.small_subdomain(65, 9.0, W.AP_DIRICHLET4, 3), 7.25),
+         ("somm_n61", W.small_subdomain(61, 10.0, W.AP_DIRX_SOMMY, 2), 12.0),
+         ("somm_n257_k30", W.dd2x2_257().subdomains[0], 31.5)]
+
+
+def cols_close(dev, host, ncomplex):
+    """max over table columns of max|dev - host| / max|host| (complex entries by modulus)."""
+    dev = dev.reshape(-1, ncomplex, 2)
+    host = host.reshape(-1, ncomplex, 2)
+    num = np.hypot(*(dev - host).transpose(2, 0, 1)).max(axis=0)
+    den = np.hypot(*host.transpose(2, 0, 1)).max(axis=0)
+    return float((num / np.maximum(den, 1e-300)).max())
+
+
+@pytest.mark.parametrize("name,sub,k1", CASES, ids=[c[0] for c in CASES])
+def test_device_factorisation_matches_host(mdp, name, sub, k1):
+    dplan = mdp.Plan([sub])
+    dplan.update_k([k1])
+    hplan = mdp.Plan([sub.with_k(k1)], host_only=True)
+    td, pd = dplan.read_tables(True)
+    th, ph = hplan.read_tables(False)
+    info = hplan.sub_info(0)
+    off = hplan.table_offsets(0)
+    assert off == dplan.table_offsets(0)
+    Nq, Nt, i0 = info["Nq"], info["Nt"], info["i0"]
+    np.testing.assert_array_equal(pd[off["piv"]:off["piv"] + Nq * Nt], ph[off["piv"]:off["piv"] + Nq * Nt])
+    seg_d = td[off["seg"]:off["seg"] + 5 * Nq].reshape(Nq, 5)
+    seg_h = th[off["seg"]:off["seg"] + 5 * Nq].reshape(Nq, 5)
+    np.testing.assert_array_equal(seg_d, seg_h)
+    FW = 8 if info["cplx"] else 4
+    fd = td[off["fact"]:off["fact"] + Nq * Nt * FW]
+    fh = th[off["fact"]:off["fact"] + Nq * Nt * FW]
+    if FW == 8:
+        assert cols_close(fd, fh, 4) < 1e-12
+    else:
+        num = np.abs(fd - fh).reshape(-1, 4).max(0)
+        assert (num / np.maximum(np.abs(fh).reshape(-1, 4).max(0), 1e-300)).max() < 1e-12
+    assert cols_close(td[off["dT"]:off["dT"] + Nq * Nt * 6], th[off["dT"]:off["dT"] + Nq * Nt * 6], 3) < 1e-13
+    # sweep rows i0 .. itop of every mode (rows above itop are never read); the sweep table
+    # [Nq][NYf][24] is the last table of a one-subdomain plan (then 32-double alignment padding)
+    NYf = (len(th) - off["fs"]) // (Nq * 24)
+    worst = 0.0
+    for q in range(Nq):
+        itop = int(seg_h[q, 4])
+        base = off["fs"] + q * NYf * 24
+        blk_d = td[base:base + (itop - i0 + 1) * 24].reshape(-1, 24)
+        blk_h = th[base:base + (itop - i0 + 1) * 24].reshape(-1, 24)
+        np.testing.assert_array_equal(blk_d[:, 22], blk_h[:, 22])
+        worst = max(worst, cols_close(blk_d[:, :22].ravel(), blk_h[:, :22].ravel(), 11))
+    assert worst < 1e-12
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+def test_projection_after_device_refactor_matches_oracle(mdp, ap):
+    sub = W.small_subdomain(65, 9.0, ap, 3)
+    plan = mdp.Plan([sub], tile_cols=16)
+    plan.update_k([13.3])
+    G, nc, _, _ = plan.layout(0)
+    got = plan.project().cpu().numpy().reshape(nc, G)
+    ref = APSystem(sub.with_k(13.3)).columns()
+    err = (np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)).max()
+    assert err < 1e-10
+    # back to the first k: the same columns as a fresh plan
+    plan.update_k([9.0])
+    again = plan.project().cpu().numpy()
+    fresh = mdp.Plan([sub], tile_cols=16).project().cpu().numpy()
+    assert np.abs(again - fresh).max() <= 1e-12 * np.abs(fresh).max()
+
+
+def test_device_refactor_reports_resonance_and_recovers(mdp):
+    """k on a discrete Dirichlet eigenvalue: the device factorisation reports MDP_ERR_SINGULAR;
+    a later update to a regular k succeeds and the columns are right again."""
+    from paper_2103_12172_gb300 import MdpError
+    n = 33
+    nc = n - 1
+    h = 1.2 / nc
+    lp, lq = -4 * np.sin(np.pi * np.array([2, 3]) / (2 * nc)) ** 2
+    k2 = -((lp + lq) / h**2 + lp * lq / (6 * h**2)) / (1 + (lp + lq) / 12)
+    sub = W.small_subdomain(n, 5.0, W.AP_DIRICHLET4, 2)
+    plan = mdp.Plan([sub])
+    with pytest.raises(MdpError) as e:
+        plan.update_k([np.sqrt(k2)])
+    assert e.value.code == 4  # MDP_ERR_SINGULAR
+    plan.update_k([6.0])
+    G, ncol, _, _ = plan.layout(0)
+    got = plan.project().cpu().numpy().reshape(ncol, G)
+    ref = APSystem(sub.with_k(6.0)).columns()
+    assert (np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)).max() < 1e-10

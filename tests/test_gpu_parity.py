@@ -71,6 +71,9 @@ PROJ_CASES = [
     ("n33_dir4_m3", W.small_subdomain(33, 6.0, W.AP_DIRICHLET4, 3), 7),
     ("n17_somm_m1", W.small_subdomain(17, 3.0, W.AP_DIRX_SOMMY, 1), None),
     ("strip_129_k40", W.strip4x1().subdomains[2], 96),
+    # grids whose Nx is not a power of 2: the dense rows take the direct sine sums
+    ("n61_somm_m3_direct", W.small_subdomain(61, 8.0, W.AP_DIRX_SOMMY, 3), 8),
+    ("n50_dir4_m2_direct_oddNx", W.small_subdomain(50, 7.0, W.AP_DIRICHLET4, 2), None),
 ]
 
 
@@ -97,6 +100,15 @@ def test_user_densities_match_oracle(dev, ap, kind):
     out = plan.project(xi=torch.from_numpy(xi.ravel()).cuda(), kind=kind).cpu().numpy().reshape(nc, G)
     ref = APSystem(sub).columns(xi=xi, kind=kind)
     assert rel_col_err(out, ref) < TOL
+
+
+def test_fft_and_direct_subdomains_in_one_launch(dev):
+    """A batch mixing a power-of-2 grid (FFT dense rows) with a 61-node grid (direct sums)."""
+    subs = [W.small_subdomain(65, 10.0, W.AP_DIRX_SOMMY, 3), W.small_subdomain(61, 9.0, W.AP_DIRX_SOMMY, 3)]
+    plan = make_plan(dev, subs, 16)
+    blocks = [b.cpu().numpy() for b in plan.blocks(plan.project())]
+    for blk, sub in zip(blocks, subs):
+        assert rel_col_err(blk, APSystem(sub).columns()) < TOL
 
 
 def test_unbatched_path_equals_batched(dev):

@@ -140,3 +140,22 @@ def test_dirichlet_resonance_is_reported(mdp):
         mdp.Plan([sub], host_only=True)
     assert e.value.code == 4  # MDP_ERR_SINGULAR
     mdp.Plan([sub.with_k(np.sqrt(k2) * 1.05)], host_only=True)  # off resonance it plans
+
+
+def test_host_refactor_equals_fresh_plan_and_table_readback(mdp):
+    """update_k on a host-only plan rebuilds the same tables as a plan made at the new k; the
+    device copy of a host-only plan is not readable (MDP_ERR_STATE)."""
+    from paper_2103_12172_gb300 import MdpError
+    sub = W.small_subdomain(33, 6.0, W.AP_DIRX_SOMMY, 2)
+    p1 = mdp.Plan([sub], host_only=True)
+    p1.update_k([8.5])
+    p2 = mdp.Plan([sub.with_k(8.5)], host_only=True)
+    t1, v1 = p1.read_tables(False)
+    t2, v2 = p2.read_tables(False)
+    np.testing.assert_array_equal(v1, v2)
+    np.testing.assert_array_equal(t1, t2)
+    off = p1.table_offsets(0)
+    assert off["fact"] == 0 and off["fs"] > off["seg"] > off["geo"] > off["sin"] > off["dT"] > 0
+    with pytest.raises(MdpError) as e:
+        p1.read_tables(True)
+    assert e.value.code == 6  # MDP_ERR_STATE
