@@ -51,6 +51,12 @@ mdp_status mdp_plan_table_sizes(const mdp_plan *p, long long *n_doubles, long lo
  * check the device factorisation against the host one. */
 mdp_status mdp_plan_read_tables(const mdp_plan *p, int device_side, double *tables, unsigned char *piv);
 
+/* y[i] = 1/x[i] for x[i] > 0 (device arrays of n doubles, on cuda_stream) by the reciprocal
+ * that the device factorisation uses: a single-precision seed refined by one cubic
+ * Newton-Raphson (Goldschmidt) step; outside [2^-120, 2^120] a division. For testing its error
+ * against 1/x. */
+mdp_status mdp_probe_rcp(const double *x, double *y, int n, void *cuda_stream);
+
 /* Offsets of subdomain `sub`'s tables (7 values): in doubles into the tables, the factor rows
  * [Nq][Nt][8 complex | 4 real AP], dT/dk rows [Nq][Nt][6], sines [4 Nx], segments [Nq][5],
  * sweep rows [Nq][rows from i0][24], gamma geometry [|gamma|][4]; then in bytes into the pivot

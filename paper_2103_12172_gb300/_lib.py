@@ -56,6 +56,7 @@ def lib():
         "mdp_plan_update_k_stream": (i, [vp, C.POINTER(d), vp]),
         "mdp_plan_table_sizes": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
         "mdp_plan_update_bytes": (ll, [vp]),
+        "mdp_probe_rcp": (i, [vp, vp, i, vp]),
         "mdp_plan_read_tables": (i, [vp, i, vp, vp]),
         "mdp_plan_table_offsets": (i, [vp, i, C.POINTER(ll)]),
         "mdp_plan_layout": (i, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(ll), C.POINTER(C.POINTER(i))]),

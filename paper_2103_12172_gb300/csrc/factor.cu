@@ -9,10 +9,18 @@
 //   - the condensed, pivot-scaled forward-sweep rows of the projection (rows above the ring
 //     folded into the last pivot by their Schur complement), with its run of real rows.
 // The host plan builds the same tables at plan creation (plan.cpp: mode_matrix, band_lu,
-// factor_mode, build_fs_mode). Here one thread streams one mode's rows with O(1) state, so
-// no per-mode scratch is needed: thread t < M factors mode t fully, thread M + t builds the
-// sweep table of mode t (M = number of modes of all subdomains).
+// factor_mode, build_fs_mode). Two kernels:
+//   k_factor_chain  the pivot recurrences, the only sequential part: one thread per (mode,
+//                   table) streams the rows with O(1) state and stores each raw LU row (l, d,
+//                   1/d, du, du2, swap) in place in its table row. A chain is a long sequence of
+//                   dependent FP64 operations, so it does nothing else, and its interior
+//                   no-swap steps take a real-coefficient fast path.
+//   k_factor_rows   everything row-local, one block per mode: u1 = du/d, u2 = du2/d, the
+//                   sweep rows (which also need row i+1's pivot, read through shared memory in
+//                   chunks so the rows can be rewritten in place), the dT/dk rows, and the runs
+//                   of exactly-real rows (block reductions).
 #include "kernels_common.cuh"
+#include "mdp_probe.h"
 
 namespace mdp {
 namespace {
@@ -23,10 +31,20 @@ constexpr double kCondenseTolD = 1e-8;    // Schur complement below this x max|T
 __device__ __forceinline__ double cabs2(cplx a) { return fma(a.re, a.re, a.im * a.im); }
 __device__ __forceinline__ cplx cscale(double s, cplx a) { return {s * a.re, s * a.im}; }
 __device__ __forceinline__ bool czero(cplx a) { return a.re == 0.0 && a.im == 0.0; }
-// 1/b and a/b through one real reciprocal of |b|^2 (the magnitudes here are O(1/h^2), far from
-// overflow and underflow)
+// 1/x for x > 0: a single-precision seed y0 (relative error below 2^-21) refined by one cubic
+// step of the Newton-Raphson iteration for 1/x (Goldschmidt form): with e = 1 - x y0,
+// 1/x = y0 / (1 - e) = y0 (1 + e + e^2) + O(e^3 y0), i.e. full double precision. Six dependent
+// operations instead of a full division on the factorisation's serial chains; x outside the
+// float range takes the division.
+__device__ __forceinline__ double rcp_pos(double x) {
+  if (!(x > 0x1p-120 && x < 0x1p120)) return 1.0 / x;
+  const double y0 = (double)__fdividef(1.0f, (float)x);
+  const double e = fma(-x, y0, 1.0);
+  return fma(y0, fma(e, e, e), y0);
+}
+// 1/b and a/b through one real reciprocal of |b|^2 (the magnitudes here are O(1/h^2))
 __device__ __forceinline__ cplx crecip(cplx b) {
-  const double r = 1.0 / cabs2(b);
+  const double r = rcp_pos(cabs2(b));
   return {b.re * r, -b.im * r};
 }
 __device__ __forceinline__ cplx cdiv(cplx a, cplx b) { return cmul(a, crecip(b)); }
@@ -80,17 +98,18 @@ __device__ ModeRows mode_rows(const SubDesc &d, int q) {
 
 // One step of the banded LU with partial pivoting, streamed: on entry (g, u) are the current
 // diagonal and super-diagonal of row i, (lsub, gn, un) the original T[i+1][i], T[i+1][i+1],
-// T[i+1][i+2]. On exit (l, dfin, dup, du2, sw) are row i's multiplier, pivot, first and second
-// super-diagonal of U and swap flag, and (g, u) hold row i+1. last2: i == n-2 (no du2 fill-in).
-// Returns false on a zero pivot.
+// T[i+1][i+2]. On exit (l, dinv, dup, du2, sw) are row i's multiplier, inverse pivot, first and
+// second super-diagonal of U and swap flag (the pivot itself is returned in dfin), and (g, u)
+// hold row i+1. last2: i == n-2 (no du2 fill-in). Returns false on a zero pivot.
 __device__ __forceinline__ bool lu_step(cplx &g, cplx &u, cplx lsub, cplx gn, cplx un, bool last2, cplx &l,
                                         cplx &dfin, cplx &dinv, cplx &dup, cplx &du2, uint8_t &sw) {
   if (cabs2(g) >= cabs2(lsub)) {
     if (czero(g)) return false;
+    const cplx lu = cmul(lsub, u);   // off the g -> g' chain
     dinv = crecip(g);
     const cplx f = cmul(lsub, dinv);
     l = f; dfin = g; dup = u; du2 = cmk(0.0, 0.0); sw = 0;
-    g = csub(gn, cmul(f, u));
+    g = csub(gn, cmul(lu, dinv));
     u = un;
   } else {
     dinv = crecip(lsub);
@@ -106,88 +125,100 @@ __device__ __forceinline__ bool lu_step(cplx &g, cplx &u, cplx lsub, cplx gn, cp
 
 __device__ __forceinline__ void set_error(int *status, int code) { atomicCAS(status, 0, code); }
 
-// Full LU of T_q: factor rows, swap flags, dT/dk rows, seg[0..1] (real-row run).
-__device__ void factor_full(const SubDesc &d, int q, double *tab, uint8_t *piv, int *status) {
+// The pivoted LU of rows 0..n-1 of T_q (diagonal of row `mod` reduced by sigma), calling
+// out(i, l, d, dinv, du, du2, sw) for every row in order. Interior steps (real a, dd entries,
+// super-diagonal of the pivot row still the original a) that keep the pivot take the fast path
+// with real coefficients. Returns false (status set) on a singular pivot.
+template <class Out>
+__device__ bool lu_chain(const ModeRows &M, int n, int mod, cplx sigma, double tol2, int *status, Out out) {
+  const int N = M.N;
+  auto ent = [&](int i, cplx &dl, cplx &dg, cplx &du) {
+    M.entries(i, dl, dg, du);
+    if (i == mod) dg = csub(dg, sigma);
+  };
+  const double a = M.a, dd = M.dd, a2 = M.a * M.a;
+  // steps i < fast_end have T[i+1][i] = a and T[i+1][i+1] = dd (not a Sommerfeld row, not the
+  // reduced row); they take the fast path while the pivot row's super-diagonal is still a
+  const int fast_end = min(M.cplx_ap ? N - 2 : n - 1, mod - 1 >= 0 ? mod - 1 : n - 1);
+  cplx g, u, dl0;
+  ent(0, dl0, g, u);
+  bool u_is_a = !M.cplx_ap;   // u still equals the original interior entry a
+  int i = 0;
+  double r = 0.0;             // 1/|g|^2 of the previous fast step
+  while (i < n - 1) {
+    if (u_is_a) {
+      // Fast path: keep the pivot while |g| >= a. Then |g|^2 >= a^2 > tol2 (a >= 1/(3h^2) is
+      // within a factor 7 of max|T|), so no singularity test is needed. The pivots of a mode
+      // settle to a fixed point, so 1/|g|^2 is refined from the previous row's: with
+      // e = 1 - n2 r0, 1/n2 = r0 / (1 - e) = r0 (1 + e + e^2) + O(e^3 r0), full precision for
+      // |e| < 2^-20; otherwise a division.
+      // The loop-carried chain is g -> |g|^2 -> 1/|g|^2 -> g' = dd - a^2 conj(g)/|g|^2; the
+      // swap test and the row's outputs branch off it.
+      const double a2dd = a2;
+      for (; i < fast_end; ++i) {
+        const double n2 = fma(g.re, g.re, g.im * g.im);
+        const double e = fma(-n2, r, 1.0);
+        double rn = fma(r, fma(e, e, e), r);
+        if (!(fabs(e) < 0x1p-20)) rn = rcp_pos(n2);
+        if (n2 < a2) break;
+        r = rn;
+        const double gr = g.re * r, gi = g.im * r;   // 1/g = (gr, -gi)
+        const cplx gnext = cmk(fma(-a2dd, gr, dd), a2dd * gi);
+        out(i, cmk(a * gr, -a * gi), g, cmk(gr, -gi), cmk(a, 0.0), cmk(0.0, 0.0), (uint8_t)0);
+        g = gnext;
+      }
+      if (i >= n - 1) break;
+    }
+    cplx lsub, gi, ui, gn, un, dln;
+    ent(i, lsub, gi, ui);
+    ent(i + 1, dln, gn, un);
+    cplx l, dfin, dinv, dup, du2;
+    uint8_t sw;
+    if (!lu_step(g, u, lsub, gn, un, i == n - 2, l, dfin, dinv, dup, du2, sw)) {
+      set_error(status, MDP_ERR_SINGULAR);
+      return false;
+    }
+    if (cabs2(dfin) < tol2) { set_error(status, MDP_ERR_SINGULAR); return false; }
+    out(i, l, dfin, dinv, dup, du2, sw);
+    // after a kept pivot u is the original T[i+1][i+2]: a for every row but the first
+    u_is_a = sw == 0;
+    if (u_is_a) u = cmk(a, 0.0);
+    ++i;
+  }
+  if (czero(g) || cabs2(g) < tol2) { set_error(status, MDP_ERR_SINGULAR); return false; }
+  out(n - 1, cmk(0.0, 0.0), g, crecip(g), cmk(0.0, 0.0), cmk(0.0, 0.0), (uint8_t)0);
+  return true;
+}
+
+// Chain of the full LU: raw factor rows (l, 1/d, du, du2) and swap flags.
+__device__ void chain_full(const SubDesc &d, int q, double *tab, uint8_t *piv, int *status) {
   const ModeRows M = mode_rows(d, q);
   const int N = M.N, FW = d.cplx ? 8 : 4;
   const double tol2 = kSingularTolD * kSingularTolD * M.scale2();
   double *F = tab + d.fact_off + (long long)(q - 1) * N * FW;
-  double *dT = tab + d.dT_off + (long long)(q - 1) * N * 6;
   uint8_t *pv = piv + d.piv_off + (long long)(q - 1) * N;
-  // dT/dk rows: (sub, diag, super)
-  for (int i = 0; i < N; ++i) {
-    cplx ts = cmk(M.da, 0.0), tg = cmk(M.ddd, 0.0), tu = cmk(M.da, 0.0);
-    if (M.cplx_ap && i == 0) { tg = M.tp; tu = M.tm; ts = cmk(0.0, 0.0); }
-    if (M.cplx_ap && i == N - 1) { tg = M.tp; ts = M.tm; tu = cmk(0.0, 0.0); }
-    if (i == 0) ts = cmk(0.0, 0.0);
-    if (i == N - 1) tu = cmk(0.0, 0.0);
-    double *t = dT + 6 * i;
-    t[0] = ts.re; t[1] = ts.im; t[2] = tg.re; t[3] = tg.im; t[4] = tu.re; t[5] = tu.im;
-  }
-  cplx g, u, dl0;
-  M.entries(0, dl0, g, u);
-  const int mid = N / 2;
-  int lastbad = -1, rlo = mid, rhi = mid;
-  bool inrun = false;
-  for (int i = 0; i < N; ++i) {
-    cplx l = cmk(0.0, 0.0), dfin, dinv, dup = cmk(0.0, 0.0), du2 = cmk(0.0, 0.0);
-    uint8_t sw = 0;
-    if (i < N - 1) {
-      cplx lsub, gi, ui, gn, un, dln;
-      M.entries(i, lsub, gi, ui);
-      M.entries(i + 1, dln, gn, un);
-      if (!lu_step(g, u, lsub, gn, un, i == N - 2, l, dfin, dinv, dup, du2, sw)) {
-        set_error(status, MDP_ERR_SINGULAR);
-        return;
-      }
-    } else {
-      if (czero(g)) { set_error(status, MDP_ERR_SINGULAR); return; }
-      dfin = g;
-      dinv = crecip(g);
-    }
-    if (cabs2(dfin) < tol2) { set_error(status, MDP_ERR_SINGULAR); return; }
-    const cplx u1 = i < N - 1 ? cmul(dup, dinv) : cmk(0.0, 0.0);
-    const cplx u2 = i < N - 2 ? cmul(du2, dinv) : cmk(0.0, 0.0);
-    if (i >= N - 1) l = cmk(0.0, 0.0);
-    if (FW == 8) {
-      double *r = F + (long long)i * 8;
-      r[0] = l.re; r[1] = l.im; r[2] = dinv.re; r[3] = dinv.im; r[4] = u1.re; r[5] = u1.im; r[6] = u2.re; r[7] = u2.im;
-      const bool re = tiny_im(l) && tiny_im(dinv) && tiny_im(u1) && tiny_im(u2);
-      if (i < mid && !re) lastbad = i;
-      if (i == mid) {
-        if (re) { rlo = lastbad + 1; inrun = true; }
-      } else if (i > mid && inrun && !re) {
-        rhi = i;
-        inrun = false;
-      }
-    } else {
-      double *r = F + (long long)i * 4;
-      r[0] = l.re; r[1] = dinv.re; r[2] = u1.re; r[3] = u2.re;
-    }
-    pv[i] = sw;
-  }
-  if (inrun) rhi = N;
-  if (FW == 8) {
-    for (int i = rlo; i < rhi; ++i)
-      for (int w = 0; w < 4; ++w) F[(long long)i * 8 + 2 * w + 1] = 0.0;
-  } else {
-    rlo = 0; rhi = N;
-  }
-  double *sg = tab + d.seg_off + 5 * (q - 1);
-  sg[0] = rlo;
-  sg[1] = rhi;
+  lu_chain(M, N, -1, cmk(0.0, 0.0), tol2, status,
+           [&](int i, cplx l, cplx, cplx dinv, cplx du, cplx du2, uint8_t sw) {
+             if (FW == 8) {
+               double *r = F + (long long)i * 8;
+               st2(r, l); st2(r + 2, dinv); st2(r + 4, du); st2(r + 6, du2);
+             } else {
+               double *r = F + (long long)i * 4;
+               r[0] = l.re; r[1] = dinv.re; r[2] = du.re; r[3] = du2.re;
+             }
+             pv[i] = sw;
+           });
 }
 
-// Condensed, pivot-scaled forward-sweep table of mode q and seg[2..4] (real run, itop).
-// Row layout (complex pairs): m = l d_i/d_{i+1}, d_i/d_{i+1}, l/d_{i+1}, 1/d_i, 1/d_{i+1},
-// c0..c3 = sin(pi q m_s/Nx)/d_{i+1} (m_s = mlo, mlo+1, mhi-1, mhi), du_i/d_i, du2_i/d_i, then the
-// swap flag and a pad.
-__device__ void factor_sweep(const SubDesc &d, int q, double *tab, int *status) {
+// Chain of the condensed system (rows 0..itop, the rows above folded into the last pivot):
+// raw rows i >= i0 in the sweep table: l, d, 1/d, du, du2 (complex pairs) and the swap flag;
+// seg[4] = itop.
+__device__ void chain_sweep(const SubDesc &d, int q, double *tab, int *status) {
   const ModeRows M = mode_rows(d, q);
   const int N = M.N;
   const double scale2 = M.scale2();
   const double tol2 = kSingularTolD * kSingularTolD * scale2, ctol2 = kCondenseTolD * kCondenseTolD * scale2;
-  // (1) top condensation
+  // top condensation: s_{N-1} = T[N-1][N-1], s_i = T[i][i] - T[i][i+1] T[i+1][i] / s_{i+1}
   const int ih = d.nhi + 1 - d.nfirst;
   int itop = N - 1;
   cplx sigma = cmk(0.0, 0.0);
@@ -208,89 +239,19 @@ __device__ void factor_sweep(const SubDesc &d, int q, double *tab, int *status) 
       sigma = cdiv(cmul(ui, li), sv);
     }
   }
-  const int n = itop + 1;
-  auto entries_c = [&](int i, cplx &dl, cplx &dg, cplx &du) {
-    M.entries(i, dl, dg, du);
-    if (i == itop) dg = csub(dg, sigma);
-  };
-  // (2) condensed LU, emitting sweep row i once d_{i+1} is final
-  const int N2 = 2 * d.Nx;
-  const int ms[4] = {d.mlo, d.mlo + 1, d.mhi - 1, d.mhi};
-  double sines[4];
-  for (int s_ = 0; s_ < 4; ++s_) sines[s_] = sin(M_PI * (double)((q * ms[s_]) % N2) / (double)d.Nx);
+  tab[d.seg_off + 5 * (q - 1) + 4] = itop;
   double *T = tab + d.fs_off + (long long)(q - 1) * d.NYf * FSW;
-  const int mid = (d.i0 + itop) / 2;
-  int lastbad = d.i0 - 1, flo = mid, fhi = mid;
-  bool inrun = false;
-  // row i of the sweep table from its LU row (l, d_i, 1/d_i, du, du2) and 1/d_{i+1}
-  auto emit = [&](int i, cplx l, cplx di, cplx dinv, cplx dni, cplx dup, cplx du2, uint8_t sw, bool last) {
-    if (i < d.i0) return;
-    if (last) { l = cmk(0.0, 0.0); dni = cmk(0.0, 0.0); }
-    cplx v[11];
-    v[0] = cmul(cmul(l, di), dni);
-    v[1] = cmul(di, dni);
-    v[2] = cmul(l, dni);
-    v[3] = dinv;
-    v[4] = dni;
-    for (int s_ = 0; s_ < 4; ++s_) v[5 + s_] = cscale(sines[s_], dni);
-    v[9] = last ? cmk(0.0, 0.0) : cmul(dup, dinv);
-    v[10] = i + 2 <= itop ? cmul(du2, dinv) : cmk(0.0, 0.0);
-    double *row = T + (long long)(i - d.i0) * FSW;
-    bool re = true;
-    for (int w = 0; w < 11; ++w) {
-      row[2 * w] = v[w].re;
-      row[2 * w + 1] = v[w].im;
-      re = re && tiny_im(v[w]);
-    }
-    row[22] = sw;
-    row[23] = 0.0;
-    if (i < mid && !re) lastbad = i;
-    if (i == mid) {
-      if (re) { flo = lastbad + 1; inrun = true; }
-    } else if (i > mid && inrun && !re) {
-      fhi = i;
-      inrun = false;
-    }
-  };
-  cplx g, u, dl0;
-  entries_c(0, dl0, g, u);
-  // pending row (its pivot d_i is final; d_{i+1} is not yet)
-  cplx pl = cmk(0.0, 0.0), pd = cmk(0.0, 0.0), pdi = cmk(0.0, 0.0), pdu = cmk(0.0, 0.0), pdu2 = cmk(0.0, 0.0);
-  uint8_t psw = 0;
-  for (int i = 0; i < n; ++i) {
-    cplx l = cmk(0.0, 0.0), dfin, dinv, dup = cmk(0.0, 0.0), du2 = cmk(0.0, 0.0);
-    uint8_t sw = 0;
-    if (i < n - 1) {
-      cplx lsub, gi, ui, gn, un, dln;
-      entries_c(i, lsub, gi, ui);
-      entries_c(i + 1, dln, gn, un);
-      if (!lu_step(g, u, lsub, gn, un, i == n - 2, l, dfin, dinv, dup, du2, sw)) {
-        set_error(status, MDP_ERR_SINGULAR);
-        return;
-      }
-    } else {
-      if (czero(g)) { set_error(status, MDP_ERR_SINGULAR); return; }
-      dfin = g;
-      dinv = crecip(g);
-    }
-    if (cabs2(dfin) < tol2) { set_error(status, MDP_ERR_SINGULAR); return; }
-    if (i > 0) emit(i - 1, pl, pd, pdi, dinv, pdu, pdu2, psw, false);
-    pl = l; pd = dfin; pdi = dinv; pdu = dup; pdu2 = du2; psw = sw;
-  }
-  emit(itop, pl, pd, pdi, cmk(0.0, 0.0), pdu, pdu2, psw, true);
-  if (inrun) fhi = itop + 1;
-  for (int i = flo; i < fhi; ++i) {
-    double *row = T + (long long)(i - d.i0) * FSW;
-    for (int w = 0; w < 11; ++w) row[2 * w + 1] = 0.0;
-  }
-  double *sg = tab + d.seg_off + 5 * (q - 1);
-  sg[2] = flo;
-  sg[3] = fhi;
-  sg[4] = itop;
+  lu_chain(M, itop + 1, itop, sigma, tol2, status,
+           [&](int i, cplx l, cplx dg, cplx dinv, cplx du, cplx du2, uint8_t sw) {
+             if (i < d.i0) return;
+             double *r = T + (long long)(i - d.i0) * FSW;
+             st2(r, l); st2(r + 2, dg); st2(r + 4, dinv); st2(r + 6, du); st2(r + 8, du2);
+             r[22] = sw;
+           });
 }
 
-__global__ void __launch_bounds__(32) k_factor(const SubDesc *subs, int n_subs, int n_modes, double *tab,
-                                                uint8_t *piv, int *status) {
+__global__ void __launch_bounds__(32) k_factor_chain(const SubDesc *subs, int n_subs, int n_modes, double *tab,
+                                                      uint8_t *piv, int *status) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * n_modes) return;
   const bool sweep = t >= n_modes;
@@ -298,22 +259,165 @@ __global__ void __launch_bounds__(32) k_factor(const SubDesc *subs, int n_subs, 
   int si = 0;
   while (si < n_subs && t >= subs[si].Nq) { t -= subs[si].Nq; ++si; }
   if (si >= n_subs) return;
-  if (sweep) factor_sweep(subs[si], t + 1, tab, status);
-  else factor_full(subs[si], t + 1, tab, piv, status);
+  if (sweep) chain_sweep(subs[si], t + 1, tab, status);
+  else chain_full(subs[si], t + 1, tab, piv, status);
+}
+
+constexpr int kRowsThreads = 256;
+
+// Block reduction of a real-row run: the run of rows with re[i] around row mid, from the
+// largest non-real row below mid and the smallest above it.
+struct RunReduce {
+  int lastbad, firstbad, midreal;
+  __device__ void init(int lo, int hi) { lastbad = lo - 1; firstbad = hi; midreal = 0; }
+};
+
+__global__ void __launch_bounds__(kRowsThreads) k_factor_rows(const SubDesc *subs, int n_subs, double *tab) {
+  __shared__ RunReduce run;
+  __shared__ double raw[(kRowsThreads + 1) * 11];
+  int t = blockIdx.x;
+  int si = 0;
+  while (si < n_subs && t >= subs[si].Nq) { t -= subs[si].Nq; ++si; }
+  if (si >= n_subs) return;
+  const SubDesc &d = subs[si];
+  const int q = t + 1, tid = threadIdx.x;
+  // the mode's coefficients and the 4 middle-row sines, computed once per block
+  __shared__ ModeRows Ms;
+  __shared__ double sines[4];
+  if (tid == 0) {
+    Ms = mode_rows(d, q);
+    const int N2 = 2 * d.Nx;
+    const int ms[4] = {d.mlo, d.mlo + 1, d.mhi - 1, d.mhi};
+    for (int s_ = 0; s_ < 4; ++s_) sines[s_] = sin(M_PI * (double)((q * ms[s_]) % N2) / (double)d.Nx);
+  }
+  __syncthreads();
+  const ModeRows &M = Ms;
+  const int N = M.N;
+  double *sg = tab + d.seg_off + 5 * (q - 1);
+  // ---- dT/dk rows (sub, diag, super)
+  double *dT = tab + d.dT_off + (long long)(q - 1) * N * 6;
+  for (int i = tid; i < N; i += kRowsThreads) {
+    cplx ts = cmk(M.da, 0.0), tg = cmk(M.ddd, 0.0), tu = cmk(M.da, 0.0);
+    if (M.cplx_ap && i == 0) { tg = M.tp; tu = M.tm; ts = cmk(0.0, 0.0); }
+    if (M.cplx_ap && i == N - 1) { tg = M.tp; ts = M.tm; tu = cmk(0.0, 0.0); }
+    if (i == 0) ts = cmk(0.0, 0.0);
+    if (i == N - 1) tu = cmk(0.0, 0.0);
+    double *r = dT + 6 * i;
+    r[0] = ts.re; r[1] = ts.im; r[2] = tg.re; r[3] = tg.im; r[4] = tu.re; r[5] = tu.im;
+  }
+  // ---- factor rows: (l, 1/d, du, du2) -> (l, 1/d, du/d, du2/d); real run around N/2
+  if (d.cplx) {
+    double *F = tab + d.fact_off + (long long)(q - 1) * N * 8;
+    const int mid = N / 2;
+    if (tid == 0) run.init(0, N);
+    __syncthreads();
+    for (int i = tid; i < N; i += kRowsThreads) {
+      double *r = F + (long long)i * 8;
+      const cplx l = ld2(r), dinv = ld2(r + 2);
+      const cplx u1 = cmul(ld2(r + 4), dinv), u2 = cmul(ld2(r + 6), dinv);
+      st2(r + 4, u1);
+      st2(r + 6, u2);
+      const bool re = tiny_im(l) && tiny_im(dinv) && tiny_im(u1) && tiny_im(u2);
+      if (!re && i < mid) atomicMax(&run.lastbad, i);
+      if (!re && i > mid) atomicMin(&run.firstbad, i);
+      if (re && i == mid) run.midreal = 1;
+    }
+    __syncthreads();
+    const int rlo = run.midreal ? run.lastbad + 1 : mid, rhi = run.midreal ? run.firstbad : mid;
+    for (int i = tid; i < N; i += kRowsThreads)
+      if (i >= rlo && i < rhi)
+        for (int w = 0; w < 4; ++w) F[(long long)i * 8 + 2 * w + 1] = 0.0;
+    if (tid == 0) { sg[0] = rlo; sg[1] = rhi; }
+    __syncthreads();
+  } else {
+    double *F = tab + d.fact_off + (long long)(q - 1) * N * 4;
+    for (int i = tid; i < N; i += kRowsThreads) {
+      double *r = F + (long long)i * 4;
+      const double dinv = r[1];
+      r[2] *= dinv;
+      r[3] *= dinv;
+    }
+    if (tid == 0) { sg[0] = 0; sg[1] = N; }
+  }
+  // ---- sweep rows i0 .. itop from the raw rows, in chunks of kRowsThreads rows
+  const int itop = (int)sg[4], i0 = d.i0;
+  const int mid = (i0 + itop) / 2;
+  double *T = tab + d.fs_off + (long long)(q - 1) * d.NYf * FSW;
+  if (tid == 0) run.init(i0, itop + 1);
+  __syncthreads();
+  for (int c0 = i0; c0 <= itop; c0 += kRowsThreads) {
+    const int nr = min(kRowsThreads + 1, itop + 1 - c0);   // raw rows c0 .. c0 + nr - 1
+    for (int k = tid; k < nr * 11; k += kRowsThreads) {
+      const int rr = k / 11, w = k % 11;
+      raw[rr * 11 + w] = T[(long long)(c0 + rr - i0) * FSW + (w < 10 ? w : 22)];
+    }
+    __syncthreads();
+    const int i = c0 + tid;
+    if (tid < kRowsThreads && i <= itop) {
+      const double *rw = raw + tid * 11;
+      const bool last = i == itop;
+      const cplx l = last ? cmk(0.0, 0.0) : cmk(rw[0], rw[1]);
+      const cplx di = cmk(rw[2], rw[3]), dinv = cmk(rw[4], rw[5]);
+      const cplx du = cmk(rw[6], rw[7]), du2 = cmk(rw[8], rw[9]);
+      const cplx dni = last ? cmk(0.0, 0.0) : cmk(rw[11 + 4], rw[11 + 5]);
+      cplx v[11];
+      v[0] = cmul(cmul(l, di), dni);
+      v[1] = cmul(di, dni);
+      v[2] = cmul(l, dni);
+      v[3] = dinv;
+      v[4] = dni;
+      for (int s_ = 0; s_ < 4; ++s_) v[5 + s_] = cscale(sines[s_], dni);
+      v[9] = last ? cmk(0.0, 0.0) : cmul(du, dinv);
+      v[10] = i + 2 <= itop ? cmul(du2, dinv) : cmk(0.0, 0.0);
+      double *row = T + (long long)(i - i0) * FSW;
+      bool re = true;
+      for (int w = 0; w < 11; ++w) {
+        row[2 * w] = v[w].re;
+        row[2 * w + 1] = v[w].im;
+        re = re && tiny_im(v[w]);
+      }
+      row[22] = rw[10];
+      row[23] = 0.0;
+      if (!re && i < mid) atomicMax(&run.lastbad, i);
+      if (!re && i > mid) atomicMin(&run.firstbad, i);
+      if (re && i == mid) run.midreal = 1;
+    }
+    __syncthreads();
+  }
+  const int flo = run.midreal ? run.lastbad + 1 : mid, fhi = run.midreal ? run.firstbad : mid;
+  for (int i = i0 + tid; i <= itop; i += kRowsThreads)
+    if (i >= flo && i < fhi) {
+      double *row = T + (long long)(i - i0) * FSW;
+      for (int w = 0; w < 11; ++w) row[2 * w + 1] = 0.0;
+    }
+  if (tid == 0) { sg[2] = flo; sg[3] = fhi; }
+}
+
+__global__ void k_probe_rcp(const double *x, double *y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = rcp_pos(x[i]);
 }
 
 }  // namespace
 
-// Each thread is one long dependent chain of FP64 operations and an SM retires 2 FP64 lanes per
-// clock, so the warps are spread one per block (one per SM while there are fewer warps than SMs)
-// instead of packed four to an SM.
+// The chains: one thread each, warps spread one per block so that they do not share an SM's
+// FP64 unit while there are fewer warps than SMs. The row kernel: one block per mode.
 cudaError_t launch_factor(const mdp_plan *p, int *status, cudaStream_t st) {
   int n_modes = 0;
   for (auto &hs : p->subs) n_modes += hs.d.Nq;
   const int threads = 2 * n_modes;
-  k_factor<<<(threads + 31) / 32, 32, 0, st>>>(p->d_subs, (int)p->subs.size(), n_modes, p->d_tables, p->d_piv,
-                                                status);
+  k_factor_chain<<<(threads + 31) / 32, 32, 0, st>>>(p->d_subs, (int)p->subs.size(), n_modes, p->d_tables,
+                                                      p->d_piv, status);
+  k_factor_rows<<<n_modes, kRowsThreads, 0, st>>>(p->d_subs, (int)p->subs.size(), p->d_tables);
   return cudaGetLastError();
 }
 
 }  // namespace mdp
+
+// The reciprocal of the factorisation chains on device arrays (test probe, include/mdp_probe.h).
+extern "C" mdp_status mdp_probe_rcp(const double *x, double *y, int n, void *cuda_stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return MDP_ERR_ARG;
+  if (n == 0) return MDP_OK;
+  mdp::k_probe_rcp<<<(n + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(x, y, n);
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_ERR_CUDA;
+}

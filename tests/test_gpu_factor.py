@@ -99,3 +99,23 @@ def test_device_refactor_reports_resonance_and_recovers(mdp):
     got = plan.project().cpu().numpy().reshape(ncol, G)
     ref = APSystem(sub.with_k(6.0)).columns()
     assert (np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)).max() < 1e-10
+
+
+def test_factor_reciprocal_is_accurate_to_an_ulp(mdp):
+    """The reciprocal of the device factorisation against the correctly rounded 1/x: within 2
+    ulp over 60 decades, at the edges of the seed's range and on both sides of them."""
+    import ctypes
+    from paper_2103_12172_gb300 import _lib
+    rng = np.random.default_rng(5)
+    x = np.concatenate([10.0 ** rng.uniform(-30, 30, 200000),
+                        rng.uniform(0.5, 2.0, 10000),
+                        [2.0 ** -120, 2.0 ** 120, 2.0 ** -121, 2.0 ** 121, 1e-300, 1e300, 1.0, 3.0]])
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    L = _lib.lib()
+    _lib.check(L.mdp_probe_rcp(ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()), len(x),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "mdp_probe_rcp")
+    y = yd.cpu().numpy()
+    r = 1.0 / x                                   # correctly rounded
+    ulps = np.abs(y - r) / np.spacing(r)
+    assert ulps.max() <= 2.0, ulps.max()
