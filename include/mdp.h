@@ -56,6 +56,13 @@ enum { MDP_OUT_Q = 0, MDP_OUT_P = 1 };
 /* Plan flags */
 #define MDP_PLAN_HOST_ONLY 0x1u   /* build host tables only; no CUDA call is made */
 #define MDP_PLAN_GRAPH 0x2u       /* mdp_project_batch replays a CUDA graph of its launches */
+/* Subdomains that pose the same auxiliary problem up to a translation (same grid, step, k, AP,
+ * M*, index sets and gamma geometry relative to the grid) share one set of tables, and
+ * mdp_project_batch of the basis columns (xi == NULL, no receivers) solves each distinct
+ * problem once and copies its block to the duplicates: the paper's reuse of Q for identical
+ * subdomains (Section 4). User densities, receivers and the adjoint still run per subdomain
+ * (on the shared tables). mdp_plan_update_k then requires equal k within each group. */
+#define MDP_PLAN_DEDUPE 0x4u
 
 /* Plan options (0 selects the default: environment MDP_TILE_COLS / MDP_WS_MB, else 256 columns
  * per work item and a 4 GiB workspace budget). */
@@ -107,6 +114,11 @@ mdp_status mdp_ap_plan_ex(const mdp_subdomain *subs, int n_subs, unsigned flags,
  * mdp_plan_update_k is mdp_plan_update_k_stream on the legacy default stream. */
 mdp_status mdp_plan_update_k(mdp_plan *p, const double *k);
 mdp_status mdp_plan_update_k_stream(mdp_plan *p, const double *k, void *cuda_stream);
+
+/* leader[i] (host array of n_subs ints): the subdomain whose tables (and, for basis columns,
+ * computed block) subdomain i shares; i itself unless MDP_PLAN_DEDUPE found an earlier
+ * identical subdomain. */
+mdp_status mdp_plan_leaders(const mdp_plan *p, int *leader);
 
 /* Layout of subdomain `sub` (host values): |gamma|, its 8*M* columns, the element offset
  * of its block in the output of mdp_project_batch, and a host pointer (owned by the plan,

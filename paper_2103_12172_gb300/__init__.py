@@ -18,7 +18,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import MdpError, MDP_OUT_P, MDP_OUT_Q, MDP_PLAN_GRAPH, MDP_PLAN_HOST_ONLY
+from ._lib import MdpError, MDP_OUT_P, MDP_OUT_Q, MDP_PLAN_DEDUPE, MDP_PLAN_GRAPH, MDP_PLAN_HOST_ONLY
 
 __all__ = ["Plan", "MdpError", "probe_fp64_gflops", "as_c_subdomains", "solve_noalloc"]
 
@@ -49,12 +49,13 @@ class Plan:
     """A plan over a list of subdomains (objects with the mdp_subdomain fields)."""
 
     def __init__(self, subdomains, host_only: bool = False, graph: bool = False, tile_cols: int = 0,
-                 workspace_bytes: int = 0):
+                 workspace_bytes: int = 0, dedupe: bool = False):
         self.L = _lib.lib()
         self.subdomains = list(subdomains)
         self._c_subs = as_c_subdomains(self.subdomains)
         handle = C.c_void_p()
-        flags = (MDP_PLAN_HOST_ONLY if host_only else 0) | (MDP_PLAN_GRAPH if graph else 0)
+        flags = ((MDP_PLAN_HOST_ONLY if host_only else 0) | (MDP_PLAN_GRAPH if graph else 0)
+                 | (MDP_PLAN_DEDUPE if dedupe else 0))
         opts = _lib.mdp_plan_options(int(tile_cols), int(workspace_bytes))
         _lib.check(self.L.mdp_ap_plan_ex(self._c_subs, len(self.subdomains), flags, C.byref(opts), C.byref(handle)),
                    "mdp_ap_plan")
@@ -198,6 +199,12 @@ class Plan:
         arr = (C.c_double * self.n_subs)(*[float(k) for k in ks])
         st = None if self.host_only else _stream_ptr(stream)
         _lib.check(self.L.mdp_plan_update_k_stream(self.handle, arr, st), "mdp_plan_update_k_stream")
+
+    def leaders(self) -> list:
+        """Per subdomain, the subdomain whose tables and basis columns it shares (dedupe)."""
+        a = (C.c_int * self.n_subs)()
+        _lib.check(self.L.mdp_plan_leaders(self.handle, a), "mdp_plan_leaders")
+        return list(a)
 
     def table_offsets(self, sub: int) -> dict:
         a = (C.c_longlong * 7)()

@@ -12,6 +12,7 @@ MDP_AP_DIRICHLET4, MDP_AP_DIRX_SOMMY = 0, 1
 MDP_OUT_Q, MDP_OUT_P = 0, 1
 MDP_PLAN_HOST_ONLY = 0x1
 MDP_PLAN_GRAPH = 0x2
+MDP_PLAN_DEDUPE = 0x4
 
 EXPORTED = [
     "mdp_ap_plan", "mdp_plan_update_k", "mdp_plan_layout", "mdp_plan_output_size", "mdp_project_batch",
@@ -56,6 +57,7 @@ def lib():
         "mdp_plan_update_k_stream": (i, [vp, C.POINTER(d), vp]),
         "mdp_plan_table_sizes": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
         "mdp_plan_update_bytes": (ll, [vp]),
+        "mdp_plan_leaders": (i, [vp, C.POINTER(i)]),
         "mdp_probe_rcp": (i, [vp, vp, i, vp]),
         "mdp_plan_read_tables": (i, [vp, i, vp, vp]),
         "mdp_plan_table_offsets": (i, [vp, i, C.POINTER(ll)]),

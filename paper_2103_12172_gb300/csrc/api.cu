@@ -37,14 +37,12 @@ void free_device(mdp_plan *p) {
   p->d_fstatus = nullptr;
   p->sub_stage.release();
   p->h_fstatus.release();
-  for (auto x : p->d_wave_items) cudaFree(x);
-  for (auto x : p->d_wave_prefix) cudaFree(x);
-  for (auto x : p->d_gwave_items) cudaFree(x);
-  for (auto x : p->d_gwave_prefix) cudaFree(x);
-  p->d_wave_items.clear();
-  p->d_wave_prefix.clear();
-  p->d_gwave_items.clear();
-  p->d_gwave_prefix.clear();
+  for (int k = 0; k < 3; ++k) {
+    for (auto x : p->d_items[k]) cudaFree(x);
+    for (auto x : p->d_prefix[k]) cudaFree(x);
+    p->d_items[k].clear();
+    p->d_prefix[k].clear();
+  }
   p->d_subs = nullptr; p->d_tables = nullptr; p->d_piv = nullptr; p->d_ws = nullptr; p->d_status = nullptr;
   if (prev >= 0) cudaSetDevice(prev);
 }
@@ -72,11 +70,11 @@ mdp_status alloc_device(mdp_plan *p) {
   CK(cudaMemset(p->d_fstatus, 0, sizeof(int)));
   mdp_status st = upload_subs_tables(p);
   if (st != MDP_OK) return st;
-  for (int pass = 0; pass < 2; ++pass) {
-    auto &waves = pass ? p->gwaves : p->waves;
-    auto &ditems = pass ? p->d_gwave_items : p->d_wave_items;
-    auto &dpre = pass ? p->d_gwave_prefix : p->d_wave_prefix;
-    auto &hpre = pass ? p->h_gwave_prefix : p->h_wave_prefix;
+  for (int sc = 0; sc < 3; ++sc) {
+    auto &waves = p->sched[sc];
+    auto &ditems = p->d_items[sc];
+    auto &dpre = p->d_prefix[sc];
+    auto &hpre = p->h_prefix[sc];
     hpre.clear();
     for (auto &w : waves) {
       const int n = (int)w.items.size();
@@ -99,16 +97,15 @@ mdp_status alloc_device(mdp_plan *p) {
   return MDP_OK;
 }
 
-void wave_batches(const mdp_plan *p, size_t w, Batch *fb, bool grad = false) {
-  const auto &waves = grad ? p->gwaves : p->waves;
-  const int n = (int)waves[w].items.size();
+void wave_batches(const mdp_plan *p, size_t w, Batch *fb, int sc) {
+  const int n = (int)p->sched[sc][w].items.size();
   for (int f = 0; f < NFAM; ++f) {
     Batch &b = fb[f];
     std::memset(&b, 0, sizeof b);
-    b.items = grad ? p->d_gwave_items[w] : p->d_wave_items[w];
-    b.prefix = (grad ? p->d_gwave_prefix[w] : p->d_wave_prefix[w]) + (size_t)f * (n + 1);
+    b.items = p->d_items[sc][w];
+    b.prefix = p->d_prefix[sc][w] + (size_t)f * (n + 1);
     b.n_items = n;
-    b.total_blocks = (grad ? p->h_gwave_prefix[w] : p->h_wave_prefix[w])[(size_t)f * (n + 1) + n];
+    b.total_blocks = p->h_prefix[sc][w][(size_t)f * (n + 1) + n];
   }
 }
 
@@ -179,6 +176,7 @@ mdp_status mdp_ap_plan(const mdp_subdomain *subs, int n_subs, unsigned flags, md
 mdp_status mdp_ap_plan_ex(const mdp_subdomain *subs, int n_subs, unsigned flags, const mdp_plan_options *opt,
                           mdp_plan **out) {
   if (!subs || n_subs < 1 || !out) return MDP_ERR_ARG;
+  if (flags & ~(MDP_PLAN_HOST_ONLY | MDP_PLAN_GRAPH | MDP_PLAN_DEDUPE)) return MDP_ERR_ARG;
   if (opt && (opt->tile_cols < 0 || opt->workspace_bytes < 0)) return MDP_ERR_ARG;
   *out = nullptr;
   mdp_plan *p = new (std::nothrow) mdp_plan();
@@ -274,6 +272,12 @@ mdp_status mdp_plan_read_tables(const mdp_plan *p, int device_side, double *tabl
   return MDP_OK;
 }
 
+mdp_status mdp_plan_leaders(const mdp_plan *p, int *leader) {
+  if (!p || !leader) return MDP_ERR_ARG;
+  for (int i = 0; i < p->n_subs; ++i) leader[i] = p->leader[i];
+  return MDP_OK;
+}
+
 mdp_status mdp_plan_layout(const mdp_plan *p, int sub, int *gamma_size, int *n_cols, long long *out_offset,
                            const int **gamma_nm) {
   if (!p || sub < 0 || sub >= p->n_subs) return MDP_ERR_ARG;
@@ -298,13 +302,26 @@ mdp_status mdp_project_batch_rec(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, m
   if (xi && (const void *)xi == (const void *)out) return MDP_ERR_ARG;
   CK(cudaSetDevice(p->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // basis columns without receivers: with duplicates, only the distinct subdomains are solved
+  // and their blocks copied to the duplicates
+  const bool dedupe = !xi && !out_rec && !p->sched[S_BASIS].empty();
+  const int sc = dedupe ? S_BASIS : S_PROJ;
   auto launch_all = [&]() -> cudaError_t {
-    for (size_t w = 0; w < p->waves.size(); ++w) {
+    for (size_t w = 0; w < p->sched[sc].size(); ++w) {
       Batch fb[NFAM];
-      wave_batches(p, w, fb);
+      wave_batches(p, w, fb, sc);
       cudaError_t e = launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, (double2 *)out_rec, st);
       if (e != cudaSuccess) return e;
     }
+    if (dedupe)
+      for (int i = 0; i < p->n_subs; ++i) {
+        const int l = p->leader[i];
+        if (l == i) continue;
+        const SubDesc &d = p->subs[i].d;
+        cudaError_t e = cudaMemcpyAsync(out + d.out_off, out + p->subs[l].d.out_off,
+                                        (size_t)d.G * d.n_cols * sizeof(mdp_c64), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+      }
     return cudaSuccess;
   };
   if (!(p->flags & MDP_PLAN_GRAPH) || st == nullptr) {
@@ -379,9 +396,9 @@ mdp_status mdp_ap_adjoint_rec(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot
     return MDP_ERR_ARG;
   CK(cudaSetDevice(p->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  for (size_t w = 0; w < p->gwaves.size(); ++w) {
+  for (size_t w = 0; w < p->sched[S_GRAD].size(); ++w) {
     Batch fb[NFAM];
-    wave_batches(p, w, fb, true);
+    wave_batches(p, w, fb, S_GRAD);
     CK(launch_adjoint(p, fb, out_kind, (const double2 *)xi, (const double2 *)cot, (const double2 *)cot_rec,
                       (double2 *)grad_xi, grad_k, st));
   }
@@ -488,10 +505,10 @@ mdp_status mdp_plan_set_receivers(mdp_plan *p, const int *rows) {
   for (auto &hs : p->subs) ds.push_back(hs.d);
   CK(cudaMemcpy(p->d_subs, ds.data(), ds.size() * sizeof(SubDesc), cudaMemcpyHostToDevice));
   // the receiver kernel's block counts changed: refresh the prefix sums (same sizes)
-  for (int pass = 0; pass < 2; ++pass) {
-    auto &waves = pass ? p->gwaves : p->waves;
-    auto &dpre = pass ? p->d_gwave_prefix : p->d_wave_prefix;
-    auto &hpre = pass ? p->h_gwave_prefix : p->h_wave_prefix;
+  for (int sc = 0; sc < 3; ++sc) {
+    auto &waves = p->sched[sc];
+    auto &dpre = p->d_prefix[sc];
+    auto &hpre = p->h_prefix[sc];
     for (size_t w = 0; w < waves.size(); ++w) {
       const int n = (int)waves[w].items.size();
       auto &pre = hpre[w];

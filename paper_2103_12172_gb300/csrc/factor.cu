@@ -125,6 +125,18 @@ __device__ __forceinline__ bool lu_step(cplx &g, cplx &u, cplx lsub, cplx gn, cp
 
 __device__ __forceinline__ void set_error(int *status, int code) { atomicCAS(status, 0, code); }
 
+// Subdomain of mode number t over the modes of the subdomains that own their tables (duplicates
+// share their leader's); t becomes the mode index within it. n_subs if t is past the end.
+__device__ __forceinline__ int mode_owner(const SubDesc *subs, int n_subs, int &t) {
+  int si = 0;
+  for (; si < n_subs; ++si) {
+    if (subs[si].leader != si) continue;
+    if (t < subs[si].Nq) break;
+    t -= subs[si].Nq;
+  }
+  return si;
+}
+
 // The pivoted LU of rows 0..n-1 of T_q (diagonal of row `mod` reduced by sigma), calling
 // out(i, l, d, dinv, du, du2, sw) for every row in order. Interior steps (real a, dd entries,
 // super-diagonal of the pivot row still the original a) that keep the pivot take the fast path
@@ -256,8 +268,7 @@ __global__ void __launch_bounds__(32) k_factor_chain(const SubDesc *subs, int n_
   if (t >= 2 * n_modes) return;
   const bool sweep = t >= n_modes;
   if (sweep) t -= n_modes;
-  int si = 0;
-  while (si < n_subs && t >= subs[si].Nq) { t -= subs[si].Nq; ++si; }
+  int si = mode_owner(subs, n_subs, t);
   if (si >= n_subs) return;
   if (sweep) chain_sweep(subs[si], t + 1, tab, status);
   else chain_full(subs[si], t + 1, tab, piv, status);
@@ -276,8 +287,7 @@ __global__ void __launch_bounds__(kRowsThreads) k_factor_rows(const SubDesc *sub
   __shared__ RunReduce run;
   __shared__ double raw[(kRowsThreads + 1) * 11];
   int t = blockIdx.x;
-  int si = 0;
-  while (si < n_subs && t >= subs[si].Nq) { t -= subs[si].Nq; ++si; }
+  const int si = mode_owner(subs, n_subs, t);
   if (si >= n_subs) return;
   const SubDesc &d = subs[si];
   const int q = t + 1, tid = threadIdx.x;
@@ -404,7 +414,8 @@ __global__ void k_probe_rcp(const double *x, double *y, int n) {
 // FP64 unit while there are fewer warps than SMs. The row kernel: one block per mode.
 cudaError_t launch_factor(const mdp_plan *p, int *status, cudaStream_t st) {
   int n_modes = 0;
-  for (auto &hs : p->subs) n_modes += hs.d.Nq;
+  for (size_t i = 0; i < p->subs.size(); ++i)
+    if (p->subs[i].d.leader == (int)i) n_modes += p->subs[i].d.Nq;
   const int threads = 2 * n_modes;
   k_factor_chain<<<(threads + 31) / 32, 32, 0, st>>>(p->d_subs, (int)p->subs.size(), n_modes, p->d_tables,
                                                       p->d_piv, status);

@@ -154,17 +154,86 @@ __global__ void __launch_bounds__(256) k_residual(Batch bt, const SubDesc *subs,
 }
 
 // ---------------------------------------------------------------- k_fwd_rows
-// ghat(q, row) = sum_m sin(pi q m / Nx) r(m, row) for the 4 dense ring rows. A thread handles
-// the mode pair (q, Nx - q): sin(pi (Nx-q) m/Nx) = (-1)^(m+1) sin(pi q m/Nx), so the odd-m and
-// even-m partial sums give both modes.
+// ghat(q, row) = sum_m sin(pi q m / Nx) r(m, row) for the 4 dense ring rows.
+//
+// FFT form (Nx a power of 2): with the odd extension x~(m) = r(m), x~(2Nx - m) = -r(m), the
+// length-2Nx DFT is V[q] = -2i ghat(q). Real ring data (basis columns) pack two rows of the same
+// column per transform, x~ = r_a + i r_b (rows nlo, nlo+1 and nhi-1, nhi): then
+// V = 2 ghat_b - 2i ghat_a, so ghat_a = -Im V / 2 and ghat_b = Re V / 2, and a column's result
+// does not depend on its neighbours. One block: one ring row (or row pair) and fpb columns.
+//
+// Direct form: a thread handles the mode pair (q, Nx - q): sin(pi (Nx-q) m/Nx) =
+// (-1)^(m+1) sin(pi q m/Nx), so the odd-m and even-m partial sums give both modes.
 template <bool CIN>
-__global__ void __launch_bounds__(128) k_fwd_rows(Batch bt, const SubDesc *subs, const double *tab, double *ws) {
+__device__ __forceinline__ void fwd_rows_fft(const Item &it, const SubDesc &d, const double *tab, double *ws,
+                                             int local, double2 *sm) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int rr = local & 3, cblk = local >> 2;
+  if (!CIN && (rr & 1)) return;                        // real data: rows rr, rr + 1 in one block
+  const int b0 = cblk * d.fpb, nf = min(d.fpb, it.ncols - b0);
+  const int Nx = d.Nx, L = 2 * Nx;
+  int lg = 0;
+  while ((1 << lg) < L) ++lg;
+  const double *r = ws + it.r_off;
+  const long long nc = it.ncols;
+  const int P = d.Px, Mr = 4 * (d.Py - 4);
+  // r(m) of ring row `row`, column b (m in [mlo, mhi]); x-centred subdomains store the pairs
+  // (r(m) + r(Nx-m), r(m) - r(Nx-m)) for m <= Nx/2 (at m = Nx/2 both slots hold r)
+  auto rval = [&](int row, int m, int b) -> cplx {
+    if (d.xsym) {
+      const int mm = m <= Nx / 2 ? m : Nx - m;
+      const long long slot = (long long)row * 2 * d.Ph + 2 * (mm - d.mlo);
+      const cplx p0 = CIN ? ld2(r + 2 * (slot * nc + b)) : cmk(r[slot * nc + b], 0.0);
+      if (2 * mm == Nx) return p0;
+      const cplx p1 = CIN ? ld2(r + 2 * ((slot + 1) * nc + b)) : cmk(r[(slot + 1) * nc + b], 0.0);
+      const cplx h = m <= Nx / 2 ? cadd(p0, p1) : csub(p0, p1);
+      return cmk(0.5 * h.re, 0.5 * h.im);
+    }
+    const int rb = row == 0 ? 0 : row == 1 ? P : row == 2 ? 2 * P + Mr : 3 * P + Mr;
+    const long long slot = rb + (m - d.mlo);
+    return CIN ? ld2(r + 2 * (slot * nc + b)) : cmk(r[slot * nc + b], 0.0);
+  };
+  for (int idx = tid; idx < d.fpb * L; idx += nt) {
+    const int f = idx >> lg, n = idx & (L - 1);
+    double2 v = make_double2(0.0, 0.0);
+    const int m = n <= Nx ? n : L - n;
+    const double sgn = n <= Nx ? 1.0 : -1.0;
+    if (f < nf && m >= d.mlo && m <= d.mhi) {
+      if (CIN) {
+        const cplx x = rval(rr, m, b0 + f);
+        v = make_double2(sgn * x.re, sgn * x.im);
+      } else {
+        v = make_double2(sgn * rval(rr, m, b0 + f).re, sgn * rval(rr + 1, m, b0 + f).re);
+      }
+    }
+    sm[(f << lg) + brev_lg(n, lg)] = v;
+  }
+  __syncthreads();
+  fft_r2_stages(sm, d.fpb, Nx, lg, tab + d.sin_off);
+  double *gr = ws + it.gr_off;
+  for (int idx = tid; idx < nf * d.Nq; idx += nt) {
+    const int f = idx % nf, q = idx / nf + 1;
+    const double2 V = sm[(f << lg) + q];
+    const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b0 + f;
+    if (CIN) {
+      st2(gr + 2 * o, cmk(-0.5 * V.y, 0.5 * V.x));
+    } else {
+      gr[o] = -0.5 * V.y;
+      gr[o + (long long)d.Nq * nc] = 0.5 * V.x;       // row rr + 1
+    }
+  }
+}
+
+template <bool CIN>
+__global__ void __launch_bounds__(256) k_fwd_rows(Batch bt, const SubDesc *subs, const double *tab, double *ws) {
+  extern __shared__ double2 fft_sm[];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
   const SubDesc &d = subs[it.sub];
+  if (d.rows_fft) { fwd_rows_fft<CIN>(it, d, tab, ws, local, fft_sm); return; }
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
-  const int q = (local / cb) * 4 + threadIdx.y + 1;
+  const int q = (local / cb) * 8 + threadIdx.y + 1;
   if (b >= it.ncols || q > d.Nx / 2) return;
   const double *S = tab + d.sin_off;
   const int N2 = 2 * d.Nx, P = d.Px, Mr = 4 * (d.Py - 4);
@@ -946,6 +1015,8 @@ static constexpr int FFT_SMEM = FFT_POINTS * 16;  // bytes: fpb x 2Nx complex va
 cudaError_t set_kernel_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_inv_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
   if (e == cudaSuccess) e = set_adj_kernel_attributes();
   return e;
 }
@@ -968,8 +1039,8 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
   if (basis) MDP_LAUNCH(F_EXT, k_extend<<<grid1(fb[F_EXT].total_blocks), 128, 0, st>>>(fb[F_EXT], ds, tab, ws, 0));
   if (basis) MDP_LAUNCH(F_RES, k_residual<false, false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
   else MDP_LAUNCH(F_RES, k_residual<true, false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
-  if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
-  else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
+  if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_FROWS], ds, tab, ws));
+  else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_FROWS], ds, tab, ws));
   if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   else MDP_LAUNCH(F_TRI, k_tri<true, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   if (basis) {
@@ -995,8 +1066,8 @@ cudaError_t launch_adjoint(mdp_plan *p, const Batch *fb, int out_kind, const dou
     if (basis) MDP_LAUNCH(F_EXT, k_extend<<<grid1(fb[F_EXT].total_blocks), 128, 0, st>>>(fb[F_EXT], ds, tab, ws, 1));
     if (basis) MDP_LAUNCH(F_RES, k_residual<false, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
     else MDP_LAUNCH(F_RES, k_residual<true, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
-    if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
-    else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b4, 0, st>>>(fb[F_FROWS], ds, tab, ws));
+    if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_FROWS], ds, tab, ws));
+    else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_FROWS], ds, tab, ws));
     if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
     else MDP_LAUNCH(F_TRI, k_tri<true, true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   }

@@ -36,7 +36,7 @@ struct SubDesc {
   int nrec;         // receiver row (nlo+1 .. nhi-1) or -1; receivers m = mlo+1 .. mhi-1
   int rows_fft;     // inverse transform of the gamma rows by FFT (Nx a power of 2, 2Nx <= 4096)
   int fpb;          // FFTs (columns) per block of that kernel: 4096 / (2 Nx)
-  int pad2;
+  int leader;       // index of the subdomain owning this one's tables (itself unless deduplicated)
   double h, k;
   double x0, x1, y0, y1, ax0, ay0;
   double c0, c1, c2;  // 9-point coefficients: centre, edge, corner (Eq. FD_scheme)
@@ -146,8 +146,11 @@ struct mdp_plan {
   long long rec_size = 0;
   int tile_cols = 256;                   // columns per work item
   long long ws_budget = 0;               // bytes of workspace
-  std::vector<mdp::Wave> waves;          // batch schedule of mdp_project_batch
-  std::vector<mdp::Wave> gwaves;         // batch schedule of mdp_ap_adjoint (larger workspace)
+  // batch schedules: [S_PROJ] mdp_project_batch over every subdomain, [S_GRAD] mdp_ap_adjoint
+  // (larger workspace), [S_BASIS] basis columns of the distinct subdomains only (MDP_PLAN_DEDUPE
+  // with duplicates; else empty)
+  std::vector<mdp::Wave> sched[3];
+  std::vector<int> leader;               // per subdomain: the subdomain whose tables and basis columns it shares
   // device side
   mdp::SubDesc *d_subs = nullptr;
   double *d_tables = nullptr;
@@ -159,10 +162,10 @@ struct mdp_plan {
   mdp::HostBuf<mdp::SubDesc> sub_stage;  // pinned copy of the subdomain descriptors (async upload)
   mdp::HostBuf<int> h_fstatus;           // pinned read-back of d_fstatus
   bool host_stale = false;               // device tables refactored since the host tables were built
-  // per wave: device items and prefix arrays (one prefix array per kernel family)
-  std::vector<mdp::Item *> d_wave_items, d_gwave_items;
-  std::vector<int *> d_wave_prefix, d_gwave_prefix;  // [wave] -> device int [NFAM][n_items + 1]
-  std::vector<std::vector<int>> h_wave_prefix, h_gwave_prefix;
+  // per schedule and wave: device items and prefix arrays (one prefix array per kernel family)
+  std::vector<mdp::Item *> d_items[3];
+  std::vector<int *> d_prefix[3];        // [wave] -> device int [NFAM][n_items + 1]
+  std::vector<std::vector<int>> h_prefix[3];
   // CUDA graphs of mdp_project_batch, keyed by (xi, out, kind, stream)
   struct GraphEntry { const void *xi; void *out; void *out_rec; int kind; cudaStream_t st; cudaGraphExec_t exec; };
   std::vector<GraphEntry> graphs;
@@ -173,6 +176,8 @@ struct mdp_plan {
 };
 
 namespace mdp {
+
+enum Sched { S_PROJ = 0, S_GRAD = 1, S_BASIS = 2 };
 
 // kernel families (each has its own block decomposition of an item); F_A* are the adjoint's
 enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_ARINGC, F_AGAM, F_IREC,
@@ -185,7 +190,9 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
   switch (f) {
     case F_EXT: return (d.G + 127) / 128;
     case F_RES: return cb * (((d.xsym ? 4 * d.Ph + 2 * (d.Py - 4) : d.R) + 7) / 8);
-    case F_FROWS: return cb * ((d.Nx / 2 + 3) / 4);
+    case F_FROWS:
+      if (d.rows_fft) return 4 * ((ncols + d.fpb - 1) / d.fpb);
+      return cb * ((d.Nx / 2 + 7) / 8);
     case F_TRI: return cb * ((d.Nq + 3) / 4);
     case F_IROWS:
       if (d.rows_fft) return 4 * ((ncols + d.fpb - 1) / d.fpb);

@@ -327,6 +327,7 @@ static mdp_status factor_all(std::vector<HostSub> &subs) {
   std::vector<std::pair<int, int>> tasks;
   for (int si = 0; si < (int)subs.size(); ++si) {
     prepare_tables(subs[si]);
+    if (subs[si].d.leader != si) continue;   // a duplicate shares its leader's tables
     for (int q = 1; q <= subs[si].d.Nq; ++q) tasks.push_back({si, q});
   }
   const int nthr = (int)std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
@@ -344,6 +345,8 @@ static mdp_status factor_all(std::vector<HostSub> &subs) {
   for (int i = 1; i < nthr; ++i) pool.emplace_back(worker);
   worker();
   for (auto &th : pool) th.join();
+  for (int si = 0; si < (int)subs.size(); ++si)
+    if (subs[si].d.leader != si) subs[si].seg = subs[subs[si].d.leader].seg;
   return (mdp_status)status.load();
 }
 
@@ -392,6 +395,13 @@ static bool layout_tables(mdp_plan *p) {
   auto al = [](long long v) { return (v + 31) & ~31LL; };
   for (auto &hs : p->subs) {
     SubDesc &d = hs.d;
+    if (d.leader != (int)(&hs - p->subs.data())) {   // a duplicate: the leader's tables
+      const SubDesc &ld = p->subs[d.leader].d;
+      d.fact_off = ld.fact_off; d.dT_off = ld.dT_off; d.sin_off = ld.sin_off; d.geo_off = ld.geo_off;
+      d.seg_off = ld.seg_off; d.fs_off = ld.fs_off; d.piv_off = ld.piv_off;
+      d.out_off = out;  out += (long long)d.G * d.n_cols;
+      continue;
+    }
     const int FW = d.cplx ? 8 : 4;
     d.fact_off = off; off += al((long long)d.Nq * d.Nt * FW);
     d.dT_off = off;   off += al((long long)d.Nq * d.Nt * 6);
@@ -418,6 +428,7 @@ static bool layout_tables(mdp_plan *p) {
 static void fill_tables(mdp_plan *p) {
   for (auto &hs : p->subs) {
     const SubDesc &d = hs.d;
+    if (d.leader != (int)(&hs - p->subs.data())) continue;
     double *S = &p->host_tables[d.sin_off];
     for (int j = 0; j < 2 * d.Nx; ++j) {
       S[j] = std::sin(M_PI * (double)j / (double)d.Nx);
@@ -434,12 +445,13 @@ static void fill_tables(mdp_plan *p) {
   }
 }
 
-static void schedule_pass(mdp_plan *p, bool grad, std::vector<Wave> &waves) {
+static void schedule_pass(mdp_plan *p, bool grad, bool leaders_only, std::vector<Wave> &waves) {
   waves.clear();
   Wave cur;
   cur.ws_doubles = 0;
   const long long budget = p->ws_budget / 8;
   for (int si = 0; si < (int)p->subs.size(); ++si) {
+    if (leaders_only && p->leader[si] != si) continue;
     const SubDesc &d = p->subs[si].d;
     for (int c0 = 0; c0 < d.n_cols; c0 += p->tile_cols) {
       Item it;
@@ -464,12 +476,47 @@ static void schedule_pass(mdp_plan *p, bool grad, std::vector<Wave> &waves) {
 }
 
 static void schedule(mdp_plan *p) {
-  schedule_pass(p, false, p->waves);
-  schedule_pass(p, true, p->gwaves);
+  schedule_pass(p, false, false, p->sched[S_PROJ]);
+  schedule_pass(p, true, false, p->sched[S_GRAD]);
+  bool dups = false;
+  for (int i = 0; i < (int)p->subs.size(); ++i) dups = dups || p->leader[i] != i;
+  if (dups) schedule_pass(p, false, true, p->sched[S_BASIS]);
+  else p->sched[S_BASIS].clear();
   long long mx = 0;
-  for (auto &w : p->waves) mx = std::max(mx, w.ws_doubles);
-  for (auto &w : p->gwaves) mx = std::max(mx, w.ws_doubles);
+  for (auto &sc : p->sched)
+    for (auto &w : sc) mx = std::max(mx, w.ws_doubles);
   p->ws_doubles = mx;
+}
+
+// Two subdomains pose the same auxiliary problem when they agree in every quantity the tables
+// and the columns depend on: grid, step, wavenumber, AP type, modes, the index sets, and the
+// gamma geometry relative to the grid (ownership, foot point, distance, side length) up to
+// rounding of the placement.
+static bool same_problem(const HostSub &a, const HostSub &b) {
+  const SubDesc &x = a.d, &y = b.d;
+  if (x.nx != y.nx || x.ny != y.ny || x.h != y.h || x.k != y.k || x.ap_bc != y.ap_bc || x.n_modes != y.n_modes ||
+      x.mlo != y.mlo || x.mhi != y.mhi || x.nlo != y.nlo || x.nhi != y.nhi || x.G != y.G || x.nfirst != y.nfirst ||
+      x.i0 != y.i0 || x.xsym != y.xsym)
+    return false;
+  const double tol = 1e-12 * x.h;
+  for (int i = 0; i < x.G; ++i) {
+    if (a.owner[i] != b.owner[i] || std::fabs(a.rho[i] - b.rho[i]) > tol || std::fabs(a.s[i] - b.s[i]) > 1e-12 ||
+        std::fabs(a.L[i] - b.L[i]) > tol)
+      return false;
+  }
+  return true;
+}
+
+static void find_leaders(mdp_plan *p) {
+  const int n = (int)p->subs.size();
+  p->leader.resize(n);
+  for (int i = 0; i < n; ++i) {
+    p->leader[i] = i;
+    if (!(p->flags & MDP_PLAN_DEDUPE)) continue;
+    for (int j = 0; j < i; ++j)
+      if (p->leader[j] == j && same_problem(p->subs[i], p->subs[j])) { p->leader[i] = j; break; }
+  }
+  for (int i = 0; i < n; ++i) p->subs[i].d.leader = p->leader[i];
 }
 
 mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n) {
@@ -478,6 +525,7 @@ mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n) {
     mdp_status st = geometry(subs[i], p->subs[i]);
     if (st != MDP_OK) return st;
   }
+  find_leaders(p);
   if (!layout_tables(p)) return MDP_ERR_NOMEM;
   mdp_status st = factor_all(p->subs);
   if (st != MDP_OK) return st;
@@ -489,6 +537,7 @@ mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n) {
 mdp_status set_k_fields(mdp_plan *p, const double *k) {
   for (int i = 0; i < (int)p->subs.size(); ++i) {
     if (!(k[i] > 0) || !std::isfinite(k[i])) return MDP_ERR_ARG;
+    if (k[i] != k[p->leader[i]]) return MDP_ERR_ARG;   // deduplicated subdomains keep one k
   }
   for (int i = 0; i < (int)p->subs.size(); ++i) {
     HostSub &hs = p->subs[i];

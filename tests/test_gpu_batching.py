@@ -63,3 +63,63 @@ def test_autotuner_picks_a_candidate_and_caches(mdp, tmp_path):
     t = tune_tile(subs, candidates=(8, 16, 32), cache_path=path)
     assert t in (8, 16, 32)
     assert tune_tile(subs, candidates=(8, 16, 32), cache_path=path) == t
+
+
+def test_dedupe_projection_adjoint_and_graph_match_the_plain_plan(mdp):
+    """MDP_PLAN_DEDUPE on the 2 x 2 decomposition (four identical subdomains, 129^2): basis
+    columns computed once and copied, user densities and the adjoint per subdomain on the shared
+    tables, graph replay -- all equal to the plan without deduplication."""
+    import numpy as np
+    subs = [W.unit_subdomain(i, j, 129, 12.0, W.AP_DIRX_SOMMY, 6) for j in range(2) for i in range(2)]
+    plain = mdp.Plan(subs, tile_cols=32)
+    dd = mdp.Plan(subs, tile_cols=32, dedupe=True)
+    assert dd.leaders() == [0, 0, 0, 0]
+    ref = plain.project().cpu().numpy()
+    got = dd.project().cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    blocks = dd.blocks(torch.from_numpy(got))
+    assert all(torch.equal(b, blocks[0]) for b in blocks[1:])
+    xi = torch.from_numpy(W.random_complex((plain.output_size,), seed=21)).cuda()
+    r1 = plain.project(xi=xi).cpu().numpy()
+    r2 = dd.project(xi=xi).cpu().numpy()
+    assert np.abs(r2 - r1).max() <= 1e-13 * np.abs(r1).max()
+    cot = torch.from_numpy(W.random_complex((plain.output_size,), seed=22)).cuda()
+    g1, k1 = plain.adjoint(cot, xi=xi)
+    g2, k2 = dd.adjoint(cot, xi=xi)
+    assert torch.allclose(g2, g1, rtol=0, atol=1e-13 * g1.abs().max().item())
+    assert torch.allclose(k2, k1, rtol=1e-11, atol=0)
+    gplan = mdp.Plan(subs, tile_cols=32, dedupe=True, graph=True)
+    s = torch.cuda.Stream()
+    out = torch.empty(gplan.output_size, dtype=torch.complex128, device="cuda")
+    with torch.cuda.stream(s):
+        gplan.project(out=out)
+        out.zero_()
+        gplan.project(out=out)      # replay of the captured graph, copies included
+    s.synchronize()
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_qcache_stores_loads_and_fills_missing_blocks(mdp, tmp_path):
+    """QCache: the first call computes and stores one file per distinct problem; the second loads
+    them; a deleted entry is recomputed alone. Translated copies of a subdomain share one entry,
+    so their blocks agree with their own computation to rounding (the placement differs in the
+    last bits), and exactly with each other."""
+    import os
+    from paper_2103_12172_gb300.qcache import QCache
+    subs = [W.unit_subdomain(i, 0, 65, 9.0, W.AP_DIRX_SOMMY, 4) for i in range(3)]
+    subs.append(W.unit_subdomain(3, 0, 65, 11.0, W.AP_DIRX_SOMMY, 4))
+    plan = mdp.Plan(subs, tile_cols=16)
+    ref = plan.project().cpu().numpy()
+    cache = QCache(str(tmp_path))
+    first = cache.project(plan).cpu().numpy()
+    assert np.array_equal(first, ref)
+    files = sorted(os.listdir(tmp_path))
+    assert len(files) == 2 and all(f.endswith(".npy") for f in files)
+    tol = 1e-13 * np.abs(ref).max()
+    second = cache.project(plan).cpu().numpy()
+    assert np.abs(second - ref).max() <= tol
+    b2 = plan.blocks(torch.from_numpy(second))
+    assert torch.equal(b2[1], b2[0]) and torch.equal(b2[2], b2[0]) and torch.equal(b2[3], plan.blocks(torch.from_numpy(ref))[3])
+    os.remove(os.path.join(tmp_path, files[0]))
+    third = cache.project(plan).cpu().numpy()
+    assert np.abs(third - ref).max() <= tol and len(os.listdir(tmp_path)) == 2

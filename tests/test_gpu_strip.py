@@ -123,3 +123,41 @@ def test_receiver_output_and_its_adjoint_match_oracle(mdp, ap, n):
     gxr, _ = S.adjoint(cot, xi=xi, cot_rec=crec, rec_row=row)
     gx = gx.cpu().numpy().reshape(nc, G)
     assert (np.abs(gx - gxr).max(axis=1) / np.abs(gxr).max(axis=1)).max() < 1e-10
+
+
+def test_layered_transmission_converges_fourth_order_on_gpu(mdp):
+    """End to end on the GPU (projection columns, receivers, DD coupling): a plane wave normally
+    incident on two layers (k = 5 | 9), impedance data of the exact transmission solution
+    (Appendix A) on the outer vertical sides, du/dn = 0 on the horizontal ones. The receiver
+    values converge to the exact solution at fourth order in h."""
+    from exact_solutions import layered_exact
+    from paper_2103_12172_gb300.strip import LayeredStrip
+    ks = [5.0, 9.0]
+    u, du = layered_exact(ks, [1.0])
+    errs = []
+    for n in (33, 65, 129, 257):
+        subs = [W.unit_subdomain(j, 0, n, k, W.AP_DIRX_SOMMY, 16) for j, k in enumerate(ks)]
+
+        def bc(j, side, kj, x, y, subs=subs):
+            if side in (1, 2):
+                return 0.0, 1.0, torch.zeros_like(x, dtype=torch.complex128)
+            xs = subs[j].x0 if side == 3 else subs[j].x1
+            sign = -1.0 if side == 3 else 1.0
+            ik = 1j * ks[j]
+            val = sign * du(j, xs) + ik * u(j, xs)
+            return ik, 1.0, torch.full(x.shape, complex(val), dtype=torch.complex128, device=x.device)
+
+        rows = []
+        for s_ in subs:
+            yy = s_.ay0 + np.arange(s_.ny) * s_.h
+            rows.append(int(np.argmin(np.abs(yy - 0.5))))
+        strip = LayeredStrip(subs, bc, rows)
+        got = [g.detach().cpu().numpy() for g in strip.receivers(torch.tensor(ks, dtype=torch.float64))]
+        err = 0.0
+        for j, s_ in enumerate(subs):
+            _, m0, cnt, _ = strip.rlayout[j]
+            ex = u(j, s_.ax0 + (m0 + np.arange(cnt)) * s_.h)
+            err = max(err, np.abs(got[j] - ex).max() / np.abs(ex).max())
+        errs.append(err)
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[-1] < 1e-6 and np.all(rates > 3.4), (errs, rates)

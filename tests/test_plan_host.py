@@ -159,3 +159,50 @@ def test_host_refactor_equals_fresh_plan_and_table_readback(mdp):
     with pytest.raises(MdpError) as e:
         p1.read_tables(True)
     assert e.value.code == 6  # MDP_ERR_STATE
+
+
+def test_dedupe_groups_identical_subdomains_and_shares_tables(mdp):
+    """MDP_PLAN_DEDUPE: the four identical 2 x 2 subdomains share the first one's tables; the
+    checkerboard forms two groups; different k or grids never group."""
+    from paper_2103_12172_gb300 import MdpError
+    subs = list(W.dd2x2_257().subdomains)
+    p = mdp.Plan(subs, host_only=True, dedupe=True)
+    assert p.leaders() == [0, 0, 0, 0]
+    assert mdp.Plan(subs, host_only=True).leaders() == [0, 1, 2, 3]
+    offs = [p.table_offsets(i) for i in range(4)]
+    assert all(o == offs[0] for o in offs)
+    single = mdp.Plan(subs[:1], host_only=True)
+    assert int(p.L.mdp_plan_table_bytes(p.handle)) == int(single.L.mdp_plan_table_bytes(single.handle))
+    # output blocks stay separate
+    assert [p.layout(i)[2] for i in range(4)] == [i * p.layout(0)[0] * p.layout(0)[1] for i in range(4)]
+    assert mdp.Plan(list(W.checker2x2().subdomains), host_only=True, dedupe=True).leaders() == [0, 1, 1, 0]
+    mixed = [subs[0], subs[1].with_k(31.0), subs[2], W.small_subdomain(65, 30.0, W.AP_DIRX_SOMMY, 32)]
+    assert mdp.Plan(mixed, host_only=True, dedupe=True).leaders() == [0, 1, 0, 3]
+    # a duplicate answers host introspection from the shared tables
+    b = W.random_complex((2 * subs[0].nx,), seed=4)[: p.sub_info(0)["Nt"]]
+    b = np.ascontiguousarray(b)
+    x0 = np.empty_like(b)
+    x3 = np.empty_like(b)
+    import ctypes
+    p.L.mdp_host_mode_solve(p.handle, 0, 7, 0, b.ctypes.data_as(ctypes.c_void_p), x0.ctypes.data_as(ctypes.c_void_p))
+    p.L.mdp_host_mode_solve(p.handle, 3, 7, 0, b.ctypes.data_as(ctypes.c_void_p), x3.ctypes.data_as(ctypes.c_void_p))
+    assert np.array_equal(x0, x3)
+    # one k per group
+    with pytest.raises(MdpError) as e:
+        p.update_k([30.0, 30.0, 31.0, 30.0])
+    assert e.value.code == 1  # MDP_ERR_ARG
+    p.update_k([31.0] * 4)
+
+
+def test_qcache_key_is_translation_invariant_and_complete():
+    """The persisted Q cache keys a block by its auxiliary problem: translated copies share a key;
+    k, M*, the AP type, the grid, the placement and the output kind each change it."""
+    from paper_2103_12172_gb300.qcache import problem_key
+    a = W.unit_subdomain(0, 0, 129, 12.0, W.AP_DIRX_SOMMY, 6)
+    b = W.unit_subdomain(3, 5, 129, 12.0, W.AP_DIRX_SOMMY, 6)
+    assert problem_key(a, "Q") == problem_key(b, "Q")
+    others = [a.with_k(12.5), W.unit_subdomain(0, 0, 129, 12.0, W.AP_DIRX_SOMMY, 7),
+              W.unit_subdomain(0, 0, 129, 12.0, W.AP_DIRICHLET4, 6), W.unit_subdomain(0, 0, 65, 12.0, W.AP_DIRX_SOMMY, 6),
+              W.unit_subdomain(0, 0, 129, 12.0, W.AP_DIRX_SOMMY, 6, margin=0.2)]
+    keys = {problem_key(o, "Q") for o in others} | {problem_key(a, "P")}
+    assert problem_key(a, "Q") not in keys and len(keys) == len(others) + 1
