@@ -156,7 +156,13 @@ def kernel_flops(plan, items):
             add("k_inv_rows", nc * 4 * (4 * L + 5 * L * (lg - 2) + 2 * (Px + 2)))
         else:
             add("k_inv_rows", nc * 4 * ((Px // 2 + 2) if xs else (Px + 2)) * Nq * inv)
-        add("k_fwd_rows", nc * (Nx // 2) * 4 * ((Px + 1) // 2 if xs else Px) * 2)
+        if (Nx & (Nx - 1)) == 0 and 8 <= Nx <= 2048:
+            # one length-2Nx FFT per row pair of a column (real data packed as re/im)
+            L = 2 * Nx
+            lg = L.bit_length() - 1
+            add("k_fwd_rows", nc * 2 * (4 * L + 5 * L * (lg - 2)))
+        else:
+            add("k_fwd_rows", nc * (Nx // 2) * 4 * ((Px + 1) // 2 if xs else Px) * 2)
         add("k_residual", nc * R * 9 * 2)
     return tot
 
