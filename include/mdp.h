@@ -168,6 +168,21 @@ mdp_status mdp_ap_adjoint(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, md
 mdp_status mdp_ap_solve_batch(mdp_plan *p, int sub, int nrhs, const mdp_c64 *g, mdp_c64 *u,
                               int adjoint, void *cuda_stream);
 
+/* Difference potential on the whole grid (Eq. Potential_def; the reconstruction of the solution
+ * inside a subdomain from its boundary density, Section 3.5): u = w - G^(h) (L^(h) w)|M+ with
+ * w = xi on gamma and 0 elsewhere, for ncols densities of subdomain `sub`. xi: device
+ * [ncols][|gamma|] (gamma order of mdp_plan_layout); u: device [ncols][ny][nx], written on every
+ * node (on N+ it is P_N+ xi; u and xi must not overlap). Uses the plan's workspace: calls on one
+ * plan must not overlap in time. */
+mdp_status mdp_potential(mdp_plan *p, int sub, int ncols, const mdp_c64 *xi, mdp_c64 *u, void *cuda_stream);
+
+/* The extended basis densities xi_c = Ex Psi_c on gamma (Sections 3.2.3-3.2.4: the Taylor
+ * extension of the Chebyshev basis function of column c, zero on the nodes owned by other
+ * sides) for columns col0 .. col0+ncols-1 of subdomain `sub`: out device [ncols][|gamma|]
+ * (real values stored complex). A DD solution's density on gamma is the combination of these
+ * columns with its coefficients. Uses the plan's workspace. */
+mdp_status mdp_basis_densities(mdp_plan *p, int sub, int col0, int ncols, mdp_c64 *out, void *cuda_stream);
+
 /* The full-grid solve of mdp_ap_solve_batch without a plan and without any device
  * allocation, for callers that cannot call cudaMalloc (an allocator-free runtime, or a caller
  * that owns every device byte). The paper has no counterpart: this is an interface choice.

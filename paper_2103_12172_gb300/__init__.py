@@ -163,6 +163,34 @@ class Plan:
                                               _stream_ptr(stream)), "mdp_project_columns")
         return out
 
+    def potential(self, sub: int, xi, out=None, stream=None):
+        """Difference potential w - G (L w)|M+ on the whole grid of subdomain `sub` for densities
+        xi [ncols, |gamma|] (device complex128): tensor [ncols, ny, nx]."""
+        import torch
+        g = self.layout(sub)[0]
+        xi = xi.reshape(-1, g).contiguous()
+        ncols = xi.shape[0]
+        s = self.subdomains[sub]
+        if out is None:
+            out = torch.empty((ncols, s.ny, s.nx), dtype=torch.complex128, device="cuda")
+        self._check_dev(out, ncols * s.ny * s.nx, "out")
+        self._check_dev(xi, ncols * g, "xi")
+        _lib.check(self.L.mdp_potential(self.handle, sub, ncols, _ptr(xi), _ptr(out), _stream_ptr(stream)),
+                   "mdp_potential")
+        return out
+
+    def basis_densities(self, sub: int, col0: int = 0, ncols=None, out=None, stream=None):
+        """Extended basis densities Ex Psi_c on gamma: tensor [ncols, |gamma|] (complex128)."""
+        import torch
+        g, nc, _, _ = self.layout(sub)
+        ncols = nc - col0 if ncols is None else ncols
+        if out is None:
+            out = torch.empty((ncols, g), dtype=torch.complex128, device="cuda")
+        self._check_dev(out, ncols * g, "out")
+        _lib.check(self.L.mdp_basis_densities(self.handle, sub, col0, ncols, _ptr(out), _stream_ptr(stream)),
+                   "mdp_basis_densities")
+        return out
+
     def adjoint(self, cot, xi=None, kind: str = "Q", grad_xi=True, grad_k=None, stream=None, cot_rec=None):
         """(grad_xi or None, grad_k) of a real loss with cotangent `cot` (layout of project())
         and optionally `cot_rec` on the receiver output."""

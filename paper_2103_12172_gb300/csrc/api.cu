@@ -382,6 +382,25 @@ mdp_status mdp_project_columns(mdp_plan *p, int sub, int col0, int ncols, const 
   return MDP_OK;
 }
 
+mdp_status mdp_potential(mdp_plan *p, int sub, int ncols, const mdp_c64 *xi, mdp_c64 *u, void *cuda_stream) {
+  if (!p || sub < 0 || sub >= p->n_subs || ncols < 1 || !xi || !u) return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_ERR_STATE;
+  if ((const void *)xi == (const void *)u) return MDP_ERR_ARG;
+  CK(cudaSetDevice(p->device));
+  CK(launch_potential(p, sub, ncols, (const double2 *)xi, (double2 *)u, (cudaStream_t)cuda_stream));
+  return MDP_OK;
+}
+
+mdp_status mdp_basis_densities(mdp_plan *p, int sub, int col0, int ncols, mdp_c64 *out, void *cuda_stream) {
+  if (!p || sub < 0 || sub >= p->n_subs || !out) return MDP_ERR_ARG;
+  const SubDesc &d = p->subs[sub].d;
+  if (col0 < 0 || ncols < 1 || col0 + ncols > d.n_cols) return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_ERR_STATE;
+  CK(cudaSetDevice(p->device));
+  CK(launch_basis_densities(p, sub, col0, ncols, (double2 *)out, (cudaStream_t)cuda_stream));
+  return MDP_OK;
+}
+
 mdp_status mdp_ap_adjoint(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot, mdp_c64 *grad_xi, double *grad_k,
                           int out_kind, void *cuda_stream) {
   return mdp_ap_adjoint_rec(p, xi, cot, nullptr, grad_xi, grad_k, out_kind, cuda_stream);

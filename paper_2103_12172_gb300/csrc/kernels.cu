@@ -14,6 +14,9 @@
 // sine-table loads are warp-uniform broadcasts and column data is read coalesced.
 #include "kernels_common.cuh"
 
+#include <algorithm>
+#include <cstring>
+
 namespace mdp {
 
 // ---------------------------------------------------------------- k_extend
@@ -988,6 +991,61 @@ cudaError_t launch_solve(const mdp_plan *p, int sub, int nrhs, const double2 *g,
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------- potential on the grid
+// The extended basis densities xi_c on gamma (k_extend's values, zero where the node belongs
+// to another side than the column's), out[c][g] complex, for the item's columns.
+__global__ void __launch_bounds__(256) k_basis_out(Item it, const SubDesc *subs, const double *tab, const double *ws,
+                                                   double2 *out) {
+  const SubDesc &d = subs[it.sub];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)it.ncols * d.G) return;
+  const int b = (int)(t / d.G), g = (int)(t % d.G);
+  const cplx v = density<false>(d, it, ws, tab, nullptr, b, g);
+  out[(long long)b * d.G + g] = make_double2(v.re, v.im);
+}
+
+// Right-hand side of the potential: r = L^(h) w on the ring inside M+ (w = xi on gamma, 0
+// elsewhere: the only nodes of M+ where L w is nonzero), written into the zeroed grid
+// u[c][n][m] that the full-grid solve then reads.
+__global__ void __launch_bounds__(256) k_pot_rhs(int sub, const SubDesc *subs, int ncols, const double2 *xi, double2 *u) {
+  const SubDesc &d = subs[sub];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ncols * d.R) return;
+  const int c = (int)(t / d.R), ri = (int)(t % d.R);
+  int n, m;
+  ring_node(d, ri, n, m);
+  const double2 *x = xi + (long long)c * d.G;
+  cplx acc = cmk(0.0, 0.0);
+#pragma unroll
+  for (int dn = -1; dn <= 1; ++dn) {
+#pragma unroll
+    for (int dm = -1; dm <= 1; ++dm) {
+      const int g = gamma_index(d, n + dn, m + dm);
+      if (g < 0) continue;
+      const int nb = (dn != 0) + (dm != 0);
+      const double cf = nb == 0 ? d.c0 : nb == 1 ? d.c1 : d.c2;
+      acc = caxpy(cf, cmk(x[g].x, x[g].y), acc);
+    }
+  }
+  u[((long long)c * d.ny + n) * d.nx + m] = make_double2(acc.re, acc.im);
+}
+
+// u <- w - u on every node (w = xi on gamma, 0 elsewhere): the difference potential.
+__global__ void __launch_bounds__(256) k_pot_fix(int sub, const SubDesc *subs, int ncols, const double2 *xi, double2 *u) {
+  const SubDesc &d = subs[sub];
+  const long long npt = (long long)d.nx * d.ny;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)ncols * npt) return;
+  const int c = (int)(t / npt);
+  const long long k = t % npt;
+  const int n = (int)(k / d.nx), m = (int)(k % d.nx);
+  double2 v = u[t];
+  v.x = -v.x; v.y = -v.y;
+  const int g = gamma_index(d, n, m);
+  if (g >= 0) { const double2 w = xi[(long long)c * d.G + g]; v.x += w.x; v.y += w.y; }
+  u[t] = v;
+}
+
 // Full-grid solve on caller-provided device tables and scratch (one subdomain at d_sub[0]).
 cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const double *tab, const uint8_t *piv,
                              double *buf, long long buf_doubles, int nrhs, const double2 *g, double2 *u, int adjoint,
@@ -1001,6 +1059,47 @@ cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const doub
     k_full_fwd<<<dim3((hd.Nq + 63) / 64, hd.Nt, nr), 64, 0, st>>>(d_sub, 0, tab, g, buf, r0, nr, adjoint);
     k_full_tri<<<dim3((hd.Nq + 63) / 64, nr), 64, 0, st>>>(d_sub, 0, tab, piv, buf, nr, adjoint);
     k_full_inv<<<dim3((hd.nx + 63) / 64, hd.ny, nr), 64, 0, st>>>(d_sub, 0, tab, buf, u, r0, nr, adjoint);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// P_N+ xi on the whole grid of subdomain `sub` for ncols densities (Eq. Potential_def):
+// w - G^(h) (L^(h) w)|M+. u doubles as the right-hand side of the full-grid solve.
+cudaError_t launch_potential(const mdp_plan *p, int sub, int ncols, const double2 *xi, double2 *u, cudaStream_t st) {
+  const SubDesc &d = p->subs[sub].d;
+  const long long npt = (long long)d.nx * d.ny;
+  cudaError_t e = cudaMemsetAsync(u, 0, (size_t)ncols * npt * sizeof(double2), st);
+  if (e != cudaSuccess) return e;
+  const long long nr = (long long)ncols * d.R;
+  k_pot_rhs<<<(unsigned)((nr + 255) / 256), 256, 0, st>>>(sub, p->d_subs, ncols, xi, u);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_solve(p, sub, ncols, u, u, 0, st);
+  if (e != cudaSuccess) return e;
+  const long long nt = (long long)ncols * npt;
+  k_pot_fix<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(sub, p->d_subs, ncols, xi, u);
+  return cudaGetLastError();
+}
+
+// The extended basis densities of columns col0 .. col0+ncols-1 of subdomain `sub`, out[c][g].
+cudaError_t launch_basis_densities(const mdp_plan *p, int sub, int col0, int ncols, double2 *out, cudaStream_t st) {
+  const SubDesc &d = p->subs[sub].d;
+  for (int c = 0; c < ncols; c += p->tile_cols) {
+    Item it;
+    std::memset(&it, 0, sizeof it);
+    it.sub = sub; it.col0 = col0 + c; it.ncols = std::min(p->tile_cols, ncols - c);
+    long long xo, ro, go, yo, ao, so, reo, tot;
+    item_workspace(d, it.ncols, false, xo, ro, go, yo, ao, so, reo, tot);
+    it.xi_off = xo; it.r_off = ro; it.gr_off = go; it.y_off = yo; it.a_off = ao; it.s_off = so; it.red_off = reo;
+    Batch b;
+    std::memset(&b, 0, sizeof b);
+    b.n_items = 1; b.one = it; b.total_blocks = blocks_for(F_EXT, d, it.ncols);
+    k_extend<<<dim3((unsigned)b.total_blocks), 128, 0, st>>>(b, p->d_subs, p->d_tables, p->d_ws, 0);
+    const long long n = (long long)it.ncols * d.G;
+    k_basis_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(it, p->d_subs, p->d_tables, p->d_ws,
+                                                              out + (long long)c * d.G);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

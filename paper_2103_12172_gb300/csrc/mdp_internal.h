@@ -245,6 +245,8 @@ cudaError_t launch_adjoint(mdp_plan *p, const Batch *fam_batches, int out_kind, 
 cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, const double2 *xi_user, const double2 *cot,
                                 const double2 *cot_rec, double2 *grad_xi, double *grad_k, cudaStream_t st);
 
+cudaError_t launch_potential(const mdp_plan *p, int sub, int ncols, const double2 *xi, double2 *u, cudaStream_t st);
+cudaError_t launch_basis_densities(const mdp_plan *p, int sub, int col0, int ncols, double2 *out, cudaStream_t st);
 cudaError_t launch_solve(const mdp_plan *p, int sub, int nrhs, const double2 *g, double2 *u, int adjoint,
                          cudaStream_t st);
 cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const double *tab, const uint8_t *piv,

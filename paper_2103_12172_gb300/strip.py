@@ -94,6 +94,31 @@ class LayeredStrip:
 
     def receivers(self, k):
         """Solution at the receivers of every layer (list of complex tensors), differentiable in k."""
+        cvecs, rec = self.coefficients(k)
+        res = []
+        for j in range(self.N):
+            row, m0, cnt, roff = self.rlayout[j]
+            nc = self.layout[j][1]
+            K = rec[roff:roff + nc * cnt].view(nc, cnt).transpose(0, 1)    # [cnt, 8M]
+            res.append(K @ cvecs[j])
+        return res
+
+    def field(self, k):
+        """The solution on the whole grid of every layer, [ny, nx] complex tensors (the difference
+        potential of the layer's boundary density, Eq. potential_solution_homo; meaningful on
+        N+). Not differentiable."""
+        with torch.no_grad():
+            cvecs, _ = self.coefficients(k)
+            out = []
+            for j in range(self.N):
+                dens = self.plan.basis_densities(j)                      # [8M, |gamma|]
+                xi = (cvecs[j].to(dens.dtype) @ dens)[None, :].contiguous()
+                out.append(self.plan.potential(j, xi)[0])
+            return out
+
+    def coefficients(self, k):
+        """The Chebyshev coefficients [c^(0) sides 1..4, c^(1) sides 1..4] of every layer's boundary
+        data from the coupled least-squares solve, and the receiver output of the projection."""
         M, N = self.M, self.N
         out, rec = ProjectWithReceivers.apply(k, self.plan)
         s = cheb_points(M, out.device)
@@ -148,7 +173,7 @@ class LayeredStrip:
         D = 1.0 / torch.linalg.vector_norm(A, dim=0)
         Qf, R = torch.linalg.qr(A * D)
         xsol = D * torch.linalg.solve_triangular(R, (Qf.conj().transpose(0, 1) @ b)[:, None], upper=True)[:, 0]
-        res = []
+        cvecs = []
         for j in range(N):
             parts0, parts1 = [], []
             for side, spec in zip((1, 2, 3, 4), coef[j]):
@@ -165,12 +190,8 @@ class LayeredStrip:
                     _, c, sgn = spec
                     parts0.append(xsol[c:c + M])
                     parts1.append(sgn * xsol[c + M:c + 2 * M])
-            cvec = torch.cat(parts0 + parts1)
-            row, m0, cnt, roff = self.rlayout[j]
-            nc = self.layout[j][1]
-            K = rec[roff:roff + nc * cnt].view(nc, cnt).transpose(0, 1)    # [cnt, 8M]
-            res.append(K @ cvec)
-        return res
+            cvecs.append(torch.cat(parts0 + parts1))
+        return cvecs, rec
 
 
 def incident_impedance_bc(theta):

@@ -179,3 +179,28 @@ def test_dd8x8_workload_sampled(dev):
         ref = APSystem(s).columns(cols=cols)
         assert rel_col_err(blocks[i].cpu().numpy()[cols], ref) < TOL, (i, s.nx)
     assert seen == {257, 513, 1025}
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("n", [65, 61])
+def test_potential_on_the_grid_matches_oracle(dev, ap, n):
+    """mdp_potential (the difference potential w - G (L w)|M+ on every node) against the oracle."""
+    sub = W.small_subdomain(n, 10.0, ap, 2)
+    plan = make_plan(dev, [sub], 8)
+    S = APSystem(sub)
+    G = plan.layout(0)[0]
+    xi = W.random_complex((3, G), seed=41)
+    u = plan.potential(0, torch.from_numpy(xi).cuda()).cpu().numpy()
+    ref = np.stack([S.potential(x) for x in xi])
+    assert rel_col_err(u.reshape(3, -1), ref.reshape(3, -1)) < TOL
+
+
+def test_basis_densities_match_oracle(dev):
+    sub = W.small_subdomain(65, 12.0, W.AP_DIRX_SOMMY, 5)
+    plan = make_plan(dev, [sub], 16)
+    S = APSystem(sub)
+    got = plan.basis_densities(0).cpu().numpy()
+    ref = np.stack([S.basis_density(c) for c in range(8 * sub.n_modes)])
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    part = plan.basis_densities(0, col0=7, ncols=20).cpu().numpy()
+    assert np.array_equal(part, got[7:27])

@@ -161,3 +161,39 @@ def test_layered_transmission_converges_fourth_order_on_gpu(mdp):
         errs.append(err)
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert errs[-1] < 1e-6 and np.all(rates > 3.4), (errs, rates)
+
+
+def test_layered_transmission_field_converges_fourth_order_on_gpu(mdp):
+    """The whole solution (not only receivers): every layer's difference potential of its DD
+    density on the full grid (mdp_basis_densities + mdp_potential), max error over all M+ nodes
+    against the exact two-layer transmission, fourth order in h."""
+    from exact_solutions import layered_exact
+    from paper_2103_12172_gb300.strip import LayeredStrip
+    ks = [5.0, 9.0]
+    u, du = layered_exact(ks, [1.0])
+    errs = []
+    for n in (33, 65, 129):
+        subs = [W.unit_subdomain(j, 0, n, k, W.AP_DIRX_SOMMY, 16) for j, k in enumerate(ks)]
+
+        def bc(j, side, kj, x, y, subs=subs):
+            if side in (1, 2):
+                return 0.0, 1.0, torch.zeros_like(x, dtype=torch.complex128)
+            xs = subs[j].x0 if side == 3 else subs[j].x1
+            sign = -1.0 if side == 3 else 1.0
+            ik = 1j * ks[j]
+            val = sign * du(j, xs) + ik * u(j, xs)
+            return ik, 1.0, torch.full(x.shape, complex(val), dtype=torch.complex128, device=x.device)
+
+        rows = [n // 2] * 2
+        strip = LayeredStrip(subs, bc, rows)
+        fields = [f.cpu().numpy() for f in strip.field(torch.tensor(ks, dtype=torch.float64))]
+        err = 0.0
+        for j, s_ in enumerate(subs):
+            xx = s_.ax0 + np.arange(s_.nx) * s_.h
+            yy = s_.ay0 + np.arange(s_.ny) * s_.h
+            inside = ((xx[None, :] > s_.x0) & (xx[None, :] < s_.x1) & (yy[:, None] > s_.y0) & (yy[:, None] < s_.y1))
+            ex = np.broadcast_to(u(j, xx)[None, :], inside.shape)
+            err = max(err, np.abs(fields[j][inside] - ex[inside]).max() / np.abs(ex[inside]).max())
+        errs.append(err)
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[-1] < 1e-5 and np.all(rates > 3.4), (errs, rates)
