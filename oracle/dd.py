@@ -40,11 +40,15 @@ def cheb_coeffs(f, n_modes):
 
 class Strip:
     """DD solve of a strip of subdomains. bc(j, side) -> (alpha, beta, phi(s)) gives the outer
-    boundary condition of side `side` of subdomain j as a function of the side parameter s."""
+    boundary condition of side `side` of subdomain j as a function of the side parameter s.
+    source(j) -> fun or None: the source of subdomain j, fun(x, y) -> (f, f_x, f_y, f_xx, f_yy)
+    (Delta u + k^2 u = f); it adds F_j to the right-hand side of Q_j c_j = F_j and G B f to the
+    solution (oracle/source.py)."""
 
-    def __init__(self, subdomains, bc):
+    def __init__(self, subdomains, bc, source=None):
         self.subs = list(subdomains)
         self.bc = bc
+        self.source = source
         self.M = self.subs[0].n_modes
         self.N = len(self.subs)
 
@@ -65,8 +69,9 @@ class Strip:
                 off += 2 * self.M
         return idx, off
 
-    def assemble(self, Qs):
-        """Global least-squares system A x = b from the per-subdomain Q_j [|gamma_j|, 8M]."""
+    def assemble(self, Qs, Fs=None):
+        """Global least-squares system A x = b from the per-subdomain Q_j [|gamma_j|, 8M] and the
+        right-hand sides F_j of Q_j c_j = F_j (zero without a source)."""
         M = self.M
         idx, n = self.unknown_map()
         rows = sum(Q.shape[0] for Q in Qs)
@@ -75,6 +80,8 @@ class Strip:
         r0 = 0
         for j, Q in enumerate(Qs):
             g = Q.shape[0]
+            if Fs is not None and Fs[j] is not None:
+                b[r0:r0 + g] += Fs[j]
             blk = lambda side, kind: Q[:, kind * 4 * M + (side - 1) * M: kind * 4 * M + side * M]
             for side in (1, 2, 3, 4):
                 Q0, Q1 = blk(side, 0), blk(side, 1)
@@ -125,10 +132,27 @@ class Strip:
 
     def solve(self, rec_rows):
         """Coefficients and the solution at the receivers (row rec_rows[j], m = mlo+1 .. mhi-1)."""
+        from .source import source_foot_data, source_on_grid, source_terms
         systems = [APSystem(s) for s in self.subs]
         Qs = [S.columns().T for S in systems]   # [|gamma|, 8M]
-        A, b = self.assemble(Qs)
+        Fs, Us = [], []
+        for j, (S, sub) in enumerate(zip(systems, self.subs)):
+            fun = self.source(j) if self.source is not None else None
+            if fun is None:
+                Fs.append(None)
+                Us.append(None)
+                continue
+            F, ub = source_terms(S, source_on_grid(sub, fun), source_foot_data(S.gs, sub, fun))
+            Fs.append(F)
+            Us.append(ub)
+        A, b = self.assemble(Qs, Fs)
         x = np.linalg.lstsq(A, b, rcond=None)[0]
         cs = self.coefficients(x)
-        urec = [S.receivers(r).T @ c for S, r, c in zip(systems, rec_rows, cs)]
+        urec = []
+        for S, r, c, ub in zip(systems, rec_rows, cs, Us):
+            u = S.receivers(r).T @ c
+            if ub is not None:
+                mlo, mhi, _, _ = S.mplus_range()
+                u = u + ub[r, mlo + 1:mhi]
+            urec.append(u)
         return cs, urec, (A, b, x)
