@@ -176,6 +176,21 @@ mdp_status mdp_ap_solve_batch(mdp_plan *p, int sub, int nrhs, const mdp_c64 *g, 
  * plan must not overlap in time. */
 mdp_status mdp_potential(mdp_plan *p, int sub, int ncols, const mdp_c64 *xi, mdp_c64 *u, void *cuda_stream);
 
+/* The terms a source f adds to subdomain `sub` (Delta u + k^2 u = f; Sections 3.2.1, 3.2.3,
+ * 3.2.5): the right-hand side of its system Q c = F (Eq. linear_system_equations),
+ *   F = (I - P_gamma) Ex^(I) f - Tr G^(h) (B^(h) f)|M+,
+ * and the source's part of the solution (Eq. potential_solution with xi = Ex^(H) + Ex^(I) f),
+ *   u = P_N+ Ex^(I) f + G^(h) (B^(h) f)|M+ on every node of the grid.
+ * f: device [ny][nx], the source at every node of the auxiliary grid (B^(h) f, Eq. rhs_g, is
+ * applied on M+, where it uses f on N+). src4: device [|gamma|][4], at the foot point of every
+ * gamma node on its owner side (mdp_plan_gamma_geometry): f, its derivative along the outward
+ * normal, its second normal and second tangential derivatives (Ex^(I) f, Eqs. extension_split,
+ * cartesian_extension). F: device [|gamma|]; u: device [ny][nx] (must not overlap f). Uses the
+ * plan's workspace (MDP_ERR_NOMEM if it is too small for one column and two grid-sized
+ * scratch arrays). */
+mdp_status mdp_source_terms(mdp_plan *p, int sub, const mdp_c64 *f, const mdp_c64 *src4, mdp_c64 *F, mdp_c64 *u,
+                            void *cuda_stream);
+
 /* The extended basis densities xi_c = Ex Psi_c on gamma (Sections 3.2.3-3.2.4: the Taylor
  * extension of the Chebyshev basis function of column c, zero on the nodes owned by other
  * sides) for columns col0 .. col0+ncols-1 of subdomain `sub`: out device [ncols][|gamma|]

@@ -179,6 +179,50 @@ class Plan:
                    "mdp_potential")
         return out
 
+    def source_terms(self, sub: int, f, src4, stream=None):
+        """(F [|gamma|], u [ny, nx]) of a source: the right-hand side of the subdomain's system
+        Q c = F and the source's part of its solution (device complex128 tensors). f: [ny, nx]
+        on the auxiliary grid; src4: [|gamma|, 4] foot data (see source_foot_data)."""
+        import torch
+        g = self.layout(sub)[0]
+        s = self.subdomains[sub]
+        f = f.reshape(s.ny, s.nx).contiguous()
+        src4 = src4.reshape(g, 4).contiguous()
+        self._check_dev(f, s.ny * s.nx, "f")
+        self._check_dev(src4, 4 * g, "src4")
+        F = torch.empty(g, dtype=torch.complex128, device="cuda")
+        u = torch.empty((s.ny, s.nx), dtype=torch.complex128, device="cuda")
+        _lib.check(self.L.mdp_source_terms(self.handle, sub, _ptr(f), _ptr(src4), _ptr(F), _ptr(u),
+                                           _stream_ptr(stream)), "mdp_source_terms")
+        return F, u
+
+    def source_foot_data(self, sub: int, fun):
+        """Host evaluation of a source at what mdp_source_terms needs: (f on the grid [ny, nx],
+        foot data [|gamma|, 4] = f, d_n f, d_nn f, d_tt f at each gamma node's foot point on its
+        owner side) as numpy complex arrays. fun(x, y) -> (f, f_x, f_y, f_xx, f_yy)."""
+        s = self.subdomains[sub]
+        x = s.ax0 + np.arange(s.nx) * s.h
+        y = s.ay0 + np.arange(s.ny) * s.h
+        X, Y = np.meshgrid(x, y)
+        fgrid = np.asarray(fun(X, Y)[0], dtype=complex) * np.ones_like(X)
+        owner, _, sp = self.gamma_geometry(sub)
+        src4 = np.zeros((owner.size, 4), dtype=complex)
+        for side in (1, 2, 3, 4):
+            sel = owner == side
+            if not sel.any():
+                continue
+            t = (sp[sel] + 1.0) / 2.0
+            if side in (1, 2):
+                fx, fy = s.x0 + t * (s.x1 - s.x0), np.full(t.shape, s.y0 if side == 1 else s.y1)
+            else:
+                fx, fy = np.full(t.shape, s.x0 if side == 3 else s.x1), s.y0 + t * (s.y1 - s.y0)
+            f, gx, gy, gxx, gyy = (np.asarray(v, dtype=complex) * np.ones_like(fx) for v in fun(fx, fy))
+            if side in (1, 2):
+                src4[sel] = np.stack([f, (-1.0 if side == 1 else 1.0) * gy, gyy, gxx], axis=1)
+            else:
+                src4[sel] = np.stack([f, (-1.0 if side == 3 else 1.0) * gx, gxx, gyy], axis=1)
+        return fgrid, src4
+
     def basis_densities(self, sub: int, col0: int = 0, ncols=None, out=None, stream=None):
         """Extended basis densities Ex Psi_c on gamma: tensor [ncols, |gamma|] (complex128)."""
         import torch

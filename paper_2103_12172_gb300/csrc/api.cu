@@ -391,6 +391,19 @@ mdp_status mdp_potential(mdp_plan *p, int sub, int ncols, const mdp_c64 *xi, mdp
   return MDP_OK;
 }
 
+mdp_status mdp_source_terms(mdp_plan *p, int sub, const mdp_c64 *f, const mdp_c64 *src4, mdp_c64 *F, mdp_c64 *u,
+                            void *cuda_stream) {
+  if (!p || sub < 0 || sub >= p->n_subs || !f || !src4 || !F || !u) return MDP_ERR_ARG;
+  if ((const void *)f == (const void *)u) return MDP_ERR_ARG;
+  if (!device_ok(p)) return MDP_ERR_STATE;
+  CK(cudaSetDevice(p->device));
+  const cudaError_t e = launch_source_terms(p, sub, (const double2 *)f, (const double2 *)src4, (double2 *)F,
+                                            (double2 *)u, (cudaStream_t)cuda_stream);
+  if (e == cudaErrorMemoryAllocation) return MDP_ERR_NOMEM;
+  CK(e);
+  return MDP_OK;
+}
+
 mdp_status mdp_basis_densities(mdp_plan *p, int sub, int col0, int ncols, mdp_c64 *out, void *cuda_stream) {
   if (!p || sub < 0 || sub >= p->n_subs || !out) return MDP_ERR_ARG;
   const SubDesc &d = p->subs[sub].d;

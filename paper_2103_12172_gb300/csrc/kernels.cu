@@ -1046,6 +1046,54 @@ __global__ void __launch_bounds__(256) k_pot_fix(int sub, const SubDesc *subs, i
   u[t] = v;
 }
 
+// ---------------------------------------------------------------- source terms
+// Ex^(I) f on gamma (the source terms of the equation-based extension): from the foot data
+// src4[g] = (f, d_n f, d_nn f, d_tt f) and the node's distance rho to its owner side,
+// rho^2/2 f + rho^3/6 d_n f + rho^4/24 (d_nn f - d_tt f - k^2 f).
+__global__ void __launch_bounds__(256) k_ext_source(int sub, const SubDesc *subs, const double *tab,
+                                                    const double2 *src4, double2 *xi) {
+  const SubDesc &d = subs[sub];
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= d.G) return;
+  const double rho = tab[d.geo_off + 4 * g + 2];
+  const double r2 = 0.5 * rho * rho, r3 = r2 * rho / 3.0, r4 = r2 * r2 / 6.0;
+  const double2 f = src4[4 * g], fn = src4[4 * g + 1], fnn = src4[4 * g + 2], ftt = src4[4 * g + 3];
+  const double k2 = d.k * d.k;
+  const double t4r = fnn.x - ftt.x - k2 * f.x, t4i = fnn.y - ftt.y - k2 * f.y;
+  xi[g] = make_double2(fma(r4, t4r, fma(r3, fn.x, r2 * f.x)), fma(r4, t4i, fma(r3, fn.y, r2 * f.y)));
+}
+
+// g = (B^(h) f)|M+: f + (f_{m+1} + f_{m-1} + f_{n+1} + f_{n-1} - 4 f) / 12 on the nodes of M+
+// (the rectangle mlo..mhi x nlo..nhi), 0 elsewhere.
+__global__ void __launch_bounds__(256) k_apply_B(int sub, const SubDesc *subs, const double2 *f, double2 *g) {
+  const SubDesc &d = subs[sub];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)d.nx * d.ny) return;
+  const int n = (int)(t / d.nx), m = (int)(t % d.nx);
+  double2 v = make_double2(0.0, 0.0);
+  if (m >= d.mlo && m <= d.mhi && n >= d.nlo && n <= d.nhi) {
+    const double2 c = f[t], e = f[t + 1], w = f[t - 1], nn = f[t + d.nx], s = f[t - d.nx];
+    v.x = c.x + (e.x + w.x + nn.x + s.x - 4.0 * c.x) / 12.0;
+    v.y = c.y + (e.y + w.y + nn.y + s.y - 4.0 * c.y) / 12.0;
+  }
+  g[t] = v;
+}
+
+// F <- -F - Tr(ub) on gamma, u <- u + ub on the grid.
+__global__ void __launch_bounds__(256) k_src_fin(int sub, const SubDesc *subs, const double2 *ub, double2 *F,
+                                                 double2 *u) {
+  const SubDesc &d = subs[sub];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)d.nx * d.ny) return;
+  const int n = (int)(t / d.nx), m = (int)(t % d.nx);
+  const double2 b = ub[t];
+  double2 v = u[t];
+  v.x += b.x; v.y += b.y;
+  u[t] = v;
+  const int g = gamma_index(d, n, m);
+  if (g >= 0) { const double2 q = F[g]; F[g] = make_double2(-q.x - b.x, -q.y - b.y); }
+}
+
 // Full-grid solve on caller-provided device tables and scratch (one subdomain at d_sub[0]).
 cudaError_t launch_solve_raw(const SubDesc *d_sub, const SubDesc &hd, const double *tab, const uint8_t *piv,
                              double *buf, long long buf_doubles, int nrhs, const double2 *g, double2 *u, int adjoint,
@@ -1080,6 +1128,45 @@ cudaError_t launch_potential(const mdp_plan *p, int sub, int ncols, const double
   if (e != cudaSuccess) return e;
   const long long nt = (long long)ncols * npt;
   k_pot_fix<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(sub, p->d_subs, ncols, xi, u);
+  return cudaGetLastError();
+}
+
+// The source's terms for subdomain `sub` (f on the grid, foot data src4 on gamma):
+// F = -(P_gamma - I) Ex^(I) f - Tr G (B f)|M+ and u = P_N+ Ex^(I) f + G (B f)|M+ on the grid.
+// Scratch at the top of the workspace: xi_I [G] and the grid of G (B f)|M+; the solves and the
+// one-column projection use the workspace from its start.
+cudaError_t launch_source_terms(mdp_plan *p, int sub, const double2 *f, const double2 *src4, double2 *F, double2 *u,
+                                cudaStream_t st) {
+  const SubDesc &d = p->subs[sub].d;
+  const long long npt = (long long)d.nx * d.ny;
+  const long long scratch = 2LL * d.G + 2 * npt + 64;
+  long long xo, ro, go, yo, ao, so, reo, tot;
+  item_workspace(d, 1, false, xo, ro, go, yo, ao, so, reo, tot);
+  const long long need = std::max((long long)d.Nq * d.Nt * 2, tot) + scratch;
+  if (p->ws_doubles < need) return cudaErrorMemoryAllocation;
+  const long long top = (p->ws_doubles - scratch) & ~31LL;
+  double2 *xi_i = reinterpret_cast<double2 *>(p->d_ws + top);
+  double2 *ub = reinterpret_cast<double2 *>(p->d_ws + top + ((2LL * d.G + 31) & ~31LL));
+  k_ext_source<<<(d.G + 255) / 256, 256, 0, st>>>(sub, p->d_subs, p->d_tables, src4, xi_i);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_potential(p, sub, 1, xi_i, u, st);                 // u = P_N+ Ex^(I) f
+  if (e != cudaSuccess) return e;
+  k_apply_B<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(sub, p->d_subs, f, ub);
+  e = launch_solve(p, sub, 1, ub, ub, 0, st);                   // ub = G (B f)|M+
+  if (e != cudaSuccess) return e;
+  Item it;                                                       // F = (P_gamma - I) xi_I
+  std::memset(&it, 0, sizeof it);
+  it.sub = sub; it.col0 = 0; it.ncols = 1;
+  it.xi_off = xo; it.r_off = ro; it.gr_off = go; it.y_off = yo; it.a_off = ao; it.s_off = so; it.red_off = reo;
+  Batch fb[NFAM];
+  for (int f_ = 0; f_ < NFAM; ++f_) {
+    std::memset(&fb[f_], 0, sizeof fb[f_]);
+    fb[f_].n_items = 1; fb[f_].one = it; fb[f_].total_blocks = blocks_for((Fam)f_, d, 1);
+  }
+  e = launch_project(p, fb, MDP_OUT_Q, xi_i, F, nullptr, st);
+  if (e != cudaSuccess) return e;
+  k_src_fin<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(sub, p->d_subs, ub, F, u);
   return cudaGetLastError();
 }
 

@@ -246,6 +246,8 @@ cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, cons
                                 const double2 *cot_rec, double2 *grad_xi, double *grad_k, cudaStream_t st);
 
 cudaError_t launch_potential(const mdp_plan *p, int sub, int ncols, const double2 *xi, double2 *u, cudaStream_t st);
+cudaError_t launch_source_terms(mdp_plan *p, int sub, const double2 *f, const double2 *src4, double2 *F, double2 *u,
+                                cudaStream_t st);
 cudaError_t launch_basis_densities(const mdp_plan *p, int sub, int col0, int ncols, double2 *out, cudaStream_t st);
 cudaError_t launch_solve(const mdp_plan *p, int sub, int nrhs, const double2 *g, double2 *u, int adjoint,
                          cudaStream_t st);

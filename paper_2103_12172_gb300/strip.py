@@ -73,11 +73,13 @@ class LayeredStrip:
     bc(j, side, k_j, x, y) -> (alpha, beta, phi values) (torch, differentiable in k_j) and a
     receiver row per layer."""
 
-    def __init__(self, subdomains, bc, receiver_rows, tile_cols=0):
+    def __init__(self, subdomains, bc, receiver_rows, tile_cols=0, source=None):
         self.subs = list(subdomains)
         self.N = len(self.subs)
         self.M = self.subs[0].n_modes
         self.bc = bc
+        self.source = source        # source(j) -> fun(x, y) -> (f, f_x, f_y, f_xx, f_yy), or None
+        self._src_cache = {}
         self.plan = Plan(self.subs, tile_cols=tile_cols)
         self.plan.set_receivers(receiver_rows)
         self.layout = [self.plan.layout(j) for j in range(self.N)]
@@ -92,16 +94,40 @@ class LayeredStrip:
             return sb.x0 + (s + 1) / 2 * (sb.x1 - sb.x0), torch.full_like(s, sb.y0 if side == 1 else sb.y1)
         return torch.full_like(s, sb.x0 if side == 3 else sb.x1), sb.y0 + (s + 1) / 2 * (sb.y1 - sb.y0)
 
+    def source_terms(self, j, kj):
+        """(F_j, u_j) of layer j's source at wavenumber kj (None without a source), cached per k."""
+        if self.source is None or self.source(j) is None:
+            return None
+        key = (j, float(kj))
+        if key not in self._src_cache:
+            fgrid, src4 = self.plan.source_foot_data(j, self.source(j))
+            self._src_cache = {kk: v for kk, v in self._src_cache.items() if kk[0] != j}
+            self._src_cache[key] = self.plan.source_terms(j, torch.from_numpy(fgrid).cuda(),
+                                                          torch.from_numpy(src4).cuda())
+        return self._src_cache[key]
+
     def receivers(self, k):
-        """Solution at the receivers of every layer (list of complex tensors), differentiable in k."""
+        """Solution at the receivers of every layer (list of complex tensors), differentiable in k
+        (without a source; the source terms are not differentiated)."""
+        if self.source is not None and k.requires_grad:
+            raise NotImplementedError("the k-gradient of the source terms is not implemented")
         cvecs, rec = self.coefficients(k)
         res = []
         for j in range(self.N):
             row, m0, cnt, roff = self.rlayout[j]
             nc = self.layout[j][1]
             K = rec[roff:roff + nc * cnt].view(nc, cnt).transpose(0, 1)    # [cnt, 8M]
-            res.append(K @ cvecs[j])
+            val = K @ cvecs[j]
+            st = self.source_terms(j, self.plan_k(j))
+            if st is not None:
+                val = val + st[1][row, m0:m0 + cnt]
+            res.append(val)
         return res
+
+    def plan_k(self, j):
+        """The wavenumber the plan is factored for in layer j."""
+        ks = getattr(self.plan, "_k_current", None)
+        return ks[j] if ks is not None else self.subs[j].k
 
     def field(self, k):
         """The solution on the whole grid of every layer, [ny, nx] complex tensors (the difference
@@ -113,7 +139,9 @@ class LayeredStrip:
             for j in range(self.N):
                 dens = self.plan.basis_densities(j)                      # [8M, |gamma|]
                 xi = (cvecs[j].to(dens.dtype) @ dens)[None, :].contiguous()
-                out.append(self.plan.potential(j, xi)[0])
+                u = self.plan.potential(j, xi)[0]
+                st = self.source_terms(j, self.plan_k(j))
+                out.append(u if st is None else u + st[1])
             return out
 
     def coefficients(self, k):
@@ -164,6 +192,9 @@ class LayeredStrip:
                     blk = torch.cat([Q0, sgn * Q1], dim=1)
                     A = A + torch.nn.functional.pad(blk, (c, n - c - 2 * M))
                     cj.append(("if", c, sgn))
+            st = self.source_terms(j, self.plan_k(j))
+            if st is not None:
+                b = b + st[0]
             A_rows.append(A)
             b_rows.append(b)
             coef.append(cj)

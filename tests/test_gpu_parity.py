@@ -204,3 +204,25 @@ def test_basis_densities_match_oracle(dev):
     assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
     part = plan.basis_densities(0, col0=7, ncols=20).cpu().numpy()
     assert np.array_equal(part, got[7:27])
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("n", [65, 61])
+def test_source_terms_match_oracle(dev, ap, n):
+    """mdp_source_terms (F = (I - P_gamma) Ex^(I) f - Tr G (B f)|M+ and the source's part of the
+    solution on the grid) against the oracle, on the same f and foot data."""
+    from oracle.source import source_foot_data, source_on_grid, source_terms
+
+    def fun(x, y):
+        u = np.exp(1j * (3.0 * x + 2.0 * y))
+        return (1.0 + x) * u, u, 2 * u, -3 * u, -4 * u
+    sub = W.small_subdomain(n, 9.0, ap, 2)
+    plan = make_plan(dev, [sub], 8)
+    S = APSystem(sub)
+    fgrid = source_on_grid(sub, fun)
+    src4 = source_foot_data(S.gs, sub, fun)
+    F, u = plan.source_terms(0, torch.from_numpy(fgrid).cuda(), torch.from_numpy(src4).cuda())
+    Fr, ur = source_terms(S, fgrid, src4)
+    F, u = F.cpu().numpy(), u.cpu().numpy()
+    assert np.abs(F - Fr).max() <= TOL * np.abs(Fr).max()
+    assert np.abs(u - ur).max() <= TOL * np.abs(ur).max()

@@ -206,3 +206,18 @@ def test_qcache_key_is_translation_invariant_and_complete():
               W.unit_subdomain(0, 0, 129, 12.0, W.AP_DIRX_SOMMY, 6, margin=0.2)]
     keys = {problem_key(o, "Q") for o in others} | {problem_key(a, "P")}
     assert problem_key(a, "Q") not in keys and len(keys) == len(others) + 1
+
+
+def test_source_foot_data_matches_the_oracle(mdp):
+    """The host evaluation of a source at the gamma foot points (product) equals the oracle's."""
+    from oracle.grid import grid_sets
+    from oracle.source import source_foot_data, source_on_grid
+    sub = W.small_subdomain(33, 7.0, W.AP_DIRX_SOMMY, 2)
+    plan = mdp.Plan([sub], host_only=True)
+
+    def fun(x, y):
+        u = np.exp(1j * (3.0 * x + 2.0 * y)) * (1.0 + x * y)
+        return u, 2 * u, 3 * u, 5 * u, 7 * u
+    fgrid, src4 = plan.source_foot_data(0, fun)
+    assert np.allclose(fgrid, source_on_grid(sub, fun), rtol=0, atol=1e-15)
+    assert np.allclose(src4, source_foot_data(grid_sets(sub), sub, fun), rtol=0, atol=1e-14)
