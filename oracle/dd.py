@@ -45,15 +45,33 @@ class Strip:
     (Delta u + k^2 u = f); it adds F_j to the right-hand side of Q_j c_j = F_j and G B f to the
     solution (oracle/source.py)."""
 
-    def __init__(self, subdomains, bc, source=None):
+    def __init__(self, subdomains, bc, source=None, positions=None):
         self.subs = list(subdomains)
         self.bc = bc
         self.source = source
         self.M = self.subs[0].n_modes
         self.N = len(self.subs)
+        # cell (i, j) of every subdomain in a rectangular layout (Section 3.4: subdomains that
+        # share whole sides); default: a strip along x
+        self.pos = [tuple(p) for p in positions] if positions is not None else [(j, 0) for j in range(self.N)]
+        self.at = {p: j for j, p in enumerate(self.pos)}
+
+    def neighbour(self, j, side):
+        i, jj = self.pos[j]
+        d = {1: (0, -1), 2: (0, 1), 3: (-1, 0), 4: (1, 0)}[side]
+        return self.at.get((i + d[0], jj + d[1]))
 
     def outer(self, j, side):
-        return not ((side == 4 and j < self.N - 1) or (side == 3 and j > 0))
+        return self.neighbour(j, side) is None
+
+    def iface(self, j, side):
+        """(key, sign) of the interface on side `side` of subdomain j: the left/bottom subdomain
+        names it (its side 4 or 2), and the two outward normals are opposite, so c^(1) enters with
+        + on that side and - on the neighbour's (Section 3.3.2)."""
+        if side in (4, 2):
+            return (j, side), 1.0
+        nb = self.neighbour(j, side)
+        return (nb, 4 if side == 3 else 2), -1.0
 
     def unknown_map(self):
         """Column offsets of the unknowns: one block of M per outer side (its c^(0), or c^(1) on a
@@ -64,9 +82,10 @@ class Strip:
                 if self.outer(j, side):
                     idx[(j, side)] = off
                     off += self.M
-            if j < self.N - 1:
-                idx[("if", j)] = off
-                off += 2 * self.M
+            for side in (4, 2):
+                if not self.outer(j, side):
+                    idx[("if", j, side)] = off
+                    off += 2 * self.M
         return idx, off
 
     def assemble(self, Qs, Fs=None):
@@ -96,11 +115,10 @@ class Strip:
                         A[r0:r0 + g, c:c + M] += Q1
                         b[r0:r0 + g] -= Q0 @ (d / alpha)
                 else:
-                    jj = j if side == 4 else j - 1
-                    c = idx[("if", jj)]
-                    sgn = 1.0 if side == 4 else -1.0
+                    key, sgn = self.iface(j, side)
+                    c = idx[("if",) + key]
                     A[r0:r0 + g, c:c + M] += Q0                 # X
-                    A[r0:r0 + g, c + M:c + 2 * M] += sgn * Q1   # +Y on the left subdomain, -Y on the right
+                    A[r0:r0 + g, c + M:c + 2 * M] += sgn * Q1   # +Y on the naming subdomain, -Y on the other
             r0 += g
         return A, b
 
@@ -123,10 +141,10 @@ class Strip:
                     else:
                         c[sl0], c[sl1] = d / alpha, u
                 else:
-                    jj = j if side == 4 else j - 1
-                    o = idx[("if", jj)]
+                    key, sgn = self.iface(j, side)
+                    o = idx[("if",) + key]
                     c[sl0] = x[o:o + M]
-                    c[sl1] = (1.0 if side == 4 else -1.0) * x[o + M:o + 2 * M]
+                    c[sl1] = sgn * x[o + M:o + 2 * M]
             cs.append(c)
         return cs
 

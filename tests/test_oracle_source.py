@@ -101,3 +101,39 @@ def test_strip_with_a_source_converges_fourth_order():
     errs = [run_strip(n, [5.0, 8.0], 12) for n in (33, 65)]
     rate = np.log2(errs[0] / errs[1])
     assert errs[1] < 2e-4 and rate > 3.4, (errs, rate)
+
+
+def run_layout(n_of, ks, M):
+    """2 x 2 layout (subdomain (i, j) -> index 2 j + i) with per-subdomain k and grid size."""
+    pos = [(i, j) for j in range(2) for i in range(2)]
+    subs = [W.unit_subdomain(i, j, n_of[2 * j + i], ks[2 * j + i], W.AP_DIRX_SOMMY, M) for (i, j) in pos]
+
+    def bc(j, side):
+        ik = 1j * ks[j]
+
+        def phi(s, side=side, j=j):
+            x, y = side_points(subs[j], side, s)
+            u = u_exact(x, y)
+            dn = {1: -1j * BE, 2: 1j * BE, 3: -1j * AL, 4: 1j * AL}[side] * u
+            return dn + ik * u
+        return ik, 1.0, phi
+
+    strip = Strip(subs, bc, source=lambda j: plane(ks[j]), positions=pos)
+    rows = [s_.ny // 2 for s_ in subs]
+    _, urec, _ = strip.solve(rows)
+    err = 0.0
+    for s_, r, ur in zip(subs, rows, urec):
+        mlo, mhi, _, _ = APSystem(s_).mplus_range()
+        ex = u_exact(s_.ax0 + np.arange(mlo + 1, mhi) * s_.h, s_.ay0 + r * s_.h)
+        err = max(err, np.abs(ur - ex).max() / np.abs(ex).max())
+    return err
+
+
+def test_two_by_two_checkerboard_with_mixed_grids_converges_fourth_order():
+    """A 2 x 2 layout (interfaces along x and y, a corner shared by four subdomains) with a
+    checkerboard wavenumber and a finer grid on the high-k subdomains (Section 4's checkerboard
+    setting, scaled down), sources making u = exp(i (3x + 2y)) exact: fourth order."""
+    ks = [4.0, 7.0, 7.0, 4.0]
+    errs = [run_layout([n, 2 * n - 1, 2 * n - 1, n], ks, 12) for n in (17, 33)]
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > 3.4 and errs[1] < 1e-4, (errs, rate)
