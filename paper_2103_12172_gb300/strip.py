@@ -69,24 +69,39 @@ def cheb_points(n, device):
 
 
 class LayeredStrip:
-    """The strip of `subdomains` (unit squares side by side along x) with outer boundary data
-    bc(j, side, k_j, x, y) -> (alpha, beta, phi values) (torch, differentiable in k_j) and a
-    receiver row per layer."""
+    """A rectangular layout of square subdomains that share whole sides (default: a strip
+    along x; `positions[j]` = cell (i, j) of subdomain j otherwise, Section 3.4) with outer
+    boundary data bc(j, side, k_j, x, y) -> (alpha, beta, phi values) (torch, differentiable in
+    k_j), a receiver row per subdomain and optionally a source per subdomain."""
 
-    def __init__(self, subdomains, bc, receiver_rows, tile_cols=0, source=None):
+    def __init__(self, subdomains, bc, receiver_rows, tile_cols=0, source=None, positions=None):
         self.subs = list(subdomains)
         self.N = len(self.subs)
         self.M = self.subs[0].n_modes
         self.bc = bc
         self.source = source        # source(j) -> fun(x, y) -> (f, f_x, f_y, f_xx, f_yy), or None
         self._src_cache = {}
+        self.pos = [tuple(p) for p in positions] if positions is not None else [(j, 0) for j in range(self.N)]
+        self.at = {p: j for j, p in enumerate(self.pos)}
         self.plan = Plan(self.subs, tile_cols=tile_cols)
         self.plan.set_receivers(receiver_rows)
         self.layout = [self.plan.layout(j) for j in range(self.N)]
         self.rlayout = [self.plan.receiver_layout(j) for j in range(self.N)]
 
+    def neighbour(self, j, side):
+        i, jj = self.pos[j]
+        di, dj = {1: (0, -1), 2: (0, 1), 3: (-1, 0), 4: (1, 0)}[side]
+        return self.at.get((i + di, jj + dj))
+
     def outer(self, j, side):
-        return not ((side == 4 and j < self.N - 1) or (side == 3 and j > 0))
+        return self.neighbour(j, side) is None
+
+    def iface(self, j, side):
+        """(key, sign) of an interface: named by the left/bottom subdomain's side 4 or 2; c^(1)
+        enters with + there and - on the neighbour (opposite outward normals)."""
+        if side in (4, 2):
+            return (j, side), 1.0
+        return (self.neighbour(j, side), 4 if side == 3 else 2), -1.0
 
     def _side_xy(self, j, side, s):
         sb = self.subs[j]
@@ -157,9 +172,10 @@ class LayeredStrip:
                 if self.outer(j, side):
                     idx[(j, side)] = n
                     n += M
-            if j < N - 1:
-                idx[("if", j)] = n
-                n += 2 * M
+            for side in (4, 2):
+                if not self.outer(j, side):
+                    idx[("if", j, side)] = n
+                    n += 2 * M
         A_rows, b_rows, coef = [], [], []
         for j in range(N):
             G, nc, off, _ = self.layout[j]
@@ -186,9 +202,8 @@ class LayeredStrip:
                         cj.append(("dirichlet", c, d, alpha, beta))
                     A = A + torch.nn.functional.pad(blk, (pad_l, pad_r))
                 else:
-                    jj = j if side == 4 else j - 1
-                    c = idx[("if", jj)]
-                    sgn = 1.0 if side == 4 else -1.0
+                    key, sgn = self.iface(j, side)
+                    c = idx[("if",) + key]
                     blk = torch.cat([Q0, sgn * Q1], dim=1)
                     A = A + torch.nn.functional.pad(blk, (c, n - c - 2 * M))
                     cj.append(("if", c, sgn))

@@ -243,3 +243,55 @@ def test_strip_with_a_source_converges_fourth_order_on_gpu(mdp):
     # at 129^2 the error (6e-9) sits at the floor of the least-squares coupling with M* = 12
     # (rounding in a system of condition ~1e7), so the rate is taken from 33 -> 65
     assert errs[-1] < 1e-8 and rates[0] > 3.4, (errs, rates)
+
+
+def test_two_by_two_checkerboard_with_mixed_grids_on_gpu(mdp):
+    """2 x 2 layout (a corner shared by four subdomains) with a checkerboard wavenumber, finer
+    grids on the high-k subdomains and sources making u = exp(i (3x + 2y)) exact: the GPU
+    pipeline matches the oracle's coupled solution and converges at fourth order."""
+    from oracle.dd import Strip, side_points
+    from paper_2103_12172_gb300.strip import LayeredStrip
+    AL, BE = 3.0, 2.0
+    ks = [4.0, 7.0, 7.0, 4.0]
+    pos = [(i, j) for j in range(2) for i in range(2)]
+
+    def ue(x, y):
+        return np.exp(1j * (AL * x + BE * y))
+
+    def src(j):
+        def fun(x, y):
+            f = (ks[j] ** 2 - AL ** 2 - BE ** 2) * ue(x, y)
+            return f, 1j * AL * f, 1j * BE * f, -AL ** 2 * f, -BE ** 2 * f
+        return fun
+
+    def bc(j, side, kj, x, y):
+        u = torch.exp(1j * (AL * x + BE * y))
+        dn = {1: -1j * BE, 2: 1j * BE, 3: -1j * AL, 4: 1j * AL}[side] * u
+        return 1j * ks[j], 1.0, dn + 1j * ks[j] * u
+
+    errs = []
+    for n in (33, 65, 129):
+        ns = [n, 2 * n - 1, 2 * n - 1, n]
+        subs = [W.unit_subdomain(i, j, ns[2 * j + i], ks[2 * j + i], W.AP_DIRX_SOMMY, 12) for (i, j) in pos]
+        rows = [s_.ny // 2 for s_ in subs]
+        lay = LayeredStrip(subs, bc, rows, source=src, positions=pos)
+        got = [r.cpu().numpy() for r in lay.receivers(torch.tensor(ks, dtype=torch.float64))]
+        err = 0.0
+        for j, s_ in enumerate(subs):
+            _, m0, cnt, _ = lay.rlayout[j]
+            ex = ue(s_.ax0 + (m0 + np.arange(cnt)) * s_.h, s_.ay0 + rows[j] * s_.h)
+            err = max(err, np.abs(got[j] - ex).max() / np.abs(ex).max())
+        errs.append(err)
+        if n == 33:   # against the oracle's coupled solve of the same problem
+            def obc(j, side):
+                def phi(s, side=side, j=j):
+                    x, y = side_points(subs[j], side, s)
+                    u = ue(x, y)
+                    dn = {1: -1j * BE, 2: 1j * BE, 3: -1j * AL, 4: 1j * AL}[side] * u
+                    return dn + 1j * ks[j] * u
+                return 1j * ks[j], 1.0, phi
+            _, ref, _ = Strip(subs, obc, source=src, positions=pos).solve(rows)
+            for g_, r_ in zip(got, ref):
+                assert np.abs(g_ - r_).max() < 1e-8 * np.abs(r_).max()
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert rates[0] > 3.4 and errs[-1] < 1e-7, (errs, rates)
