@@ -223,6 +223,67 @@ def run_reference(args, wl):
     return 0
 
 
+# ------------------------------------------------------------------ DD pipeline legs
+def dd_legs(reps=5):
+    """Timings of the layered strip (4 x 129^2, k = 40, M* = 24, impedance data of a plane wave):
+    one coupled solve to the receivers, one loss + k-gradient step, the field of every layer,
+    and a solve with a source in every layer. Milliseconds per call (CUDA events, after
+    warm-up); the projection columns are recomputed inside every call."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2103_12172_gb300.strip import LayeredStrip, incident_impedance_bc, receiver_row
+    subs = list(W.strip4x1().subdomains)
+    rows = [receiver_row(s) for s in subs]
+    strip = LayeredStrip(subs, incident_impedance_bc(0.3), rows)
+    k0 = [s.k for s in subs]
+    targets = [u.clone() for u in strip.receivers(torch.tensor(W.strip_targets(), dtype=torch.float64))]
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def solve():
+        with torch.no_grad():
+            strip.receivers(torch.tensor(k0, dtype=torch.float64))
+
+    def grad_step():
+        k = torch.tensor(k0, dtype=torch.float64, requires_grad=True)
+        loss = sum(torch.sum(torch.abs(u - t) ** 2) for u, t in zip(strip.receivers(k), targets))
+        loss.backward()
+
+    def field():
+        strip.field(torch.tensor(k0, dtype=torch.float64))
+
+    al, be = 40.0 * math.cos(0.3), 40.0 * math.sin(0.3) * 1.1
+
+    def src(j):
+        def fun(x, y):
+            f = (40.0 ** 2 - al ** 2 - be ** 2) * np.exp(1j * (al * x + be * y))
+            return f, 1j * al * f, 1j * be * f, -al ** 2 * f, -be ** 2 * f
+        return fun
+    sstrip = LayeredStrip(subs, incident_impedance_bc(0.3), rows, source=src)
+
+    def solve_src():
+        sstrip._src_cache = {}   # recompute the source terms every call
+        with torch.no_grad():
+            sstrip.receivers(torch.tensor(k0, dtype=torch.float64))
+
+    out = {"workload": W.strip4x1().name, "solve_ms": timed(solve), "grad_step_ms": timed(grad_step),
+           "field_ms": timed(field), "solve_with_source_ms": timed(solve_src)}
+    strip.plan.close()
+    sstrip.plan.close()
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, wl):
     import torch
@@ -402,6 +463,8 @@ def run_ours(args, wl):
         "e2e": e2e,
         "wall_s_timed": wall,
     }
+    if rank == 0 and not args.no_dd_legs:
+        line["dd_pipeline"] = dd_legs()
 
     # CPU baseline: the oracle as it stands, on the host cores, bounded sample (rank 0 at N=1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -428,6 +491,7 @@ def main():
     ap.add_argument("--workload", default="dd2x2_257", choices=sorted(W.WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dd-legs", action="store_true", help="skip the layered-strip pipeline timings")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1195,7 +1195,7 @@ cudaError_t launch_basis_densities(const mdp_plan *p, int sub, int col0, int nco
 
 // ---------------------------------------------------------------- launchers
 static inline dim3 grid1(int n) { return dim3((unsigned)n, 1, 1); }
-static constexpr int FFT_SMEM = FFT_POINTS * 16;  // bytes: fpb x 2Nx complex values
+static constexpr int FFT_SMEM = FFT_POINTS * 16;  // the most dynamic shared memory an FFT block may take
 
 // Dynamic shared memory above 48 KiB must be opted into per kernel on the current device.
 cudaError_t set_kernel_attributes() {
@@ -1225,15 +1225,15 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
   if (basis) MDP_LAUNCH(F_EXT, k_extend<<<grid1(fb[F_EXT].total_blocks), 128, 0, st>>>(fb[F_EXT], ds, tab, ws, 0));
   if (basis) MDP_LAUNCH(F_RES, k_residual<false, false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
   else MDP_LAUNCH(F_RES, k_residual<true, false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
-  if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_FROWS], ds, tab, ws));
-  else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_FROWS], ds, tab, ws));
+  if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
+  else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
   if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   else MDP_LAUNCH(F_TRI, k_tri<true, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   if (basis) {
-    MDP_LAUNCH(F_IROWS, k_inv_rows<false><<<grid1(fb[F_IROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
+    MDP_LAUNCH(F_IROWS, k_inv_rows<false><<<grid1(fb[F_IROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
     MDP_LAUNCH(F_ICOLS, k_inv_cols<false><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
   } else {
-    MDP_LAUNCH(F_IROWS, k_inv_rows<true><<<grid1(fb[F_IROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
+    MDP_LAUNCH(F_IROWS, k_inv_rows<true><<<grid1(fb[F_IROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
     MDP_LAUNCH(F_ICOLS, k_inv_cols<true><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
   }
   if (out_rec)
@@ -1252,8 +1252,8 @@ cudaError_t launch_adjoint(mdp_plan *p, const Batch *fb, int out_kind, const dou
     if (basis) MDP_LAUNCH(F_EXT, k_extend<<<grid1(fb[F_EXT].total_blocks), 128, 0, st>>>(fb[F_EXT], ds, tab, ws, 1));
     if (basis) MDP_LAUNCH(F_RES, k_residual<false, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
     else MDP_LAUNCH(F_RES, k_residual<true, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
-    if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_FROWS], ds, tab, ws));
-    else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, FFT_SMEM, st>>>(fb[F_FROWS], ds, tab, ws));
+    if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
+    else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
     if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
     else MDP_LAUNCH(F_TRI, k_tri<true, true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   }

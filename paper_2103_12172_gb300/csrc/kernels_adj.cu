@@ -514,14 +514,14 @@ cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, cons
       prof_end(p, fam, st);                       \
     }                                             \
   } while (0)
-  ADJ_LAUNCH(F_AFWD, k_adj_rows<<<g1(fb[F_AFWD].total_blocks), b8, FFT_SMEM_ADJ, st>>>(fb[F_AFWD], ds, tab, ws, cot, cot_rec));
+  ADJ_LAUNCH(F_AFWD, k_adj_rows<<<g1(fb[F_AFWD].total_blocks), b8, p->fft_smem, st>>>(fb[F_AFWD], ds, tab, ws, cot, cot_rec));
   if (dk) ADJ_LAUNCH(F_ATRI, k_adj_tri<true><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot, cot_rec ? 1 : 0));
   else ADJ_LAUNCH(F_ATRI, k_adj_tri<false><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot, cot_rec ? 1 : 0));
   if (dk) {
-    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<true><<<g1(fb[F_ARING].total_blocks), b8, FFT_SMEM_ADJ, st>>>(fb[F_ARING], ds, tab, ws));
+    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<true><<<g1(fb[F_ARING].total_blocks), b8, p->fft_smem, st>>>(fb[F_ARING], ds, tab, ws));
     ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<true><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));
   } else {
-    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<false><<<g1(fb[F_ARING].total_blocks), b8, FFT_SMEM_ADJ, st>>>(fb[F_ARING], ds, tab, ws));
+    ADJ_LAUNCH(F_ARING, k_adj_ring_rows<false><<<g1(fb[F_ARING].total_blocks), b8, p->fft_smem, st>>>(fb[F_ARING], ds, tab, ws));
     ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<false><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));
   }
   if (dk && basis)

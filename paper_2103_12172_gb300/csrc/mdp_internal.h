@@ -80,7 +80,8 @@ struct Batch {
 };
 
 constexpr int FSW = 24;  // doubles per forward-sweep table row
-constexpr int FFT_POINTS = 4096;  // complex values per block of the dense-row FFT kernels (64 KiB)
+constexpr int FFT_POINTS = 4096;        // longest transform (2 Nx) of the dense-row FFT kernels (64 KiB)
+constexpr int FFT_BLOCK_POINTS = 1024;  // complex values per block when 2 Nx is shorter: fpb = 1024 / (2 Nx)
 
 // Host buffer of the plan's tables: page-locked (cudaMallocHost) for plans with a device, so
 // that uploads (plan creation, mdp_plan_update_k) run at full link speed; plain heap memory for
@@ -159,6 +160,7 @@ struct mdp_plan {
   long long ws_doubles = 0;
   int *d_status = nullptr;
   int *d_fstatus = nullptr;               // status word of the device factorisation
+  int fft_smem = 16;                     // dynamic shared memory of the FFT kernels: max fpb * 2 Nx * 16 B
   mdp::HostBuf<mdp::SubDesc> sub_stage;  // pinned copy of the subdomain descriptors (async upload)
   mdp::HostBuf<int> h_fstatus;           // pinned read-back of d_fstatus
   bool host_stale = false;               // device tables refactored since the host tables were built

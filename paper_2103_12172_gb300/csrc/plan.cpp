@@ -79,7 +79,7 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   d.R2 = d.xsym ? 8 * d.Ph + 4 * (d.Py - 4) : d.R;  // (sum, difference) per pair unit
   d.nrec = -1;
   d.rows_fft = (d.Nx & (d.Nx - 1)) == 0 && 2 * d.Nx <= FFT_POINTS && d.Nx >= 8;
-  d.fpb = d.rows_fft ? FFT_POINTS / (2 * d.Nx) : 0;
+  d.fpb = d.rows_fft ? std::max(1, FFT_BLOCK_POINTS / (2 * d.Nx)) : 0;
   d.nfirst = d.cplx ? 0 : 1;
   d.Nt = d.cplx ? in.ny : in.ny - 2;
   d.i0 = (nlo - 1) - d.nfirst;
@@ -526,6 +526,9 @@ mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n) {
     if (st != MDP_OK) return st;
   }
   find_leaders(p);
+  p->fft_smem = 16;
+  for (auto &hs : p->subs)
+    if (hs.d.rows_fft) p->fft_smem = std::max(p->fft_smem, hs.d.fpb * 2 * hs.d.Nx * 16);
   if (!layout_tables(p)) return MDP_ERR_NOMEM;
   mdp_status st = factor_all(p->subs);
   if (st != MDP_OK) return st;

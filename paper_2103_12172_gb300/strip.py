@@ -51,6 +51,33 @@ class ProjectWithReceivers(torch.autograd.Function):
         return gk.to(dtype=dtype, device=device), None
 
 
+class LeastSquares(torch.autograd.Function):
+    """x = argmin ||A x - b|| for a full-column-rank A (m >= n) by Householder QR of the
+    column-equilibrated A D (Section 3.5, steps 2(b)-(c); the scaling leaves the minimiser
+    unchanged and improves the conditioning of R). The backward pass uses the closed form of the
+    minimiser's derivative instead of differentiating the factorisation: with r = b - A x and
+    w = (A^H A)^{-1} g = D R^{-1} R^{-H} D g for the incoming gradient g,
+        grad_b = A w,   grad_A = r w^H - (A w) x^H."""
+
+    @staticmethod
+    def forward(ctx, A, b):
+        D = 1.0 / torch.linalg.vector_norm(A, dim=0)
+        Qf, R = torch.linalg.qr(A * D)
+        x = D * torch.linalg.solve_triangular(R, (Qf.conj().transpose(0, 1) @ b)[:, None], upper=True)[:, 0]
+        ctx.save_for_backward(A, b, x, R, D)
+        return x
+
+    @staticmethod
+    def backward(ctx, g):
+        A, b, x, R, D = ctx.saved_tensors
+        t = torch.linalg.solve_triangular(R.conj().transpose(0, 1), (D * g)[:, None], upper=False)
+        w = D * torch.linalg.solve_triangular(R, t, upper=True)[:, 0]
+        Aw = A @ w
+        r = b - A @ x
+        grad_A = torch.outer(r, w.conj()) - torch.outer(Aw, x.conj())
+        return grad_A, Aw
+
+
 def cheb_coeffs(fvals, n):
     """Chebyshev coefficients of the degree n-1 interpolant from values at the n first-kind
     Chebyshev points x_i = cos(pi (i + 1/2) / n) (i = 0..n-1): c_m = (2/n) sum_i f(x_i) T_m(x_i),
@@ -215,10 +242,7 @@ class LayeredStrip:
             coef.append(cj)
         A = torch.cat(A_rows)
         b = torch.cat(b_rows)
-        # columns scaled to unit norm (same minimiser, better-conditioned QR), x = D y
-        D = 1.0 / torch.linalg.vector_norm(A, dim=0)
-        Qf, R = torch.linalg.qr(A * D)
-        xsol = D * torch.linalg.solve_triangular(R, (Qf.conj().transpose(0, 1) @ b)[:, None], upper=True)[:, 0]
+        xsol = LeastSquares.apply(A, b)
         cvecs = []
         for j in range(N):
             parts0, parts1 = [], []
