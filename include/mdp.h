@@ -191,6 +191,14 @@ mdp_status mdp_potential(mdp_plan *p, int sub, int ncols, const mdp_c64 *xi, mdp
 mdp_status mdp_source_terms(mdp_plan *p, int sub, const mdp_c64 *f, const mdp_c64 *src4, mdp_c64 *F, mdp_c64 *u,
                             void *cuda_stream);
 
+/* Householder QR of a dense complex matrix (the least-squares step of the coupled subdomain
+ * system, Section 3.5 steps 2(b)-(c)). A: device, column-major, m rows, n + nrhs columns,
+ * leading dimension lda >= m; n <= m. Factors the first n columns in place (R in the upper
+ * triangle, the reflectors H_k = I - tau_k v_k v_k^H below the diagonal with v_k(k) = 1 implied)
+ * and applies Q^H to the nrhs columns after them; tau: device [n]. The least-squares solution
+ * of A(:, 0:n) x = b is then R^{-1} (Q^H b)(0:n). Enqueued on cuda_stream; no allocation. */
+mdp_status mdp_householder_qr(int m, int n, int nrhs, mdp_c64 *A, long long lda, mdp_c64 *tau, void *cuda_stream);
+
 /* The extended basis densities xi_c = Ex Psi_c on gamma (Sections 3.2.3-3.2.4: the Taylor
  * extension of the Chebyshev basis function of column c, zero on the nodes owned by other
  * sides) for columns col0 .. col0+ncols-1 of subdomain `sub`: out device [ncols][|gamma|]

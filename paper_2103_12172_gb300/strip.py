@@ -51,6 +51,21 @@ class ProjectWithReceivers(torch.autograd.Function):
         return gk.to(dtype=dtype, device=device), None
 
 
+def householder_qr(A, b):
+    """(R, (Q^H b)[:n]) of a tall complex CUDA matrix A [m, n] by mdp_householder_qr."""
+    import ctypes as C
+    from . import _lib
+    m, n = A.shape
+    M = torch.empty((n + 1, m), dtype=torch.complex128, device=A.device)   # column-major [A | b]
+    M[:n] = A.transpose(0, 1)
+    M[n] = b
+    tau = torch.empty(n, dtype=torch.complex128, device=A.device)
+    _lib.check(_lib.lib().mdp_householder_qr(m, n, 1, C.c_void_p(M.data_ptr()), m, C.c_void_p(tau.data_ptr()),
+                                             C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+               "mdp_householder_qr")
+    return torch.triu(M[:n, :n].transpose(0, 1)), M[n, :n].clone()
+
+
 class LeastSquares(torch.autograd.Function):
     """x = argmin ||A x - b|| for a full-column-rank A (m >= n) by Householder QR of the
     column-equilibrated A D (Section 3.5, steps 2(b)-(c); the scaling leaves the minimiser
@@ -62,8 +77,12 @@ class LeastSquares(torch.autograd.Function):
     @staticmethod
     def forward(ctx, A, b):
         D = 1.0 / torch.linalg.vector_norm(A, dim=0)
-        Qf, R = torch.linalg.qr(A * D)
-        x = D * torch.linalg.solve_triangular(R, (Qf.conj().transpose(0, 1) @ b)[:, None], upper=True)[:, 0]
+        if A.is_cuda:
+            R, qb = householder_qr(A * D, b)          # libmdp's QR (mdp_householder_qr)
+        else:
+            Qf, R = torch.linalg.qr(A * D)
+            qb = Qf.conj().transpose(0, 1) @ b
+        x = D * torch.linalg.solve_triangular(R, qb[:, None], upper=True)[:, 0]
         ctx.save_for_backward(A, b, x, R, D)
         return x
 

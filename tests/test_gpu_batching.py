@@ -123,3 +123,22 @@ def test_qcache_stores_loads_and_fills_missing_blocks(mdp, tmp_path):
     os.remove(os.path.join(tmp_path, files[0]))
     third = cache.project(plan).cpu().numpy()
     assert np.abs(third - ref).max() <= tol and len(os.listdir(tmp_path)) == 2
+
+
+@pytest.mark.parametrize("m,n", [(500, 60), (3424, 384), (64, 64)])
+def test_householder_qr_gram_identity_and_least_squares(mdp, m, n):
+    """mdp_householder_qr: R^H R = A^H A, and R^{-1} (Q^H b) is the least-squares solution."""
+    from paper_2103_12172_gb300.strip import householder_qr
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+    A[:, 1] = 0.0
+    A[1, 1] = 2.0 + 0.0j        # a column already of the form beta e_k below row 0 ... plus row 0
+    A[0, 1] = 0.5
+    b = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    R, qb = householder_qr(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda())
+    R = R.cpu().numpy()
+    G = A.conj().T @ A
+    assert np.abs(R.conj().T @ R - G).max() <= 1e-12 * np.abs(G).max()
+    x = np.linalg.solve(R, qb.cpu().numpy())
+    xr = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert np.abs(x - xr).max() <= 1e-10 * np.abs(xr).max()
