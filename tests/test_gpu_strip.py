@@ -295,3 +295,71 @@ def test_two_by_two_checkerboard_with_mixed_grids_on_gpu(mdp):
                 assert np.abs(g_ - r_).max() < 1e-8 * np.abs(r_).max()
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert rates[0] > 3.4 and errs[-1] < 1e-7, (errs, rates)
+
+
+@pytest.mark.slow
+def test_config2_decomposition_with_dirichlet_plane_wave_data(mdp):
+    """The 2 x 2 decomposition at full size (257^2, k = 30, M* = 32, 1024 columns) with Dirichlet
+    outer data from the plane wave at angle 0.7: the GPU coupled solution at the receivers equals
+    the oracle's (1e-8) and the plane wave to the discretisation error (1.7e-4 here)."""
+    from oracle.dd import Strip, side_points
+    from paper_2103_12172_gb300.strip import LayeredStrip
+    subs = list(W.dd2x2_257().subdomains)
+    pos = [(i, j) for j in range(2) for i in range(2)]
+    k, th = 30.0, 0.7
+
+    def ue(x, y):
+        return np.exp(1j * k * (x * np.cos(th) + y * np.sin(th)))
+
+    def bc(j, side, kj, x, y):
+        return 1.0, 0.0, torch.exp(1j * k * (x * math.cos(th) + y * math.sin(th)))
+
+    rows = [s.ny // 2 for s in subs]
+    lay = LayeredStrip(subs, bc, rows, positions=pos)
+    got = [r.cpu().numpy() for r in lay.receivers(torch.tensor([k] * 4, dtype=torch.float64))]
+
+    def obc(j, side):
+        return 1.0, 0.0, (lambda s, side=side, j=j: ue(*side_points(subs[j], side, s)))
+    _, ref, _ = Strip(subs, obc, positions=pos).solve(rows)
+    for j, (g_, r_, s_) in enumerate(zip(got, ref, subs)):
+        assert np.abs(g_ - r_).max() < 1e-8 * np.abs(r_).max(), j
+        _, m0, cnt, _ = lay.rlayout[j]
+        ex = ue(s_.ax0 + (m0 + np.arange(cnt)) * s_.h, s_.ay0 + rows[j] * s_.h)
+        assert np.abs(g_ - ex).max() < 3e-4, j
+
+
+def test_config3_checkerboard_transmission_with_mixed_outer_data(mdp):
+    """The checkerboard configuration at full size (129^2 with k = 10 and 513^2 with k = 100,
+    M* = 48, 1536 columns): Dirichlet data on the x-facing outer sides, Neumann data on the
+    y-facing ones, sources making u = exp(i (3x + 2y)) exact in every subdomain. The coupled GPU
+    solution matches u over all of M+ of every subdomain."""
+    from paper_2103_12172_gb300.strip import LayeredStrip
+    AL, BE = 3.0, 2.0
+    subs = list(W.checker2x2().subdomains)
+    pos = [(i, j) for j in range(2) for i in range(2)]
+    ks = [s.k for s in subs]
+
+    def ue(x, y):
+        return np.exp(1j * (AL * x + BE * y))
+
+    def src(j):
+        def fun(x, y):
+            f = (ks[j] ** 2 - AL ** 2 - BE ** 2) * ue(x, y)
+            return f, 1j * AL * f, 1j * BE * f, -AL ** 2 * f, -BE ** 2 * f
+        return fun
+
+    def bc(j, side, kj, x, y):
+        u = torch.exp(1j * (AL * x + BE * y))
+        if side in (3, 4):
+            return 1.0, 0.0, u                                       # Dirichlet
+        return 0.0, 1.0, (-1j * BE if side == 1 else 1j * BE) * u    # Neumann
+
+    lay = LayeredStrip(subs, bc, [s.ny // 2 for s in subs], source=src, positions=pos)
+    fields = [f.cpu().numpy() for f in lay.field(torch.tensor(ks, dtype=torch.float64))]
+    errs = []
+    for j, s_ in enumerate(subs):
+        xx = s_.ax0 + np.arange(s_.nx) * s_.h
+        yy = s_.ay0 + np.arange(s_.ny) * s_.h
+        inside = ((xx[None, :] > s_.x0) & (xx[None, :] < s_.x1) & (yy[:, None] > s_.y0) & (yy[:, None] < s_.y1))
+        errs.append(np.abs(fields[j] - ue(xx[None, :], yy[:, None]))[inside].max())
+    assert max(errs) < 1e-5, errs
