@@ -199,6 +199,13 @@ mdp_status mdp_source_terms(mdp_plan *p, int sub, const mdp_c64 *f, const mdp_c6
  * of A(:, 0:n) x = b is then R^{-1} (Q^H b)(0:n). Enqueued on cuda_stream; no allocation. */
 mdp_status mdp_householder_qr(int m, int n, int nrhs, mdp_c64 *A, long long lda, mdp_c64 *tau, void *cuda_stream);
 
+/* mdp_householder_qr of `batch` matrices of the same shape at A + b*stride (stride >=
+ * lda * (n + nrhs)); tau: device [batch][n]. Used for the first stage of the structured least
+ * squares: one QR per subdomain's rows (those touch only that subdomain's unknowns), then one of
+ * the stacked triangular factors. */
+mdp_status mdp_householder_qr_batched(int batch, int m, int n, int nrhs, mdp_c64 *A, long long lda,
+                                      long long stride, mdp_c64 *tau, void *cuda_stream);
+
 /* The extended basis densities xi_c = Ex Psi_c on gamma (Sections 3.2.3-3.2.4: the Taylor
  * extension of the Chebyshev basis function of column c, zero on the nodes owned by other
  * sides) for columns col0 .. col0+ncols-1 of subdomain `sub`: out device [ncols][|gamma|]

@@ -8,7 +8,8 @@
 // holds tau_k, and the last nrhs columns hold Q^H b. The construction follows the textbook
 // Householder method: with x = A(k:m, k), alpha = x(0),
 //   beta = -sign(Re alpha) ||x||,  tau = (beta - alpha) / beta,  v = x / (alpha - beta), v(0) = 1.
-// One launch per column: block b applies H_k^H to column k+1+b (w = v^H a, a -= conj(tau) v w)
+// A batch of equal-shaped matrices (stride elements apart) is factored together: launch y
+// index = matrix. One launch per column: block b applies H_k^H to column k+1+b (w = v^H a, a -= conj(tau) v w)
 // and block 0, which holds column k+1, then forms the next reflector from it. Reductions run in
 // a fixed order (deterministic).
 #include "kernels_common.cuh"
@@ -59,15 +60,19 @@ __device__ void qr_reflector(int m, int k, double2 *A, long long lda, double2 *t
   }
 }
 
-__global__ void __launch_bounds__(kQrThreads) k_qr_first(int m, double2 *A, long long lda, double2 *tau) {
+__global__ void __launch_bounds__(kQrThreads) k_qr_first(int m, int n, double2 *A, long long lda, long long stride,
+                                                          double2 *tau) {
   __shared__ double sh[kQrThreads];
-  qr_reflector(m, 0, A, lda, tau, sh);
+  qr_reflector(m, 0, A + (long long)blockIdx.y * stride, lda, tau + (long long)blockIdx.y * n, sh);
 }
 
 // Step k: column k+1+blockIdx.x gets w = v^H a (v(k) = 1), a -= conj(tau) v w; block 0 then
 // forms the reflector of column k+1 for step k+1 (n: the number of columns to factor).
-__global__ void __launch_bounds__(kQrThreads) k_qr_step(int m, int n, int k, double2 *A, long long lda, double2 *tau) {
+__global__ void __launch_bounds__(kQrThreads) k_qr_step(int m, int n, int k, double2 *A, long long lda,
+                                                         long long stride, double2 *tau) {
   __shared__ double sh[kQrThreads];
+  A += (long long)blockIdx.y * stride;   // matrix blockIdx.y of the batch
+  tau += (long long)blockIdx.y * n;
   const double2 t = tau[k];
   const double2 *v = A + (long long)k * lda;
   double2 *a = A + (long long)(k + 1 + blockIdx.x) * lda;
@@ -99,16 +104,23 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_step(int m, int n, int k, dou
 }  // namespace
 }  // namespace mdp
 
-extern "C" mdp_status mdp_householder_qr(int m, int n, int nrhs, mdp_c64 *A, long long lda, mdp_c64 *tau,
-                                         void *cuda_stream) {
-  if (m < 1 || n < 1 || n > m || nrhs < 0 || !A || !tau || lda < m) return MDP_ERR_ARG;
+extern "C" mdp_status mdp_householder_qr_batched(int batch, int m, int n, int nrhs, mdp_c64 *A, long long lda,
+                                                 long long stride, mdp_c64 *tau, void *cuda_stream) {
+  if (batch < 1 || batch > 65535 || m < 1 || n < 1 || n > m || nrhs < 0 || !A || !tau || lda < m ||
+      (batch > 1 && stride < lda * (long long)(n + nrhs)))
+    return MDP_ERR_ARG;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   double2 *a = reinterpret_cast<double2 *>(A);
   double2 *t = reinterpret_cast<double2 *>(tau);
-  mdp::k_qr_first<<<1, mdp::kQrThreads, 0, st>>>(m, a, lda, t);
+  mdp::k_qr_first<<<dim3(1, batch), mdp::kQrThreads, 0, st>>>(m, n, a, lda, stride, t);
   for (int k = 0; k < n; ++k) {
     const int ncol = n + nrhs - k - 1;
-    if (ncol > 0) mdp::k_qr_step<<<ncol, mdp::kQrThreads, 0, st>>>(m, n, k, a, lda, t);
+    if (ncol > 0) mdp::k_qr_step<<<dim3(ncol, batch), mdp::kQrThreads, 0, st>>>(m, n, k, a, lda, stride, t);
   }
   return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_ERR_CUDA;
+}
+
+extern "C" mdp_status mdp_householder_qr(int m, int n, int nrhs, mdp_c64 *A, long long lda, mdp_c64 *tau,
+                                         void *cuda_stream) {
+  return mdp_householder_qr_batched(1, m, n, nrhs, A, lda, 0, tau, cuda_stream);
 }

@@ -66,6 +66,41 @@ def householder_qr(A, b):
     return torch.triu(M[:n, :n].transpose(0, 1)), M[n, :n].clone()
 
 
+def structured_qr(A, b, rows, cols):
+    """(R, (Q^H b)[:n]) of the stacked system A [m, n] whose row block j (rows[j] rows) has
+    nonzeros only in the columns cols[j], in two stages: a batched QR of every block restricted
+    to its columns (mdp_householder_qr_batched; blocks zero-padded to a common shape), then the
+    QR of the stacked triangular factors placed in their global columns. A^H A and the
+    least-squares minimiser are those of the whole system; the work is a fraction of one QR of
+    A when the blocks are narrow."""
+    import ctypes as C
+    from . import _lib
+    n = A.shape[1]
+    batch = len(rows)
+    mmax = max(rows)
+    nmax = max(len(c) for c in cols)
+    if mmax < nmax or batch * nmax < n:
+        return householder_qr(A, b)
+    M = torch.zeros((batch, nmax + 1, mmax), dtype=torch.complex128, device=A.device)   # column-major blocks
+    r0 = 0
+    for j, (g, cj) in enumerate(zip(rows, cols)):
+        idx = torch.as_tensor(cj, device=A.device)
+        M[j, :len(cj), :g] = A[r0:r0 + g].index_select(1, idx).transpose(0, 1)
+        M[j, nmax, :g] = b[r0:r0 + g]
+        r0 += g
+    tau = torch.empty((batch, nmax), dtype=torch.complex128, device=A.device)
+    _lib.check(_lib.lib().mdp_householder_qr_batched(batch, mmax, nmax, 1, C.c_void_p(M.data_ptr()), mmax,
+                                                     (nmax + 1) * mmax, C.c_void_p(tau.data_ptr()),
+                                                     C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+               "mdp_householder_qr_batched")
+    S = torch.zeros((batch * nmax, n), dtype=torch.complex128, device=A.device)
+    t = M[:, nmax, :nmax].reshape(-1).clone()
+    for j, cj in enumerate(cols):
+        Rj = torch.triu(M[j, :nmax, :nmax].transpose(0, 1))
+        S[j * nmax:(j + 1) * nmax].index_copy_(1, torch.as_tensor(cj, device=A.device), Rj[:, :len(cj)])
+    return householder_qr(S, t)
+
+
 class LeastSquares(torch.autograd.Function):
     """x = argmin ||A x - b|| for a full-column-rank A (m >= n) by Householder QR of the
     column-equilibrated A D (Section 3.5, steps 2(b)-(c); the scaling leaves the minimiser
@@ -75,9 +110,11 @@ class LeastSquares(torch.autograd.Function):
         grad_b = A w,   grad_A = r w^H - (A w) x^H."""
 
     @staticmethod
-    def forward(ctx, A, b):
+    def forward(ctx, A, b, blocks=None):
         D = 1.0 / torch.linalg.vector_norm(A, dim=0)
-        if A.is_cuda:
+        if A.is_cuda and blocks is not None:
+            R, qb = structured_qr(A * D, b, *blocks)  # per-subdomain QRs, then the stacked factors
+        elif A.is_cuda:
             R, qb = householder_qr(A * D, b)          # libmdp's QR (mdp_householder_qr)
         else:
             Qf, R = torch.linalg.qr(A * D)
@@ -94,7 +131,7 @@ class LeastSquares(torch.autograd.Function):
         Aw = A @ w
         r = b - A @ x
         grad_A = torch.outer(r, w.conj()) - torch.outer(Aw, x.conj())
-        return grad_A, Aw
+        return grad_A, Aw, None
 
 
 def cheb_coeffs(fvals, n):
@@ -222,13 +259,14 @@ class LayeredStrip:
                 if not self.outer(j, side):
                     idx[("if", j, side)] = n
                     n += 2 * M
-        A_rows, b_rows, coef = [], [], []
+        A_rows, b_rows, coef, col_sets = [], [], [], []
         for j in range(N):
             G, nc, off, _ = self.layout[j]
             Q = out[off:off + G * nc].view(nc, G).transpose(0, 1)          # [G, 8M]
             A = torch.zeros(G, n, dtype=torch.complex128, device=out.device)
             b = torch.zeros(G, dtype=torch.complex128, device=out.device)
             cj = []
+            used = []                 # the unknowns this subdomain's rows touch
             for side in (1, 2, 3, 4):
                 Q0 = Q[:, (side - 1) * M: side * M]
                 Q1 = Q[:, 4 * M + (side - 1) * M: 4 * M + side * M]
@@ -247,11 +285,13 @@ class LayeredStrip:
                         b = b - Q0 @ (d / alpha)
                         cj.append(("dirichlet", c, d, alpha, beta))
                     A = A + torch.nn.functional.pad(blk, (pad_l, pad_r))
+                    used.extend(range(c, c + M))
                 else:
                     key, sgn = self.iface(j, side)
                     c = idx[("if",) + key]
                     blk = torch.cat([Q0, sgn * Q1], dim=1)
                     A = A + torch.nn.functional.pad(blk, (c, n - c - 2 * M))
+                    used.extend(range(c, c + 2 * M))
                     cj.append(("if", c, sgn))
             st = self.source_terms(j, self.plan_k(j))
             if st is not None:
@@ -259,9 +299,10 @@ class LayeredStrip:
             A_rows.append(A)
             b_rows.append(b)
             coef.append(cj)
+            col_sets.append(sorted(set(used)))
         A = torch.cat(A_rows)
         b = torch.cat(b_rows)
-        xsol = LeastSquares.apply(A, b)
+        xsol = LeastSquares.apply(A, b, ([r.shape[0] for r in A_rows], col_sets))
         cvecs = []
         for j in range(N):
             parts0, parts1 = [], []
