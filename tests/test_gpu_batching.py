@@ -1,4 +1,4 @@
-"""Batching schedule (SURVEY row a7): CUDA-graph replay, stream capture of the allocation-free
+"""Batching schedule: CUDA-graph replay, stream capture of the allocation-free
 calls, multi-wave schedules with uneven subdomains, and the tile autotuner."""
 import numpy as np
 import pytest

@@ -1,4 +1,4 @@
-"""Layered strip (SURVEY row a10): the GPU DD pipeline against the oracle's DD solve, and the
+"""Layered strip: the GPU DD pipeline against the oracle's DD solve, and the
 wavenumber gradient of the receiver misfit (autograd through the coupling, libmdp's adjoint for
 the AP solves) against central differences."""
 import math
