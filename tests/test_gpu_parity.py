@@ -226,3 +226,36 @@ def test_source_terms_match_oracle(dev, ap, n):
     F, u = F.cpu().numpy(), u.cpu().numpy()
     assert np.abs(F - Fr).max() <= TOL * np.abs(Fr).max()
     assert np.abs(u - ur).max() <= TOL * np.abs(ur).max()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n", [2049, 1001])
+def test_largest_grids_against_the_sine_transform_closed_form(dev, n):
+    """Maximum sizes: a 2049^2 Dirichlet AP (the longest dense-row FFT, 2 Nx = 4096, one column
+    per block) and a 1001^2 one (Nx = 1000: the direct sums), every basis column against the
+    oracle's extension and stencil with the AP solved in closed form by the 2-D DST-I (the
+    closed form is pinned against the sparse LU; a sparse LU at these sizes is out of reach)."""
+    import scipy.fft
+    from oracle.extension import basis_column
+    from oracle.grid import grid_sets
+    from oracle.scheme import apply_L
+    k = 37.3
+    sub = W.small_subdomain(n, k, W.AP_DIRICHLET4, 2)
+    plan = make_plan(dev, [sub], 16)
+    G, nc, _, _ = plan.layout(0)
+    got = plan.project().cpu().numpy().reshape(nc, G)
+    gs = grid_sets(sub)
+    h, ncell = sub.h, n - 1
+    lam = -4 * np.sin(np.pi * np.arange(1, ncell) / (2 * ncell)) ** 2
+    LP, LQ = np.meshgrid(lam, lam)
+    mu = (LP + LQ) / h**2 + LP * LQ / (6 * h**2) + k**2 + k**2 * (LP + LQ) / 12
+    ref = np.zeros((nc, G), complex)
+    for c in range(nc):
+        w = np.zeros((n, n), complex)
+        w[gs.gamma_n, gs.gamma_m] = basis_column(gs, k, sub.n_modes, c)
+        r = apply_L(w, h, k)
+        r[~gs.Mp] = 0.0
+        u = np.zeros((n, n), complex)
+        u[1:-1, 1:-1] = scipy.fft.idstn(scipy.fft.dstn(r[1:-1, 1:-1], type=1) / mu, type=1)
+        ref[c] = -u[gs.gamma_n, gs.gamma_m]
+    assert rel_col_err(got, ref) < TOL
