@@ -424,14 +424,42 @@ __device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const
   if (CF) for (; i >= ilo; --i) back_complex(i);
 }
 
+// Asynchronous global -> shared copies (cp.async): operands of rows ahead are in flight while
+// the current row is swept, without holding registers for them.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Staging of the projection sweep: each warp owns TRI_STAGES stages of shared memory and copies
+// the operands of row i + TRI_STAGES while row i is swept. Forward stage: the table row (FSW
+// doubles) and up to 4 ring values per lane ([slot][lane]); backward stage: table doubles 18..23
+// (u1, u2, swap flag) and the lane's stored y~.
+constexpr int TRI_STAGES = 2;
+template <bool CIN>
+__host__ __device__ constexpr int tri_stage_bytes() { return FSW * 8 + 4 * 32 * (CIN ? 16 : 8); }
+template <bool CIN>
+__host__ __device__ constexpr int tri_smem_bytes() { return TRI_WARPS * TRI_STAGES * tri_stage_bytes<CIN>(); }
+
 // The projection's sweep over the condensed, pivot-scaled table (plan: build_fs): rows
 // i0 .. itop, y~ = y / d stored, so the back substitution is x = y~ - u1 x' - u2 x''. The rows
 // with real entries [frlo, frhi) use real coefficients; while no complex value has entered the
 // sweep (real densities and the run starts at i0) the forward recurrence is real.
-// CD: complex mode-space data (complex AP or complex densities).
+// CD: complex mode-space data (complex AP or complex densities). sw: the warp's stages; the
+// active lanes are 0 .. nact-1 (mask).
 template <bool CD, bool CIN>
 __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, const double *tab, double *ws, int b,
-                                            int q) {
+                                            int q, char *sw, int lane, int nact, unsigned mask) {
+  constexpr int VS = CIN ? 16 : 8, SB = tri_stage_bytes<CIN>(), RING = FSW * 8;
+  // descriptor fields in registers: the copies' memory clobbers would otherwise reload them
+  const int i0 = d.i0, nfirst = d.nfirst, nlo = d.nlo, nhi = d.nhi, Nq = d.Nq, Ph = d.Ph;
+  const bool xsym = d.xsym;
   const double *T = tab + d.fs_off + (long long)(q - 1) * d.NYf * FSW;
   const double *sg = tab + d.seg_off + 5 * (q - 1);
   const int frlo = (int)sg[2], frhi = (int)sg[3], itop = (int)sg[4];
@@ -446,169 +474,237 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
   const int nc = it.ncols, P = d.Px;
   const long long ybase = (long long)(q - 1) * d.NYf * nc + b;
   auto ystore = [&](int i, cplx v) {
-    const long long o = ybase + (long long)(i - d.i0) * nc;
+    const long long o = ybase + (long long)(i - i0) * nc;
     if (CD) st2(y + 2 * o, v); else y[o] = v.re;
   };
-  auto yload = [&](int i) -> cplx {
-    const long long o = ybase + (long long)(i - d.i0) * nc;
-    return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
-  };
-  // ring data of grid row n: dense rows give gr (complex if CIN); middle rows give the slot values
   auto dense = [&](int n) -> int {
-    return n == d.nlo ? 0 : n == d.nlo + 1 ? 1 : n == d.nhi - 1 ? 2 : n == d.nhi ? 3 : -1;
+    return n == nlo ? 0 : n == nlo + 1 ? 1 : n == nhi - 1 ? 2 : n == nhi ? 3 : -1;
   };
-  auto rv = [&](long long slot) -> cplx { return CIN ? ld2(r + 2 * (slot * nc + b)) : cmk(r[slot * nc + b], 0.0); };
+  // ---- staging: forward rows
+  auto fetch_fwd = [&](int i) {
+    char *st = sw + ((i - i0) & (TRI_STAGES - 1)) * SB;
+    const double *src = T + (long long)(i - i0) * FSW;
+    if (nact >= FSW / 2) {
+      if (lane < FSW / 2) cp_async16(st + 16 * lane, src + 2 * lane);
+    } else {
+      for (int c = lane; c < FSW / 2; c += nact) cp_async16(st + 16 * c, src + 2 * c);
+    }
+    const int n = i + 1 + nfirst;
+    if (n >= nlo && n <= nhi) {
+      char *rb = st + RING + VS * lane;
+      auto cpv = [&](int slot, const double *base, long long o) {
+        if (CIN) cp_async16(rb + slot * 32 * VS, base + 2 * o); else cp_async8(rb + slot * 32 * VS, base + o);
+      };
+      const int rr = dense(n);
+      if (rr >= 0) {
+        cpv(0, gr, ((long long)rr * Nq + (q - 1)) * nc + b);
+      } else if (xsym) {
+        const long long base = 8LL * Ph + 4 * (n - nlo - 2) + par;
+        cpv(0, r, base * nc + b);
+        cpv(1, r, (base + 2) * nc + b);
+      } else {
+        const long long ri = 2 * P + 4 * (n - nlo - 2);
+        for (int s_ = 0; s_ < 4; ++s_) cpv(s_, r, (ri + s_) * nc + b);
+      }
+    }
+    cp_async_commit();
+  };
+  // ring value `slot` of this lane in stage st
+  auto sv = [&](const char *st, int slot) -> cplx {
+    const double *p = reinterpret_cast<const double *>(st + RING + VS * lane + slot * 32 * VS);
+    return CIN ? ld2(p) : cmk(p[0], 0.0);
+  };
   // raw right-hand side of grid row n (swapped steps)
-  auto graw = [&](int n) -> cplx {
-    if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
-    const int rr = dense(n);
-    if (rr >= 0) {
-      const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b;
-      return CIN ? ld2(gr + 2 * o) : cmk(gr[o], 0.0);
+  auto graw = [&](const char *st, int n) -> cplx {
+    if (n < nlo || n > nhi) return cmk(0.0, 0.0);
+    if (dense(n) >= 0) return sv(st, 0);
+    if (xsym) {
+      const cplx a0 = sv(st, 0);
+      return caxpy(sm1, sv(st, 1), cmk(sm0 * a0.re, sm0 * a0.im));
     }
-    if (d.xsym) {
-      const long long base = 8LL * d.Ph + 4 * (n - d.nlo - 2) + par;
-      return caxpy(sm1, rv(base + 2), cmk(sm0 * rv(base).re, sm0 * rv(base).im));
-    }
-    const long long ri = 2 * P + 4 * (n - d.nlo - 2);
     cplx v = cmk(0.0, 0.0);
-    v = caxpy(sm0, rv(ri), v); v = caxpy(sm1, rv(ri + 1), v); v = caxpy(sm2, rv(ri + 2), v); v = caxpy(sm3, rv(ri + 3), v);
+    v = caxpy(sm0, sv(st, 0), v); v = caxpy(sm1, sv(st, 1), v); v = caxpy(sm2, sv(st, 2), v); v = caxpy(sm3, sv(st, 3), v);
     return v;
   };
   // scaled right-hand side g / d_{i+1} of grid row n from table row `row` (complex coefficients)
-  auto ghat_c = [&](const double *row, int n) -> cplx {
-    if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
-    const int rr = dense(n);
+  auto ghat_c = [&](const char *st, const double *row, int n) -> cplx {
+    if (n < nlo || n > nhi) return cmk(0.0, 0.0);
     const cplx sc = ld2(row + 8);
-    if (rr >= 0) {
-      const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b;
-      if (CIN) return cmul(sc, ld2(gr + 2 * o));
-      const double g = gr[o];
-      return cmk(sc.re * g, sc.im * g);
+    if (dense(n) >= 0) {
+      const cplx g = sv(st, 0);
+      if (CIN) return cmul(sc, g);
+      return cmk(sc.re * g.re, sc.im * g.re);
     }
-    if (d.xsym) {
-      const long long base = 8LL * d.Ph + 4 * (n - d.nlo - 2) + par;
-      if (CIN) return cadd(cmul(ld2(row + 10), rv(base)), cmul(ld2(row + 12), rv(base + 2)));
-      const double a0 = r[base * nc + b], a1 = r[(base + 2) * nc + b];
+    if (xsym) {
+      if (CIN) return cadd(cmul(ld2(row + 10), sv(st, 0)), cmul(ld2(row + 12), sv(st, 1)));
+      const double a0 = sv(st, 0).re, a1 = sv(st, 1).re;
       const cplx c0 = ld2(row + 10), c1 = ld2(row + 12);
       return cmk(fma(c1.re, a1, c0.re * a0), fma(c1.im, a1, c0.im * a0));
     }
-    const long long ri = 2 * P + 4 * (n - d.nlo - 2);
     cplx v = cmk(0.0, 0.0);
-    for (int s_ = 0; s_ < 4; ++s_) v = cadd(v, cmul(ld2(row + 10 + 2 * s_), rv(ri + s_)));
+    for (int s_ = 0; s_ < 4; ++s_) v = cadd(v, cmul(ld2(row + 10 + 2 * s_), sv(st, s_)));
     return v;
   };
   // the same with real coefficients (rows of the real run)
-  auto ghat_r = [&](const double *row, int n) -> cplx {
-    if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
-    const int rr = dense(n);
+  auto ghat_r = [&](const char *st, const double *row, int n) -> cplx {
+    if (n < nlo || n > nhi) return cmk(0.0, 0.0);
     const double sc = row[8];
-    if (rr >= 0) {
-      const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b;
-      if (CIN) { const cplx g = ld2(gr + 2 * o); return cmk(sc * g.re, sc * g.im); }
-      return cmk(sc * gr[o], 0.0);
+    if (dense(n) >= 0) {
+      const cplx g = sv(st, 0);
+      if (CIN) return cmk(sc * g.re, sc * g.im);
+      return cmk(sc * g.re, 0.0);
     }
-    if (d.xsym) {
-      const long long base = 8LL * d.Ph + 4 * (n - d.nlo - 2) + par;
-      const cplx a0 = rv(base);
-      return caxpy(row[12], rv(base + 2), cmk(row[10] * a0.re, row[10] * a0.im));
+    if (xsym) {
+      const cplx a0 = sv(st, 0);
+      return caxpy(row[12], sv(st, 1), cmk(row[10] * a0.re, row[10] * a0.im));
     }
-    const long long ri = 2 * P + 4 * (n - d.nlo - 2);
     cplx v = cmk(0.0, 0.0);
-    for (int s_ = 0; s_ < 4; ++s_) v = caxpy(row[10 + 2 * s_], rv(ri + s_), v);
+    for (int s_ = 0; s_ < 4; ++s_) v = caxpy(row[10 + 2 * s_], sv(st, s_), v);
     return v;
   };
   // the swap flag (0.0 or 1.0) tested on its bits: an integer compare, not an FP64-pipe DSETP
-  auto swapped = [](const double *row) { return __double_as_longlong(row[22]) != 0; };
+  auto swapped = [](double flag) { return __double_as_longlong(flag) != 0; };
+  // stage of row i ready (this lane's copies complete, then every lane's visible)
+  auto begin_fwd = [&](int i) -> const char * {
+    cp_async_wait<TRI_STAGES - 1>();
+    __syncwarp(mask);
+    return sw + ((i - i0) & (TRI_STAGES - 1)) * SB;
+  };
+  // every lane is done with the stage of row i: refill it with row i + TRI_STAGES
+  auto end_fwd = [&](int i) {
+    __syncwarp(mask);
+    if (i + TRI_STAGES < itop) fetch_fwd(i + TRI_STAGES); else cp_async_commit();
+  };
+  for (int j = 0; j < TRI_STAGES; ++j) {
+    if (i0 + j < itop) fetch_fwd(i0 + j); else cp_async_commit();
+  }
   // ---- forward sweep
   cplx ct = cmk(0.0, 0.0);
-  int i = d.i0;
+  int i = i0;
   if (CD) {
     for (; i < min(frlo, itop); ++i) {
-      const double *row = T + (long long)(i - d.i0) * FSW;
-      const int n = i + 1 + d.nfirst;
-      if (!swapped(row)) { ystore(i, ct); ct = cfms(ghat_c(row, n), ld2(row), ct); }
+      const char *st = begin_fwd(i);
+      const double *row = reinterpret_cast<const double *>(st);
+      const int n = i + 1 + nfirst;
+      if (!swapped(row[22])) { ystore(i, ct); ct = cfms(ghat_c(st, row, n), ld2(row), ct); }
       else {
-        const cplx g = graw(n);
+        const cplx g = graw(st, n);
         ystore(i, cmul(ld2(row + 6), g));
         ct = cfms(cmul(ld2(row + 2), ct), ld2(row + 4), g);
       }
+      end_fwd(i);
     }
   }
   {
     const int e = min(max(frhi, i), itop);
-    if (!CIN && i == d.i0) {     // real data so far: real recurrence
+    if (!CIN && i == i0) {     // real data so far: real recurrence
       for (; i < e; ++i) {
-        const double *row = T + (long long)(i - d.i0) * FSW;
-        const int n = i + 1 + d.nfirst;
-        if (!swapped(row)) { ystore(i, ct); ct.re = fma(-row[0], ct.re, ghat_r(row, n).re); }
+        const char *st = begin_fwd(i);
+        const double *row = reinterpret_cast<const double *>(st);
+        const int n = i + 1 + nfirst;
+        if (!swapped(row[22])) { ystore(i, ct); ct.re = fma(-row[0], ct.re, ghat_r(st, row, n).re); }
         else {
-          const double g = graw(n).re;
+          const double g = graw(st, n).re;
           ystore(i, cmk(row[6] * g, 0.0));
           ct.re = fma(-row[4], g, row[2] * ct.re);
         }
+        end_fwd(i);
       }
     } else {
       for (; i < e; ++i) {
-        const double *row = T + (long long)(i - d.i0) * FSW;
-        const int n = i + 1 + d.nfirst;
-        if (!swapped(row)) { ystore(i, ct); ct = caxpy(-row[0], ct, ghat_r(row, n)); }
+        const char *st = begin_fwd(i);
+        const double *row = reinterpret_cast<const double *>(st);
+        const int n = i + 1 + nfirst;
+        if (!swapped(row[22])) { ystore(i, ct); ct = caxpy(-row[0], ct, ghat_r(st, row, n)); }
         else {
-          const cplx g = graw(n);
+          const cplx g = graw(st, n);
           ystore(i, cmk(row[6] * g.re, row[6] * g.im));
           ct = caxpy(-row[4], g, cmk(row[2] * ct.re, row[2] * ct.im));
         }
+        end_fwd(i);
       }
     }
   }
   if (CD) {
     for (; i < itop; ++i) {
-      const double *row = T + (long long)(i - d.i0) * FSW;
-      const int n = i + 1 + d.nfirst;
-      if (!swapped(row)) { ystore(i, ct); ct = cfms(ghat_c(row, n), ld2(row), ct); }
+      const char *st = begin_fwd(i);
+      const double *row = reinterpret_cast<const double *>(st);
+      const int n = i + 1 + nfirst;
+      if (!swapped(row[22])) { ystore(i, ct); ct = cfms(ghat_c(st, row, n), ld2(row), ct); }
       else {
-        const cplx g = graw(n);
+        const cplx g = graw(st, n);
         ystore(i, cmul(ld2(row + 6), g));
         ct = cfms(cmul(ld2(row + 2), ct), ld2(row + 4), g);
       }
+      end_fwd(i);
     }
   }
   ystore(itop, ct);
+  // the stored y~ are read back below by this thread's asynchronous copies: order them after
+  // its stores
+  __threadfence_block();
   // ---- back substitution (rows nlo-1 .. nhi+1 are kept)
-  const int ikeep = d.nhi + 1 - d.nfirst;
+  auto fetch_back = [&](int i) {
+    char *st = sw + ((itop - i) & (TRI_STAGES - 1)) * SB;
+    const double *src = T + (long long)(i - i0) * FSW + 18;
+    if (nact >= 3) {
+      if (lane < 3) cp_async16(st + 16 * lane, src + 2 * lane);
+    } else {
+      for (int c = lane; c < 3; c += nact) cp_async16(st + 16 * c, src + 2 * c);
+    }
+    const long long o = ybase + (long long)(i - i0) * nc;
+    if (CD) cp_async16(st + RING + 16 * lane, y + 2 * o); else cp_async8(st + RING + 8 * lane, y + o);
+    cp_async_commit();
+  };
+  for (int j = 0; j < TRI_STAGES; ++j) {
+    if (itop - j >= i0) fetch_back(itop - j); else cp_async_commit();
+  }
+  const int ikeep = nhi + 1 - nfirst;
   cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
-  for (i = itop; i >= d.i0; --i) {
-    const double *row = T + (long long)(i - d.i0) * FSW;
-    const cplx yi = yload(i);
+  for (i = itop; i >= i0; --i) {
+    cp_async_wait<TRI_STAGES - 1>();
+    __syncwarp(mask);
+    const char *st = sw + ((itop - i) & (TRI_STAGES - 1)) * SB;
+    const double *rb = reinterpret_cast<const double *>(st);        // table doubles 18..23
+    const double *yp = reinterpret_cast<const double *>(st + RING + (CD ? 16 : 8) * lane);
+    const cplx yi = CD ? ld2(yp) : cmk(yp[0], 0.0);
     cplx x;
     if (!CD || (i >= frlo && i < frhi)) {
-      x = cmk(fma(-row[18], x1.re, yi.re), CD ? fma(-row[18], x1.im, yi.im) : 0.0);
-      if (swapped(row)) { x.re = fma(-row[20], x2.re, x.re); if (CD) x.im = fma(-row[20], x2.im, x.im); }
+      x = cmk(fma(-rb[0], x1.re, yi.re), CD ? fma(-rb[0], x1.im, yi.im) : 0.0);
+      if (swapped(rb[4])) { x.re = fma(-rb[2], x2.re, x.re); if (CD) x.im = fma(-rb[2], x2.im, x.im); }
     } else {
-      x = cfms(yi, ld2(row + 18), x1);
-      if (swapped(row)) x = cfms(x, ld2(row + 20), x2);
+      x = cfms(yi, ld2(rb), x1);
+      if (swapped(rb[4])) x = cfms(x, ld2(rb + 2), x2);
     }
+    __syncwarp(mask);
+    if (i - TRI_STAGES >= i0) fetch_back(i - TRI_STAGES); else cp_async_commit();
     if (i <= ikeep) ystore(i, x);
     x2 = x1; x1 = x;
   }
 }
 
 template <bool CIN, bool FULL>
-__global__ void __launch_bounds__(128, 8) k_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
+__global__ void __launch_bounds__(32 * TRI_WARPS, 32 / TRI_WARPS) k_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
                                              double *ws) {
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
-  const int q = (local / cb) * 4 + threadIdx.y + 1;
-  if (b >= it.ncols || q > d.Nq) return;
+  const int q = (local / cb) * TRI_WARPS + threadIdx.y + 1;
   if (FULL) {
+    if (b >= it.ncols || q > d.Nq) return;
     if (d.cplx) tri_body<true, CIN, true>(it, d, tab, pivtab, ws, b, q);
     else tri_body<false, CIN, true>(it, d, tab, pivtab, ws, b, q);
   } else {
-    if (d.cplx || CIN) tri_fs_body<true, CIN>(it, d, tab, ws, b, q);
-    else tri_fs_body<false, CIN>(it, d, tab, ws, b, q);
+    // a warp shares q; its active lanes (columns b < ncols) are lanes 0 .. nact-1
+    extern __shared__ __align__(16) char tri_sm[];
+    const bool act = b < it.ncols && q <= d.Nq;
+    const unsigned mask = __ballot_sync(0xffffffffu, act);
+    if (!act) return;
+    char *sw = tri_sm + threadIdx.y * TRI_STAGES * tri_stage_bytes<CIN>();
+    if (d.cplx || CIN) tri_fs_body<true, CIN>(it, d, tab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
+    else tri_fs_body<false, CIN>(it, d, tab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
   }
 }
 
@@ -1204,6 +1300,11 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
   if (e == cudaSuccess) e = set_adj_kernel_attributes();
+  // the sweep's staging buffers take 32 x 2.4 KiB per SM at full occupancy: prefer shared memory
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tri<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tri<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   return e;
 }
 
@@ -1213,7 +1314,7 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
   const SubDesc *ds = p->d_subs;
   const double *tab = p->d_tables;
   double *ws = p->d_ws;
-  const dim3 b8(32, 8), b4(32, 4);
+  const dim3 b8(32, 8), btri(32, TRI_WARPS);
 #define MDP_LAUNCH(fam, ...)                      \
   do {                                            \
     if (fb[fam].total_blocks > 0) {               \
@@ -1227,8 +1328,8 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
   else MDP_LAUNCH(F_RES, k_residual<true, false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
   if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
   else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
-  if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
-  else MDP_LAUNCH(F_TRI, k_tri<true, false><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false><<<grid1(fb[F_TRI].total_blocks), btri, tri_smem_bytes<false>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  else MDP_LAUNCH(F_TRI, k_tri<true, false><<<grid1(fb[F_TRI].total_blocks), btri, tri_smem_bytes<true>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   if (basis) {
     MDP_LAUNCH(F_IROWS, k_inv_rows<false><<<grid1(fb[F_IROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
     MDP_LAUNCH(F_ICOLS, k_inv_cols<false><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
@@ -1247,15 +1348,15 @@ cudaError_t launch_adjoint(mdp_plan *p, const Batch *fb, int out_kind, const dou
   const SubDesc *ds = p->d_subs;
   const double *tab = p->d_tables;
   double *ws = p->d_ws;
-  const dim3 b8(32, 8), b4(32, 4);
+  const dim3 b8(32, 8), btri(32, TRI_WARPS);
   if (grad_k) {  // forward recompute with every mode-space row kept, and the k-derivative sources
     if (basis) MDP_LAUNCH(F_EXT, k_extend<<<grid1(fb[F_EXT].total_blocks), 128, 0, st>>>(fb[F_EXT], ds, tab, ws, 1));
     if (basis) MDP_LAUNCH(F_RES, k_residual<false, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
     else MDP_LAUNCH(F_RES, k_residual<true, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
     if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
     else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
-    if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
-    else MDP_LAUNCH(F_TRI, k_tri<true, true><<<grid1(fb[F_TRI].total_blocks), b4, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+    if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true><<<grid1(fb[F_TRI].total_blocks), btri, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+    else MDP_LAUNCH(F_TRI, k_tri<true, true><<<grid1(fb[F_TRI].total_blocks), btri, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

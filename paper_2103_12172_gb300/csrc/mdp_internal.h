@@ -80,6 +80,7 @@ struct Batch {
 };
 
 constexpr int FSW = 24;  // doubles per forward-sweep table row
+constexpr int TRI_WARPS = 1;  // warps (modes) per block of the per-mode sweep kernel k_tri
 constexpr int FFT_POINTS = 4096;        // longest transform (2 Nx) of the dense-row FFT kernels (64 KiB)
 constexpr int FFT_BLOCK_POINTS = 1024;  // complex values per block when 2 Nx is shorter: fpb = 1024 / (2 Nx)
 
@@ -195,7 +196,7 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
     case F_FROWS:
       if (d.rows_fft) return 4 * ((ncols + d.fpb - 1) / d.fpb);
       return cb * ((d.Nx / 2 + 7) / 8);
-    case F_TRI: return cb * ((d.Nq + 3) / 4);
+    case F_TRI: return cb * ((d.Nq + TRI_WARPS - 1) / TRI_WARPS);
     case F_IROWS:
       if (d.rows_fft) return 4 * ((ncols + d.fpb - 1) / d.fpb);
       return cb * (((d.xsym ? 4 * (d.Ph + 1) : 4 * (d.Px + 2)) + 7) / 8);
