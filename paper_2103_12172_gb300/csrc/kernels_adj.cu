@@ -108,14 +108,39 @@ __global__ void __launch_bounds__(256) k_adj_rows(Batch bt, const SubDesc *subs,
   }
 }
 
+// The cotangent at the 4 gamma columns (mlo-1, mlo, mhi, mhi+1) of the middle rows nlo+1 ..
+// nhi-1, gathered column-fastest into the r buffer ([4 (n - nlo - 1) + s][b], complex; r is free
+// between the forward recompute and k_adj_ring_rows) for the sine transform in k_adj_tri. On an
+// x-symmetric subdomain (mhi + 1 = Nx - (mlo - 1), mhi = Nx - mlo, so sin(pi q m'/Nx) =
+// (-1)^(q+1) sin(pi q m/Nx) for the mirrored column m') the slots hold the pairs
+// (c0 + c3, c0 - c3, c1 + c2, c1 - c2), and a mode needs two of them.
+__global__ void __launch_bounds__(256) k_adj_cols(Batch bt, const SubDesc *subs, double *ws, const double2 *cot) {
+  Item it; int local;
+  locate(bt, blockIdx.x, it, local);
+  const SubDesc &d = subs[it.sub];
+  const int cb = (it.ncols + 31) >> 5;
+  const int b = (local % cb) * 32 + threadIdx.x;
+  const int t = (local / cb) * 8 + threadIdx.y;
+  if (b >= it.ncols || t >= d.Py - 2) return;
+  const double2 *c = cot + it.io_off + (long long)b * d.G + 2 * (d.Px + 2) + 4 * t;
+  const cplx c0 = cmk(c[0].x, c[0].y), c1 = cmk(c[1].x, c[1].y), c2 = cmk(c[2].x, c[2].y), c3 = cmk(c[3].x, c[3].y);
+  cplx v[4] = {c0, c1, c2, c3};
+  if (d.xsym) {
+    v[0] = cadd(c0, c3); v[1] = csub(c0, c3);
+    v[2] = cadd(c1, c2); v[3] = csub(c1, c2);
+  }
+  double *r = ws + it.r_off;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) st2(r + 2 * ((4LL * t + s) * it.ncols + b), v[s]);
+}
+
 // muhat = T_q^{-H} yhat for one (mode, column): U^H forward substitution (rows below the
 // gamma band carry zero), then the transposed eliminations and row swaps from the top down to
 // row 0. With DK the term Re <muhat, T_q' uhat> is accumulated as rows become final; muhat is
 // kept on the ring rows nlo..nhi (a buffer, rows in matrix numbering).
 template <bool CF, bool DK>
 __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d, const double *tab,
-                                               const uint8_t *pivtab, double *ws, const double2 *cot, bool rec,
-                                               int b, int q) {
+                                               const uint8_t *pivtab, double *ws, bool rec, int b, int q) {
   constexpr int FW = CF ? 8 : 4;
   const double *F = tab + d.fact_off + (long long)(q - 1) * d.Nt * FW;
   const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * d.Nt;
@@ -124,22 +149,30 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
   const double *S = tab + d.sin_off;
   const double sg0 = S[(q * (d.mlo - 1)) % N2], sg1 = S[(q * d.mlo) % N2];
   const double sg2 = S[(q * d.mhi) % N2], sg3 = S[(q * (d.mhi + 1)) % N2];
-  const int W = d.Px + 2, nc = it.ncols;
-  const double2 *ct = cot + it.io_off + (long long)b * d.G;
+  const int nc = it.ncols;
   const double *gr = ws + it.gr_off;
   double *a = ws + it.a_off;
   const long long abase = (long long)(q - 1) * d.Nt * nc + b;
   auto aptr = [&](int i) { return a + 2 * (abase + (long long)i * nc); };
+  // middle rows: the cotangent at the 4 gamma columns as gathered by k_adj_cols (column-fastest;
+  // (sum, difference) pairs on x-symmetric subdomains: odd q takes the sums, even q the differences)
+  const double *cc = ws + it.r_off;
+  const int par = (q & 1) ? 0 : 1;
   auto rhs = [&](int n) -> cplx {
     if (n < d.nlo - 1 || n > d.nhi + 1) return cmk(0.0, 0.0);
     const int rr = n == d.nlo - 1 ? 0 : n == d.nlo ? 1 : n == d.nhi ? 2 : n == d.nhi + 1 ? 3 : -1;
     if (rr >= 0) return ld2(gr + 2 * (((long long)rr * d.Nq + (q - 1)) * nc + b));
-    const int g0 = 2 * W + 4 * (n - d.nlo - 1);
+    const long long s0 = 4LL * (n - d.nlo - 1);
     cplx v = (rec && n == d.nrec) ? ld2(gr + 2 * ((4LL * d.Nq + (q - 1)) * nc + b)) : cmk(0.0, 0.0);
-    v = caxpy(sg0, cmk(ct[g0].x, ct[g0].y), v);
-    v = caxpy(sg1, cmk(ct[g0 + 1].x, ct[g0 + 1].y), v);
-    v = caxpy(sg2, cmk(ct[g0 + 2].x, ct[g0 + 2].y), v);
-    v = caxpy(sg3, cmk(ct[g0 + 3].x, ct[g0 + 3].y), v);
+    if (d.xsym) {
+      v = caxpy(sg0, ld2(cc + 2 * ((s0 + par) * nc + b)), v);
+      v = caxpy(sg1, ld2(cc + 2 * ((s0 + 2 + par) * nc + b)), v);
+    } else {
+      v = caxpy(sg0, ld2(cc + 2 * (s0 * nc + b)), v);
+      v = caxpy(sg1, ld2(cc + 2 * ((s0 + 1) * nc + b)), v);
+      v = caxpy(sg2, ld2(cc + 2 * ((s0 + 2) * nc + b)), v);
+      v = caxpy(sg3, ld2(cc + 2 * ((s0 + 3) * nc + b)), v);
+    }
     return v;
   };
   // Factor rows [rlo, rhi) of a complex mode are exactly real (plan: factor_mode); there the
@@ -232,7 +265,7 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
 
 template <bool DK>
 __global__ void __launch_bounds__(128, 7) k_adj_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
-                                                 double *ws, const double2 *cot, int has_rec) {
+                                                 double *ws, int has_rec) {
   __shared__ double sh[128];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
@@ -242,8 +275,8 @@ __global__ void __launch_bounds__(128, 7) k_adj_tri(Batch bt, const SubDesc *sub
   const int q = (local / cb) * 4 + threadIdx.y + 1;
   double dk = 0.0;
   if (b < it.ncols && q <= d.Nq)
-    dk = d.cplx ? adj_tri_body<true, DK>(it, d, tab, pivtab, ws, cot, has_rec && d.nrec >= 0, b, q)
-                : adj_tri_body<false, DK>(it, d, tab, pivtab, ws, cot, has_rec && d.nrec >= 0, b, q);
+    dk = d.cplx ? adj_tri_body<true, DK>(it, d, tab, pivtab, ws, has_rec && d.nrec >= 0, b, q)
+                : adj_tri_body<false, DK>(it, d, tab, pivtab, ws, has_rec && d.nrec >= 0, b, q);
   if (DK) {
     const double s = block_sum<128>(dk * (2.0 / d.Nx), sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) ws[it.red_off + local] = s;   // slot base 0: k_adj_tri
@@ -515,8 +548,9 @@ cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, cons
     }                                             \
   } while (0)
   ADJ_LAUNCH(F_AFWD, k_adj_rows<<<g1(fb[F_AFWD].total_blocks), b8, p->fft_smem, st>>>(fb[F_AFWD], ds, tab, ws, cot, cot_rec));
-  if (dk) ADJ_LAUNCH(F_ATRI, k_adj_tri<true><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot, cot_rec ? 1 : 0));
-  else ADJ_LAUNCH(F_ATRI, k_adj_tri<false><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot, cot_rec ? 1 : 0));
+  ADJ_LAUNCH(F_ACOLS, k_adj_cols<<<g1(fb[F_ACOLS].total_blocks), b8, 0, st>>>(fb[F_ACOLS], ds, ws, cot));
+  if (dk) ADJ_LAUNCH(F_ATRI, k_adj_tri<true><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot_rec ? 1 : 0));
+  else ADJ_LAUNCH(F_ATRI, k_adj_tri<false><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot_rec ? 1 : 0));
   if (dk) {
     ADJ_LAUNCH(F_ARING, k_adj_ring_rows<true><<<g1(fb[F_ARING].total_blocks), b8, p->fft_smem, st>>>(fb[F_ARING], ds, tab, ws));
     ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<true><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));

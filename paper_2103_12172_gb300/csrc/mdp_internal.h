@@ -184,7 +184,7 @@ enum Sched { S_PROJ = 0, S_GRAD = 1, S_BASIS = 2 };
 
 // kernel families (each has its own block decomposition of an item); F_A* are the adjoint's
 enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_ARINGC, F_AGAM, F_IREC,
-           NFAM };
+           F_ACOLS, NFAM };
 
 // Blocks of kernel family f for an item of ncols columns: 32 columns (x) times BY tasks (y).
 // The same function numbers the blocks on the host (prefix sums) and in the kernels.
@@ -211,6 +211,7 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
     case F_ARINGC: return cb * ((d.Py - 4 + 7) / 8);
     case F_AGAM: return cb * ((d.G + 7) / 8);
     case F_IREC: return d.nrec < 0 ? 0 : cb * (((d.xsym ? d.Ph - 1 : d.Px - 2) + 7) / 8);
+    case F_ACOLS: return cb * ((d.Py - 2 + 7) / 8);
     default: return 0;
   }
 }

@@ -23,7 +23,7 @@ static const double kSingularTol = 1e-13; // pivot below this x max|T| -> singul
 const char *fam_name(int f) {
   static const char *names[NFAM] = {"k_extend", "k_residual", "k_fwd_rows", "k_tri", "k_inv_rows", "k_inv_cols",
                                     "k_adj_rows", "k_adj_tri", "k_adj_ring_rows", "k_adj_ring_cols", "k_adj_gamma",
-                                    "k_inv_rec"};
+                                    "k_inv_rec", "k_adj_cols"};
   return (f >= 0 && f < NFAM) ? names[f] : "?";
 }
 
