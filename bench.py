@@ -149,19 +149,21 @@ def kernel_flops(plan, items):
             inv = 2
         add("k_tri", nc * Nq * tri)
         add("k_inv_cols", nc * (Py - 2) * Nq * (2 if xs else 4) * inv)
-        if (Nx & (Nx - 1)) == 0 and 8 <= Nx <= 2048:
-            # radix-2 FFT of length L = 2 Nx per dense row: two multiply-free stages (4 L flops),
-            # log2(L) - 2 stages of L/2 butterflies (complex multiply 6 + two complex adds 4)
-            L = 2 * Nx
-            lg = L.bit_length() - 1
-            add("k_inv_rows", nc * 4 * (4 * L + 5 * L * (lg - 2) + 2 * (Px + 2)))
+        fft_rows = (Nx & (Nx - 1)) == 0 and 8 <= Nx <= 2048
+        if fft_rows:
+            # DST-I of a dense row by one complex FFT of length Nx: the twist of the input pairs
+            # (two complex adds and four FMA per pair, 6 Nx), two multiply-free stages (4 Nx),
+            # log2(Nx) - 2 stages of Nx/2 butterflies (complex multiply 6 + two complex adds 4),
+            # the even outputs and the odd terms (4 Nx) and the segmented scan over Nx/2 terms
+            # (Nx flops per step, log2(min(32, Nx/2)) steps)
+            lg = Nx.bit_length() - 1
+            dst = 6 * Nx + 4 * Nx + 5 * Nx * (lg - 2) + 4 * Nx + Nx * min(5, lg - 1)
+            add("k_inv_rows", nc * 4 * (dst + 2 * (Px + 2)))
         else:
             add("k_inv_rows", nc * 4 * ((Px // 2 + 2) if xs else (Px + 2)) * Nq * inv)
-        if (Nx & (Nx - 1)) == 0 and 8 <= Nx <= 2048:
-            # one length-2Nx FFT per row pair of a column (real data packed as re/im)
-            L = 2 * Nx
-            lg = L.bit_length() - 1
-            add("k_fwd_rows", nc * 2 * (4 * L + 5 * L * (lg - 2)))
+        if fft_rows:
+            # one DST-I per row pair of a column (real data packed as re/im)
+            add("k_fwd_rows", nc * 2 * dst)
         else:
             add("k_fwd_rows", nc * (Nx // 2) * 4 * ((Px + 1) // 2 if xs else Px) * 2)
         add("k_residual", nc * R * 9 * 2)

@@ -159,70 +159,83 @@ __global__ void __launch_bounds__(256) k_residual(Batch bt, const SubDesc *subs,
 // ---------------------------------------------------------------- k_fwd_rows
 // ghat(q, row) = sum_m sin(pi q m / Nx) r(m, row) for the 4 dense ring rows.
 //
-// FFT form (Nx a power of 2): with the odd extension x~(m) = r(m), x~(2Nx - m) = -r(m), the
-// length-2Nx DFT is V[q] = -2i ghat(q). Real ring data (basis columns) pack two rows of the same
-// column per transform, x~ = r_a + i r_b (rows nlo, nlo+1 and nhi-1, nhi): then
-// V = 2 ghat_b - 2i ghat_a, so ghat_a = -Im V / 2 and ghat_b = Re V / 2, and a column's result
-// does not depend on its neighbours. One block: one ring row (or row pair) and fpb columns.
+// FFT form (Nx a power of 2): a DST-I by one complex FFT of length Nx (dst1_post). Real ring
+// data (basis columns) pack two rows of the same column per transform, x = r_a + i r_b (rows
+// nlo, nlo+1 and nhi-1, nhi): the transform is linear with real coefficients, so ghat_a = Re F
+// and ghat_b = Im F, and a column's result does not depend on its neighbours. One block: one
+// ring row (or row pair) and fpb columns.
 //
 // Direct form: a thread handles the mode pair (q, Nx - q): sin(pi (Nx-q) m/Nx) =
 // (-1)^(m+1) sin(pi q m/Nx), so the odd-m and even-m partial sums give both modes.
 template <bool CIN>
 __device__ __forceinline__ void fwd_rows_fft(const Item &it, const SubDesc &d, const double *tab, double *ws,
                                              int local, double2 *sm) {
+  __shared__ double2 tot[32];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
   const int rr = local & 3, cblk = local >> 2;
   if (!CIN && (rr & 1)) return;                        // real data: rows rr, rr + 1 in one block
   const int b0 = cblk * d.fpb, nf = min(d.fpb, it.ncols - b0);
-  const int Nx = d.Nx, L = 2 * Nx;
+  const int N = d.Nx, H = N / 2;
   int lg = 0;
-  while ((1 << lg) < L) ++lg;
+  while ((1 << lg) < N) ++lg;
+  const double *sn = tab + d.sin_off;
   const double *r = ws + it.r_off;
   const long long nc = it.ncols;
   const int P = d.Px, Mr = 4 * (d.Py - 4);
-  // r(m) of ring row `row`, column b (m in [mlo, mhi]); x-centred subdomains store the pairs
-  // (r(m) + r(Nx-m), r(m) - r(Nx-m)) for m <= Nx/2 (at m = Nx/2 both slots hold r)
-  auto rval = [&](int row, int m, int b) -> cplx {
+  auto rv = [&](long long slot, int b) -> cplx { return CIN ? ld2(r + 2 * (slot * nc + b)) : cmk(r[slot * nc + b], 0.0); };
+  // (x_j + x_{N-j}, x_j - x_{N-j}) of ring row `row`, column b, j = 1 .. N/2: x-centred
+  // subdomains store exactly these pairs for j in [mlo, N/2] (at j = N/2 both slots hold r)
+  auto pm = [&](int row, int j, int b, cplx &p, cplx &m) {
     if (d.xsym) {
-      const int mm = m <= Nx / 2 ? m : Nx - m;
-      const long long slot = (long long)row * 2 * d.Ph + 2 * (mm - d.mlo);
-      const cplx p0 = CIN ? ld2(r + 2 * (slot * nc + b)) : cmk(r[slot * nc + b], 0.0);
-      if (2 * mm == Nx) return p0;
-      const cplx p1 = CIN ? ld2(r + 2 * ((slot + 1) * nc + b)) : cmk(r[(slot + 1) * nc + b], 0.0);
-      const cplx h = m <= Nx / 2 ? cadd(p0, p1) : csub(p0, p1);
-      return cmk(0.5 * h.re, 0.5 * h.im);
+      if (j < d.mlo) { p = m = cmk(0.0, 0.0); return; }
+      const long long slot = (long long)row * 2 * d.Ph + 2 * (j - d.mlo);
+      p = rv(slot, b);
+      m = 2 * j == N ? cmk(0.0, 0.0) : rv(slot + 1, b);
+      if (2 * j == N) p = cmk(2.0 * p.re, 2.0 * p.im);
+      return;
     }
     const int rb = row == 0 ? 0 : row == 1 ? P : row == 2 ? 2 * P + Mr : 3 * P + Mr;
-    const long long slot = rb + (m - d.mlo);
-    return CIN ? ld2(r + 2 * (slot * nc + b)) : cmk(r[slot * nc + b], 0.0);
+    const cplx xa = (j >= d.mlo && j <= d.mhi) ? rv(rb + (j - d.mlo), b) : cmk(0.0, 0.0);
+    const cplx xb = (N - j >= d.mlo && N - j <= d.mhi) ? rv(rb + (N - j - d.mlo), b) : cmk(0.0, 0.0);
+    p = cadd(xa, xb);
+    m = 2 * j == N ? cmk(0.0, 0.0) : csub(xa, xb);
   };
-  for (int idx = tid; idx < d.fpb * L; idx += nt) {
-    const int f = idx >> lg, n = idx & (L - 1);
-    double2 v = make_double2(0.0, 0.0);
-    const int m = n <= Nx ? n : L - n;
-    const double sgn = n <= Nx ? 1.0 : -1.0;
-    if (f < nf && m >= d.mlo && m <= d.mhi) {
+  // the twisted sequence y, bit-reversed, for the pairs (j, N - j)
+  for (int idx = tid; idx < d.fpb * (H + 1); idx += nt) {
+    const int f = idx / (H + 1), j = idx - f * (H + 1);
+    double2 *S = sm + (long long)f * N;
+    if (j == 0) { S[0] = make_double2(0.0, 0.0); continue; }
+    cplx p = cmk(0.0, 0.0), m = cmk(0.0, 0.0);
+    if (f < nf) {
       if (CIN) {
-        const cplx x = rval(rr, m, b0 + f);
-        v = make_double2(sgn * x.re, sgn * x.im);
-      } else {
-        v = make_double2(sgn * rval(rr, m, b0 + f).re, sgn * rval(rr + 1, m, b0 + f).re);
+        pm(rr, j, b0 + f, p, m);
+      } else {   // rows rr (real part) and rr + 1 (imaginary part)
+        cplx p1, m1;
+        pm(rr, j, b0 + f, p, m);
+        pm(rr + 1, j, b0 + f, p1, m1);
+        p = cmk(p.re, p1.re);
+        m = cmk(m.re, m1.re);
       }
     }
-    sm[(f << lg) + brev_lg(n, lg)] = v;
+    if (2 * j == N) { S[brev_lg(j, lg)] = make_double2(p.re, p.im); continue; }   // y_{N/2} = 2 x_{N/2}
+    const double sj = sn[j];
+    S[brev_lg(j, lg)] = make_double2(fma(sj, p.re, 0.5 * m.re), fma(sj, p.im, 0.5 * m.im));
+    S[brev_lg(N - j, lg)] = make_double2(fma(sj, p.re, -0.5 * m.re), fma(sj, p.im, -0.5 * m.im));
   }
   __syncthreads();
-  fft_r2_stages(sm, d.fpb, Nx, lg, tab + d.sin_off);
+  fft_r2_stages(sm, d.fpb, N, lg, sn);
+  double2 *F = sm + (long long)d.fpb * N;
+  dst1_post(sm, F, d.fpb, N, tot);
   double *gr = ws + it.gr_off;
   for (int idx = tid; idx < nf * d.Nq; idx += nt) {
     const int f = idx % nf, q = idx / nf + 1;
-    const double2 V = sm[(f << lg) + q];
+    const double2 V = F[(long long)f * N + q];
     const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b0 + f;
     if (CIN) {
-      st2(gr + 2 * o, cmk(-0.5 * V.y, 0.5 * V.x));
+      st2(gr + 2 * o, cmk(V.x, V.y));
     } else {
-      gr[o] = -0.5 * V.y;
-      gr[o + (long long)d.Nq * nc] = 0.5 * V.x;       // row rr + 1
+      gr[o] = V.x;
+      gr[o + (long long)d.Nq * nc] = V.y;       // row rr + 1
     }
   }
 }
@@ -758,47 +771,57 @@ __device__ __forceinline__ void inv_rows_body(const Item &it, const SubDesc &d, 
   if (d.xsym && d.Nx - m != m) write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b, gidx(d.Nx - m), csub(e, o));
 }
 
-// The same rows by FFT: u(m) = (2/Nx) sum_q yhat(q) sin(pi q m/Nx) = (i/Nx) V[m], where V is the
-// length-2Nx DFT of the odd extension x~ = (0, yhat_1 .. yhat_{Nx-1}, 0, -yhat_{Nx-1} .. -yhat_1)
-// (V[m] = -2i sum_q yhat_q sin(pi q m/Nx)). Radix-2 decimation in time in shared memory: inputs
-// stored bit-reversed, log2(2Nx) butterfly stages, output in natural order. One block: one
-// gamma row and fpb = 4096/(2Nx) columns (64 KiB of complex values). Twiddles e^{-i pi j/Nx}
-// come from the sine table (cos(pi j/Nx) = sin(pi (j + Nx/2)/Nx)).
+// The same rows by FFT: u(m) = (2/Nx) F_m with F the DST-I of yhat (dst1_post: one complex FFT
+// of length Nx of the twisted sequence, radix-2 decimation in time in shared memory, inputs
+// stored bit-reversed). One block: one gamma row and fpb = 1024/(2Nx) columns (or one column
+// when Nx >= 512); the transforms take the first fpb Nx values of shared memory, the outputs the
+// next fpb Nx.
 template <bool CD, bool CIN>
 __device__ __forceinline__ void inv_rows_fft_body(const Item &it, const SubDesc &d, const double *tab,
                                                   const double *ws, const double2 *xi_user, double2 *out, int kind,
                                                   int local, double2 *sm) {
+  __shared__ double2 tot[32];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
   const int grow = local & 3, cblk = local >> 2;
   const int b0 = cblk * d.fpb, nf = min(d.fpb, it.ncols - b0);
-  const int L = 2 * d.Nx, Nx = d.Nx;
+  const int N = d.Nx, H = N / 2;
   int lg = 0;
-  while ((1 << lg) < L) ++lg;
+  while ((1 << lg) < N) ++lg;
+  const double *sn = tab + d.sin_off;
   const int n = grow == 0 ? d.nlo - 1 : grow == 1 ? d.nlo : grow == 2 ? d.nhi : d.nhi + 1;
   const int yrow = n - (d.nlo - 1);
   const double *y = ws + it.y_off;
   const long long qstride = (long long)d.NYf * it.ncols;
-  auto brev = [&](int j) { return brev_lg(j, lg); };
-  // load the odd extension, bit-reversed
-  for (int idx = tid; idx < d.fpb * (Nx + 1); idx += nt) {
-    const int f = idx % d.fpb, q = idx / d.fpb;       // q = 0 .. Nx
-    double2 v = make_double2(0.0, 0.0);
-    if (q >= 1 && q <= Nx - 1 && f < nf) {
-      const long long o = (long long)(q - 1) * qstride + (long long)yrow * it.ncols + b0 + f;
-      v = CD ? *reinterpret_cast<const double2 *>(y + 2 * o) : make_double2(y[o], 0.0);
+  auto yv = [&](int q, int f) -> cplx {   // yhat(q) of column b0 + f, q = 1 .. N-1
+    const long long o = (long long)(q - 1) * qstride + (long long)yrow * it.ncols + b0 + f;
+    return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
+  };
+  // the twisted sequence, bit-reversed, for the pairs (q, N - q); the column is fastest
+  for (int idx = tid; idx < d.fpb * (H + 1); idx += nt) {
+    const int f = idx % d.fpb, j = idx / d.fpb;
+    double2 *S = sm + (long long)f * N;
+    if (j == 0) { S[0] = make_double2(0.0, 0.0); continue; }
+    cplx xa = cmk(0.0, 0.0), xb = cmk(0.0, 0.0);
+    if (f < nf) {
+      xa = yv(j, f);
+      if (2 * j != N) xb = yv(N - j, f);
     }
-    double2 *S = sm + (long long)f * L;
-    S[brev(q)] = v;
-    if (q >= 1 && q <= Nx - 1) S[brev(L - q)] = make_double2(-v.x, -v.y);
+    if (2 * j == N) { S[brev_lg(j, lg)] = make_double2(2.0 * xa.re, 2.0 * xa.im); continue; }
+    cplx ya, yb;
+    dst1_twist(xa, xb, sn[j], ya, yb);
+    S[brev_lg(j, lg)] = make_double2(ya.re, ya.im);
+    S[brev_lg(N - j, lg)] = make_double2(yb.re, yb.im);
   }
   __syncthreads();
-  fft_r2_stages(sm, d.fpb, Nx, lg, tab + d.sin_off);
+  fft_r2_stages(sm, d.fpb, N, lg, sn);
+  double2 *F = sm + (long long)d.fpb * N;
+  dst1_post(sm, F, d.fpb, N, tot);
   const int W = d.Px + 2, Mr = d.Py - 2;
-  const double sc = 1.0 / Nx;
+  const double sc = 2.0 / N;
   for (int idx = tid; idx < nf * W; idx += nt) {
     const int f = idx / W, dm = idx % W, m = d.mlo - 1 + dm;
-    const double2 V = sm[(long long)f * L + m];
-    const cplx u = cmk(-V.y * sc, V.x * sc);   // (i/Nx) V
+    const double2 V = F[(long long)f * N + m];
+    const cplx u = cmk(sc * V.x, sc * V.y);
     const int g = grow <= 1 ? grow * W + dm : 2 * W + 4 * Mr + (grow - 2) * W + dm;
     write_out<CD, CIN>(d, it, ws, tab, xi_user, out, kind, b0 + f, g, u);
   }

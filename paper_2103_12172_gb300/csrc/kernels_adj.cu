@@ -21,18 +21,19 @@ static constexpr int FFT_SMEM_ADJ = FFT_POINTS * 16;  // bytes of dynamic shared
 // yhat(q, row) = sum_m c(m) sin(pi q m / Nx) of the 4 full gamma rows of the cotangent (and
 // the receiver row): by FFT where the plan allows it (Nx a power of 2), else a direct sum.
 //
-// FFT form: with the odd extension x~(m) = c(m), x~(2Nx - m) = -c(m) (zero at 0 and Nx), the
-// length-2Nx DFT is V[q] = -2i sum_m c(m) sin(pi q m / Nx), so yhat(q) = (i/2) V[q]. One block:
-// one row and fpb columns.
+// FFT form: a DST-I by one complex FFT of length Nx (dst1_post). One block: one row and fpb
+// columns.
 __device__ __forceinline__ void adj_rows_fft(const Item &it, const SubDesc &d, const double *tab, double *ws,
                                              const double2 *cot, const double2 *cot_rec, int local, double2 *sm) {
+  __shared__ double2 tot[32];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
   const int rr = local % 5, cblk = local / 5;
   if (rr == 4 && !(cot_rec && d.nrec >= 0)) return;   // uniform over the block
   const int b0 = cblk * d.fpb, nf = min(d.fpb, it.ncols - b0);
-  const int Nx = d.Nx, L = 2 * Nx;
+  const int N = d.Nx, H = N / 2;
   int lg = 0;
-  while ((1 << lg) < L) ++lg;
+  while ((1 << lg) < N) ++lg;
+  const double *sn = tab + d.sin_off;
   const int W = d.Px + 2, M4 = 4 * (d.Py - 2);
   // the row's values c(m) for m in [m0, m0 + cnt), column f at src(f) + (m - m0)
   const int m0 = rr == 4 ? d.mlo + 1 : d.mlo - 1, cnt = rr == 4 ? d.Px - 2 : W;
@@ -41,22 +42,36 @@ __device__ __forceinline__ void adj_rows_fft(const Item &it, const SubDesc &d, c
     return rr == 4 ? cot_rec + d.rec_off + (long long)(it.col0 + b0 + f) * (d.Px - 2)
                    : cot + it.io_off + (long long)(b0 + f) * d.G + g0;
   };
-  for (int idx = tid; idx < d.fpb * L; idx += nt) {
-    const int f = idx >> lg, n = idx & (L - 1);
-    double2 v = make_double2(0.0, 0.0);
+  auto cv = [&](int f, int m) -> cplx {
+    if (m < m0 || m >= m0 + cnt) return cmk(0.0, 0.0);
+    const double2 v = src(f)[m - m0];
+    return cmk(v.x, v.y);
+  };
+  // the twisted sequence, bit-reversed, for the pairs (m, N - m)
+  for (int idx = tid; idx < d.fpb * (H + 1); idx += nt) {
+    const int f = idx / (H + 1), j = idx - f * (H + 1);
+    double2 *S = sm + (long long)f * N;
+    if (j == 0) { S[0] = make_double2(0.0, 0.0); continue; }
+    cplx xa = cmk(0.0, 0.0), xb = cmk(0.0, 0.0);
     if (f < nf) {
-      if (n >= m0 && n < m0 + cnt) v = src(f)[n - m0];
-      else if (L - n >= m0 && L - n < m0 + cnt) { const double2 w = src(f)[L - n - m0]; v = make_double2(-w.x, -w.y); }
+      xa = cv(f, j);
+      if (2 * j != N) xb = cv(f, N - j);
     }
-    sm[(f << lg) + brev_lg(n, lg)] = v;
+    if (2 * j == N) { S[brev_lg(j, lg)] = make_double2(2.0 * xa.re, 2.0 * xa.im); continue; }
+    cplx ya, yb;
+    dst1_twist(xa, xb, sn[j], ya, yb);
+    S[brev_lg(j, lg)] = make_double2(ya.re, ya.im);
+    S[brev_lg(N - j, lg)] = make_double2(yb.re, yb.im);
   }
   __syncthreads();
-  fft_r2_stages(sm, d.fpb, Nx, lg, tab + d.sin_off);
+  fft_r2_stages(sm, d.fpb, N, lg, sn);
+  double2 *F = sm + (long long)d.fpb * N;
+  dst1_post(sm, F, d.fpb, N, tot);
   double *gr = ws + it.gr_off;
   for (int idx = tid; idx < nf * d.Nq; idx += nt) {
     const int f = idx % nf, q = idx / nf + 1;
-    const double2 V = sm[(f << lg) + q];
-    st2(gr + 2 * (((long long)rr * d.Nq + (q - 1)) * it.ncols + b0 + f), cmk(-0.5 * V.y, 0.5 * V.x));
+    const double2 V = F[(long long)f * N + q];
+    st2(gr + 2 * (((long long)rr * d.Nq + (q - 1)) * it.ncols + b0 + f), cmk(V.x, V.y));
   }
 }
 
@@ -284,41 +299,54 @@ __global__ void __launch_bounds__(128, 7) k_adj_tri(Batch bt, const SubDesc *sub
 }
 
 // mu on the 4 full ring rows (into the r buffer, complex [R][b]); DK: -Re <mu, s>.
-// FFT form (as for the forward path's gamma rows): mu(m) = (2/Nx) sum_q muhat_q sin(pi q m/Nx)
-// = (i/Nx) V[m], V the length-2Nx DFT of the odd extension of muhat. One block: one ring row and
-// fpb columns.
+// FFT form (as for the forward path's gamma rows): mu(m) = (2/Nx) F_m with F the DST-I of
+// muhat (dst1_post). One block: one ring row and fpb columns.
 template <bool DK>
 __device__ __forceinline__ double adj_ring_rows_fft(const Item &it, const SubDesc &d, const double *tab, double *ws,
                                                     int local, double2 *sm) {
+  __shared__ double2 tot[32];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
   const int rr = local & 3, cblk = local >> 2;
   const int b0 = cblk * d.fpb, nf = min(d.fpb, it.ncols - b0);
-  const int Nx = d.Nx, L = 2 * Nx;
+  const int N = d.Nx, H = N / 2;
   int lg = 0;
-  while ((1 << lg) < L) ++lg;
+  while ((1 << lg) < N) ++lg;
+  const double *sn = tab + d.sin_off;
   const int P = d.Px, Mr = 4 * (d.Py - 4);
   const int n = rr == 0 ? d.nlo : rr == 1 ? d.nlo + 1 : rr == 2 ? d.nhi - 1 : d.nhi;
   const int j = n - d.nfirst;
   const double *a = ws + it.a_off;
   const long long qstride = (long long)d.Nt * it.ncols;
-  for (int idx = tid; idx < d.fpb * (Nx + 1); idx += nt) {
-    const int f = idx % d.fpb, q = idx / d.fpb;   // q = 0 .. Nx
-    double2 v = make_double2(0.0, 0.0);
-    if (q >= 1 && q <= Nx - 1 && f < nf)
-      v = *reinterpret_cast<const double2 *>(a + 2 * ((long long)(q - 1) * qstride + (long long)j * it.ncols + b0 + f));
-    double2 *S = sm + (f << lg);
-    S[brev_lg(q, lg)] = v;
-    if (q >= 1 && q <= Nx - 1) S[brev_lg(L - q, lg)] = make_double2(-v.x, -v.y);
+  auto mv = [&](int q, int f) -> cplx {   // muhat(q) of column b0 + f, q = 1 .. N-1
+    return ld2(a + 2 * ((long long)(q - 1) * qstride + (long long)j * it.ncols + b0 + f));
+  };
+  // the twisted sequence, bit-reversed, for the pairs (q, N - q); the column is fastest
+  for (int idx = tid; idx < d.fpb * (H + 1); idx += nt) {
+    const int f = idx % d.fpb, q = idx / d.fpb;
+    double2 *S = sm + (long long)f * N;
+    if (q == 0) { S[0] = make_double2(0.0, 0.0); continue; }
+    cplx xa = cmk(0.0, 0.0), xb = cmk(0.0, 0.0);
+    if (f < nf) {
+      xa = mv(q, f);
+      if (2 * q != N) xb = mv(N - q, f);
+    }
+    if (2 * q == N) { S[brev_lg(q, lg)] = make_double2(2.0 * xa.re, 2.0 * xa.im); continue; }
+    cplx ya, yb;
+    dst1_twist(xa, xb, sn[q], ya, yb);
+    S[brev_lg(q, lg)] = make_double2(ya.re, ya.im);
+    S[brev_lg(N - q, lg)] = make_double2(yb.re, yb.im);
   }
   __syncthreads();
-  fft_r2_stages(sm, d.fpb, Nx, lg, tab + d.sin_off);
+  fft_r2_stages(sm, d.fpb, N, lg, sn);
+  double2 *F = sm + (long long)d.fpb * N;
+  dst1_post(sm, F, d.fpb, N, tot);
   const int rb = rr == 0 ? 0 : rr == 1 ? P : rr == 2 ? 2 * P + Mr : 3 * P + Mr;
-  const double sc = 1.0 / Nx;
+  const double sc = 2.0 / N;
   double dk = 0.0;
   for (int idx = tid; idx < nf * P; idx += nt) {
     const int f = idx % nf, dm = idx / nf;
-    const double2 V = sm[(f << lg) + d.mlo + dm];
-    const cplx acc = cmk(-V.y * sc, V.x * sc);
+    const double2 V = F[(long long)f * N + d.mlo + dm];
+    const cplx acc = cmk(sc * V.x, sc * V.y);
     const long long o = (long long)(rb + dm) * it.ncols + b0 + f;
     st2(ws + it.r_off + 2 * o, acc);
     if (DK) {

@@ -132,7 +132,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 __device__ __forceinline__ int brev_lg(int j, int lg) { return (int)(__brev((unsigned)j) >> (32 - lg)); }
 
 // Radix-2 decimation-in-time FFT with the forward sign, V[k] = sum_n x[n] e^{-2 pi i n k / L},
-// of nf sequences of length L = 2 Nx = 2^lg (lg >= 2) stored one after another in shared memory
+// of nf sequences of length L = 2^lg (4 <= L <= 2 Nx) stored one after another in shared memory
 // with their inputs in bit-reversed order; the output is in natural order. Twiddles come from
 // the sine table sn[j] = sin(pi j / Nx), j < 2 Nx (cos(pi j / Nx) = sn[j + Nx/2]). The first
 // two stages (twiddles 1 and -i) take no multiplies. Called by every thread of the block.
@@ -169,6 +169,61 @@ __device__ __forceinline__ void fft_r2_stages(double2 *sm, int nf, int Nx, int l
     }
     __syncthreads();
   }
+}
+
+
+// ---------------------------------------------------------------- DST-I by a length-N FFT
+// F_q = sum_{j=1}^{N-1} x_j sin(pi q j / N), q = 1 .. N-1, for complex x and N = 2^lg, from one
+// complex FFT of length N (the odd extension would take one of length 2N). With s_j = sin(pi j/N)
+// the twisted sequence y_0 = 0, y_j = s_j (x_j + x_{N-j}) + (x_j - x_{N-j}) / 2 has the DFT
+// C_k = sum_j y_j e^{-2 pi i j k / N} with
+//   F_{2k} = (i/2) (C_k - C_{N-k}),   F_1 = C_0 / 2,   F_{2k+1} = F_{2k-1} + (C_k + C_{N-k}) / 2:
+// the part of y symmetric under j -> N - j gives cosine sums, and 2 sin(pi j/N) cos(2 pi j k/N)
+// = sin(pi j (2k+1)/N) - sin(pi j (2k-1)/N) makes them differences of consecutive odd outputs;
+// the antisymmetric part gives the sine sums at the even outputs. The odd outputs are a prefix
+// sum over k (a tree scan: rounding grows like log N).
+
+// y_j and y_{N-j} from the pair xa = x_j, xb = x_{N-j} (j = 1 .. N/2 - 1)
+__device__ __forceinline__ void dst1_twist(cplx xa, cplx xb, double s, cplx &ya, cplx &yb) {
+  const cplx p = cadd(xa, xb), m = csub(xa, xb);
+  ya = cmk(fma(s, p.re, 0.5 * m.re), fma(s, p.im, 0.5 * m.im));
+  yb = cmk(fma(s, p.re, -0.5 * m.re), fma(s, p.im, -0.5 * m.im));
+}
+
+// From C (nseq transforms of length N, stride N) to F[f N + q] = F_q (q = 1 .. N-1; F[f N] is
+// not written). nseq N / 2 must be a multiple of the block size (256 threads: the FFT kernels
+// use nseq = 1024 / (2N), or 1 when N >= 512). tot: shared scratch of nseq N / 64 values.
+// Called by every thread of the block.
+__device__ __forceinline__ void dst1_post(const double2 *C, double2 *F, int nseq, int N, double2 *tot) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  const int H = N >> 1, E = nseq * H, lane = tid & 31;
+  const int W = H < 32 ? H : 32;   // scan segment in a warp: a whole sequence, or 32 of its terms
+  for (int e0 = 0; e0 < E; e0 += nt) {
+    const int e = e0 + tid, f = e / H, k = e - f * H;
+    const double2 *Cf = C + (long long)f * N;
+    double2 *Ff = F + (long long)f * N;
+    const double2 a = Cf[k], c = Cf[k == 0 ? 0 : N - k];
+    if (k > 0) Ff[2 * k] = make_double2(-0.5 * (a.y - c.y), 0.5 * (a.x - c.x));
+    double2 t = k == 0 ? make_double2(0.5 * a.x, 0.5 * a.y) : make_double2(0.5 * (a.x + c.x), 0.5 * (a.y + c.y));
+    for (int off = 1; off < W; off <<= 1) {   // inclusive scan within the segment
+      const double ux = __shfl_up_sync(0xffffffffu, t.x, off, W), uy = __shfl_up_sync(0xffffffffu, t.y, off, W);
+      if ((lane & (W - 1)) >= off) { t.x += ux; t.y += uy; }
+    }
+    Ff[2 * k + 1] = t;
+    if (H > 32 && lane == 31) tot[e >> 5] = t;   // total of this 32-term chunk
+  }
+  if (H <= 32) { __syncthreads(); return; }
+  __syncthreads();
+  for (int e0 = 0; e0 < E; e0 += nt) {   // add the totals of the sequence's earlier chunks
+    const int e = e0 + tid, f = e / H, k = e - f * H;
+    const int c = e >> 5, cfirst = (f * H) >> 5;
+    if (c == cfirst) continue;
+    double sx = 0.0, sy = 0.0;
+    for (int cc = cfirst; cc < c; ++cc) { sx += tot[cc].x; sy += tot[cc].y; }
+    double2 *o = F + (long long)f * N + 2 * k + 1;
+    *o = make_double2(o->x + sx, o->y + sy);
+  }
+  __syncthreads();
 }
 
 }  // namespace mdp

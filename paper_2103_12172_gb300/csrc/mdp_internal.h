@@ -35,7 +35,7 @@ struct SubDesc {
   int R2;           // ring residual slots: R, or 8 Ph + 4 (Py - 4) with xsym
   int nrec;         // receiver row (nlo+1 .. nhi-1) or -1; receivers m = mlo+1 .. mhi-1
   int rows_fft;     // inverse transform of the gamma rows by FFT (Nx a power of 2, 2Nx <= 4096)
-  int fpb;          // FFTs (columns) per block of that kernel: 4096 / (2 Nx)
+  int fpb;          // FFTs (columns) per block of the dense-row kernels: max(1, 1024 / (2 Nx))
   int leader;       // index of the subdomain owning this one's tables (itself unless deduplicated)
   double h, k;
   double x0, x1, y0, y1, ax0, ay0;
