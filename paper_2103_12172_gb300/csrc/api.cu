@@ -4,6 +4,7 @@
 #include "mdp_probe.h"
 
 #include <algorithm>
+#include <array>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -40,8 +41,10 @@ void free_device(mdp_plan *p) {
   for (int k = 0; k < 3; ++k) {
     for (auto x : p->d_items[k]) cudaFree(x);
     for (auto x : p->d_prefix[k]) cudaFree(x);
+    for (auto x : p->d_order[k]) cudaFree(x);
     p->d_items[k].clear();
     p->d_prefix[k].clear();
+    p->d_order[k].clear();
   }
   p->d_subs = nullptr; p->d_tables = nullptr; p->d_piv = nullptr; p->d_ws = nullptr; p->d_status = nullptr;
   if (prev >= 0) cudaSetDevice(prev);
@@ -91,6 +94,23 @@ mdp_status alloc_device(mdp_plan *p) {
               pre[(size_t)f * (n + 1) + i] + blocks_for((Fam)f, p->subs[w.items[i].sub].d, w.items[i].ncols);
       CK(cudaMemcpy(di, w.items.data(), n * sizeof(Item), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(dp, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
+      // k_tri's launch order, longest sweeps first so that the shortest fill the tail: by the
+      // number of rows a sweep covers (larger subdomains first), then by mode group (low modes
+      // first: the propagating modes carry the complex rows), then item, then column block
+      const int *pt = pre.data() + (size_t)F_TRI * (n + 1);
+      std::vector<std::array<int, 4>> keys;
+      keys.reserve(pt[n]);
+      for (int i = 0; i < n; ++i) {
+        const int cb = (w.items[i].ncols + 31) / 32, rows = p->subs[w.items[i].sub].d.NYf;
+        for (int l = 0; l < pt[i + 1] - pt[i]; ++l) keys.push_back({-rows, l / cb, i, l});
+      }
+      std::stable_sort(keys.begin(), keys.end());
+      std::vector<int> order(keys.size());
+      for (size_t b = 0; b < keys.size(); ++b) order[b] = pt[keys[b][2]] + keys[b][3];
+      int *dord = nullptr;
+      if (!al((void **)&dord, order.size() * sizeof(int))) return MDP_ERR_NOMEM;
+      p->d_order[sc].push_back(dord);
+      if (!order.empty()) CK(cudaMemcpy(dord, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
       hpre.push_back(pre);
     }
   }
@@ -104,6 +124,7 @@ void wave_batches(const mdp_plan *p, size_t w, Batch *fb, int sc) {
     std::memset(&b, 0, sizeof b);
     b.items = p->d_items[sc][w];
     b.prefix = p->d_prefix[sc][w] + (size_t)f * (n + 1);
+    b.order = f == F_TRI ? p->d_order[sc][w] : nullptr;
     b.n_items = n;
     b.total_blocks = p->h_prefix[sc][w][(size_t)f * (n + 1) + n];
   }

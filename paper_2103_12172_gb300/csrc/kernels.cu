@@ -700,7 +700,7 @@ template <bool CIN, bool FULL>
 __global__ void __launch_bounds__(32 * TRI_WARPS, 32 / TRI_WARPS) k_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
                                              double *ws) {
   Item it; int local;
-  locate(bt, blockIdx.x, it, local);
+  locate(bt, bt.order ? bt.order[blockIdx.x] : (int)blockIdx.x, it, local);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
