@@ -94,19 +94,23 @@ mdp_status alloc_device(mdp_plan *p) {
               pre[(size_t)f * (n + 1) + i] + blocks_for((Fam)f, p->subs[w.items[i].sub].d, w.items[i].ncols);
       CK(cudaMemcpy(di, w.items.data(), n * sizeof(Item), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(dp, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
-      // k_tri's launch order, longest sweeps first so that the shortest fill the tail: by the
-      // number of rows a sweep covers (larger subdomains first), then by mode group (low modes
-      // first: the propagating modes carry the complex rows), then item, then column block
-      const int *pt = pre.data() + (size_t)F_TRI * (n + 1);
-      std::vector<std::array<int, 4>> keys;
-      keys.reserve(pt[n]);
-      for (int i = 0; i < n; ++i) {
-        const int cb = (w.items[i].ncols + 31) / 32, rows = p->subs[w.items[i].sub].d.NYf;
-        for (int l = 0; l < pt[i + 1] - pt[i]; ++l) keys.push_back({-rows, l / cb, i, l});
+      // launch order of the per-mode sweeps (k_tri, then k_adj_tri), longest first so that the
+      // shortest fill the tail: by the number of rows a sweep covers (larger subdomains first),
+      // then by mode group (low modes first: the propagating modes carry the complex rows), then
+      // item, then column block
+      std::vector<int> order;
+      for (const Fam f : {F_TRI, F_ATRI}) {
+        const int *pt = pre.data() + (size_t)f * (n + 1);
+        std::vector<std::array<int, 4>> keys;
+        keys.reserve(pt[n]);
+        for (int i = 0; i < n; ++i) {
+          const SubDesc &d = p->subs[w.items[i].sub].d;
+          const int cb = (w.items[i].ncols + 31) / 32, rows = f == F_TRI ? d.NYf : d.Nt;
+          for (int l = 0; l < pt[i + 1] - pt[i]; ++l) keys.push_back({-rows, l / cb, i, l});
+        }
+        std::stable_sort(keys.begin(), keys.end());
+        for (const auto &k : keys) order.push_back(pt[k[2]] + k[3]);
       }
-      std::stable_sort(keys.begin(), keys.end());
-      std::vector<int> order(keys.size());
-      for (size_t b = 0; b < keys.size(); ++b) order[b] = pt[keys[b][2]] + keys[b][3];
       int *dord = nullptr;
       if (!al((void **)&dord, order.size() * sizeof(int))) return MDP_ERR_NOMEM;
       p->d_order[sc].push_back(dord);
@@ -124,7 +128,9 @@ void wave_batches(const mdp_plan *p, size_t w, Batch *fb, int sc) {
     std::memset(&b, 0, sizeof b);
     b.items = p->d_items[sc][w];
     b.prefix = p->d_prefix[sc][w] + (size_t)f * (n + 1);
-    b.order = f == F_TRI ? p->d_order[sc][w] : nullptr;
+    b.order = f == F_TRI ? p->d_order[sc][w]
+              : f == F_ATRI ? p->d_order[sc][w] + p->h_prefix[sc][w][(size_t)F_TRI * (n + 1) + n]
+                            : nullptr;
     b.n_items = n;
     b.total_blocks = p->h_prefix[sc][w][(size_t)f * (n + 1) + n];
   }

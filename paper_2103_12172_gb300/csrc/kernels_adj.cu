@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(128, 7) k_adj_tri(Batch bt, const SubDesc *sub
                                                  double *ws, int has_rec) {
   __shared__ double sh[128];
   Item it; int local;
-  locate(bt, blockIdx.x, it, local);
+  locate(bt, bt.order ? bt.order[blockIdx.x] : (int)blockIdx.x, it, local);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;

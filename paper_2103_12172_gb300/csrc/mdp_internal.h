@@ -75,7 +75,7 @@ struct Batch {
   const Item *items;    // device array (nullptr: use `one`)
   const int *prefix;    // device array [n_items + 1] of block prefix sums for this kernel
   const int *order;     // device array [total_blocks]: the item-major block number that launch
-                        // block b runs (nullptr: b itself); k_tri runs its longest sweeps first
+                        // block b runs (nullptr: b itself); the sweeps run their longest first
   int n_items;
   int total_blocks;
   Item one;
@@ -169,7 +169,7 @@ struct mdp_plan {
   bool host_stale = false;               // device tables refactored since the host tables were built
   // per schedule and wave: device items and prefix arrays (one prefix array per kernel family)
   std::vector<mdp::Item *> d_items[3];
-  std::vector<int *> d_order[3];         // [wave] -> device int [k_tri blocks]: launch order of k_tri
+  std::vector<int *> d_order[3];         // [wave] -> device int [k_tri + k_adj_tri blocks]: launch orders
   std::vector<int *> d_prefix[3];        // [wave] -> device int [NFAM][n_items + 1]
   std::vector<std::vector<int>> h_prefix[3];
   // CUDA graphs of mdp_project_batch, keyed by (xi, out, kind, stream)
