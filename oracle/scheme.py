@@ -25,6 +25,12 @@ rotated by 90 degrees):
     condition: du/dy = delta/h - (h^2/24) u_yyy and u = abar - (h^2/8) u_yy at the
     half node, with u_yy = -u_xx - k^2 u from the homogeneous equation (g = 0 next
     to the auxiliary boundary, Section 3.2.1).
+  * AP_DIRX_SOMMY_PAPER: the Sommerfeld rows as printed (Eqs. AP_bounds_right/left), rotated,
+    with the undefined u_{M-1/2} read as abar and the i k bracket's difference quotient read as
+    abar, so that the bracket is dimensionally consistent:
+        (1/h)[delta - D delta/6 - (k^2 h^2/24) delta] + i k [abar + D abar/2 + (k^2 h^2/8) abar] = 0.
+    It is consistent with du/dn + i k u = 0 but only to O(h^2) (pinned); it exists to show that
+    the range of P_gamma does not depend on the choice of these rows.
 
 The unknowns are the nodes not fixed by a Dirichlet condition, in row-major
 (n, m) order.
@@ -34,7 +40,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-from workloads import AP_DIRICHLET4, AP_DIRX_SOMMY
+from workloads import AP_DIRICHLET4, AP_DIRX_SOMMY, AP_DIRX_SOMMY_PAPER
 
 
 def apply_L(w, h, k):
@@ -67,7 +73,7 @@ def unknown_mask(sub):
     m[:, 0] = m[:, -1] = False           # u = 0 at x = const (both AP types)
     if sub.ap_bc == AP_DIRICHLET4:
         m[0, :] = m[-1, :] = False       # and at y = const
-    elif sub.ap_bc != AP_DIRX_SOMMY:
+    elif sub.ap_bc not in (AP_DIRX_SOMMY, AP_DIRX_SOMMY_PAPER):
         raise ValueError("unknown AP type")
     return m
 
@@ -99,9 +105,22 @@ def _stencil_entries(sub, k, deriv=False):
     return rows, cols, vals
 
 
-def sommerfeld_row_weights(h, k, deriv=False):
+def sommerfeld_row_weights(h, k, deriv=False, paper=False):
     """Weights of the Sommerfeld row on (delta, D delta, abar, D abar):
-    row = wd*delta + wdd*D(delta) + wa*abar + wda*D(abar). deriv=True gives d/dk."""
+    row = wd*delta + wdd*D(delta) + wa*abar + wda*D(abar). deriv=True gives d/dk.
+    paper=True: the printed rows (AP_DIRX_SOMMY_PAPER)."""
+    if paper:
+        if not deriv:
+            wd = (1.0 / h) * (1.0 - k**2 * h**2 / 24.0)
+            wdd = -(1.0 / h) / 6.0
+            wa = 1j * k * (1.0 + k**2 * h**2 / 8.0)
+            wda = 1j * k / 2.0
+        else:
+            wd = -(1.0 / h) * (2.0 * k * h**2 / 24.0)
+            wdd = 0.0
+            wa = 1j * (1.0 + 3.0 * k**2 * h**2 / 8.0)
+            wda = 1j / 2.0
+        return wd, wdd, wa, wda
     if not deriv:
         wd = (1.0 / h) * (1.0 + k**2 * h**2 / 24.0)
         wdd = (1.0 / h) / 24.0
@@ -117,7 +136,7 @@ def sommerfeld_row_weights(h, k, deriv=False):
 
 def _sommerfeld_entries(sub, k, deriv=False):
     """(row_node, col_node, value) triples of the Sommerfeld rows at n = 0 and n = ny-1."""
-    wd, wdd, wa, wda = sommerfeld_row_weights(sub.h, k, deriv)
+    wd, wdd, wa, wda = sommerfeld_row_weights(sub.h, k, deriv, paper=sub.ap_bc == AP_DIRX_SOMMY_PAPER)
     nx, ny = sub.nx, sub.ny
     rows, cols, vals = [], [], []
     for (nb, ni) in ((ny - 1, ny - 2), (0, 1)):   # (boundary row, its inner neighbour)
@@ -148,7 +167,7 @@ def assemble(sub, k=None, deriv=False):
         R.append(idx[rn, rm][keep])
         C.append(idx[cn, cm][keep])
         V.append(v[keep])
-    if sub.ap_bc == AP_DIRX_SOMMY:
+    if sub.ap_bc in (AP_DIRX_SOMMY, AP_DIRX_SOMMY_PAPER):
         rows, cols, vals = _sommerfeld_entries(sub, k, deriv)
         for (rn, rm), (cn, cm), v in zip(rows, cols, vals):
             if U[cn, cm]:

@@ -75,10 +75,10 @@ def test_splu_matches_dense_solve_and_adjoint(ap, n):
     assert np.abs(xa - xd).max() < 1e-11 * np.abs(xd).max()
 
 
-def _sommerfeld_truncation(n, k, theta, top):
+def _sommerfeld_truncation(n, k, theta, top, ap=W.AP_DIRX_SOMMY):
     """Residual of the assembled Sommerfeld row on a continuous plane wave, minus the
     exact du/dn + i k u at the half node (n outward)."""
-    sub = W.small_subdomain(n, k, W.AP_DIRX_SOMMY, 4)
+    sub = W.small_subdomain(n, k, ap, 4)
     A, U, idx = assemble(sub)
     x, y = node_coordinates(sub)
     X, Y = np.meshgrid(x, y)
@@ -103,8 +103,19 @@ def test_sommerfeld_rows_are_fourth_order(top):
     assert np.all(rates > 3.7), rates
 
 
-def test_dk_matrix_matches_finite_difference():
-    sub = W.small_subdomain(17, 7.0, W.AP_DIRX_SOMMY, 4)
+@pytest.mark.parametrize("top", [True, False])
+def test_paper_sommerfeld_rows_are_second_order(top):
+    """The Sommerfeld rows as printed (AP_DIRX_SOMMY_PAPER: D delta / 6 with a minus sign,
+    -k^2 h^2 / 24, D abar / 2) are consistent with du/dn + i k u = 0 but only to O(h^2): the
+    truncation error falls ~4x per halving of h. This is why the default rows are re-derived."""
+    errs = [_sommerfeld_truncation(n, 10.0, 0.7, top, W.AP_DIRX_SOMMY_PAPER) for n in (33, 65, 129, 257)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(rates - 2.0) < 0.2), rates
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRX_SOMMY, W.AP_DIRX_SOMMY_PAPER])
+def test_dk_matrix_matches_finite_difference(ap):
+    sub = W.small_subdomain(17, 7.0, ap, 4)
     dA = assemble(sub, deriv=True)[0].toarray()
     d = 1e-5
     fd = (assemble(sub, k=7.0 + d)[0].toarray() - assemble(sub, k=7.0 - d)[0].toarray()) / (2 * d)

@@ -13,8 +13,11 @@ same configuration scaled by 1/2.
 
 Auxiliary-problem boundary types (Section 3.2.1, rotated so that the sine
 transform runs along x):
-  AP_DIRICHLET4   -- u = 0 on all four sides of the auxiliary rectangle;
-  AP_DIRX_SOMMY   -- u = 0 at x = const, local Sommerfeld rows at y = const.
+  AP_DIRICHLET4        -- u = 0 on all four sides of the auxiliary rectangle;
+  AP_DIRX_SOMMY        -- u = 0 at x = const, local Sommerfeld rows at y = const (the O(h^4)
+                          half-node rows of our own derivation);
+  AP_DIRX_SOMMY_PAPER  -- the same with the Sommerfeld rows as printed in the paper (Eqs.
+                          AP_bounds_right/left), read with u_{M-1/2} = the half-node mean.
 """
 from __future__ import annotations
 
@@ -25,6 +28,7 @@ import numpy as np
 
 AP_DIRICHLET4 = 0
 AP_DIRX_SOMMY = 1
+AP_DIRX_SOMMY_PAPER = 2
 
 
 @dataclass(frozen=True)
@@ -35,7 +39,7 @@ class Subdomain:
     ax0, ay0, h    : lower-left corner of the auxiliary grid and its step
     nx, ny         : nodes of the auxiliary grid along x and y
     k              : real wavenumber on Omega_i
-    ap_bc          : AP_DIRICHLET4 or AP_DIRX_SOMMY
+    ap_bc          : AP_DIRICHLET4, AP_DIRX_SOMMY or AP_DIRX_SOMMY_PAPER
     n_modes        : M*, Chebyshev modes per side (Section 3.2.4)
     """
     x0: float
