@@ -11,7 +11,11 @@
  *  - The sine transform runs along x: u = 0 on the sides x = const. Along y the AP has
  *    u = 0 (MDP_AP_DIRICHLET4) or the local Sommerfeld condition du/dn + i k u = 0,
  *    imposed at the half node between the last two node rows with O(h^4) corrections
- *    (MDP_AP_DIRX_SOMMY; Section 3.2.1, Eq. auxiliary_problem).
+ *    (MDP_AP_DIRX_SOMMY; Section 3.2.1, Eq. auxiliary_problem). MDP_AP_DIRX_SOMMY_PAPER
+ *    takes the Sommerfeld rows as printed (Eqs. AP_bounds_right/left, rotated; the undefined
+ *    u_{M-1/2} and the i k bracket's difference quotient read as the half-node mean), which
+ *    are second-order accurate; the range of P_gamma, and so any coupled solution, does not
+ *    depend on the AP's boundary rows.
  *  - gamma is ordered row-major in (n, m). Column c of a subdomain's block is the basis
  *    pair Psi: c = kind*4M* + (side-1)*M* + (j-1), kind 0 = Dirichlet (psi_j, 0), kind 1 =
  *    Neumann (0, psi_j), sides 1 bottom, 2 top, 3 left, 4 right, psi_j = T_{j-1}(s)
@@ -50,7 +54,7 @@ typedef enum {
   MDP_ERR_STATE = 6      /* call not valid for this plan (e.g. host-only plan) */
 } mdp_status;
 
-enum { MDP_AP_DIRICHLET4 = 0, MDP_AP_DIRX_SOMMY = 1 };
+enum { MDP_AP_DIRICHLET4 = 0, MDP_AP_DIRX_SOMMY = 1, MDP_AP_DIRX_SOMMY_PAPER = 2 };
 enum { MDP_OUT_Q = 0, MDP_OUT_P = 1 };
 
 /* Plan flags */
@@ -78,7 +82,7 @@ typedef struct {
   double ax0, ay0, h;     /* AP lower-left corner and grid step (the same in x and y, Section 3.1) */
   int nx, ny;             /* AP nodes along x and y */
   double k;               /* real wavenumber on Omega_i, > 0 */
-  int ap_bc;              /* MDP_AP_DIRICHLET4 or MDP_AP_DIRX_SOMMY */
+  int ap_bc;              /* MDP_AP_DIRICHLET4, MDP_AP_DIRX_SOMMY or MDP_AP_DIRX_SOMMY_PAPER */
   int n_modes;            /* M* >= 1: Chebyshev modes per side; 8*M* columns */
 } mdp_subdomain;
 
@@ -270,7 +274,7 @@ mdp_status mdp_plan_gamma_geometry(const mdp_plan *p, int sub, int *owner, doubl
 
 /* Solve one mode's tridiagonal system T_q x = b (adjoint = 0) or T_q^H x = b (adjoint = 1)
  * on the host with the plan's stored factors, q = 1..nx-2. b and x are host arrays over the
- * y unknowns (ny values for MDP_AP_DIRX_SOMMY, n = 0..ny-1; ny-2 values for
+ * y unknowns (ny values for the Sommerfeld APs, n = 0..ny-1; ny-2 values for
  * MDP_AP_DIRICHLET4, n = 1..ny-2). A grid function sin(pi q m/(nx-1)) b(n) on M0 is mapped
  * by G^(h) to sin(pi q m/(nx-1)) x(n). */
 mdp_status mdp_host_mode_solve(const mdp_plan *p, int sub, int q, int adjoint, const mdp_c64 *b,

@@ -96,7 +96,12 @@ class Plan:
         return owner, rho, s
 
     def host_mode_solve(self, sub: int, q: int, b, adjoint: bool = False):
+        """T_q^{-1} b (or T_q^{-H} b) on the host: b holds one value per unknown row of the
+        mode system (Nt values; the C call reads and writes exactly that many)."""
         b = np.ascontiguousarray(b, dtype=np.complex128)
+        nt = self.sub_info(sub)["Nt"]
+        if b.ndim != 1 or b.size != nt:
+            raise ValueError(f"host_mode_solve: b must hold {nt} values, got shape {b.shape}")
         x = np.zeros_like(b)
         _lib.check(self.L.mdp_host_mode_solve(self.handle, sub, q, int(adjoint), b.ctypes.data_as(C.c_void_p),
                                               x.ctypes.data_as(C.c_void_p)), "mdp_host_mode_solve")

@@ -8,7 +8,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmdp.so")
 
 MDP_OK, MDP_ERR_ARG, MDP_ERR_CUDA, MDP_ERR_NOMEM, MDP_ERR_SINGULAR, MDP_ERR_TIMEOUT, MDP_ERR_STATE = range(7)
-MDP_AP_DIRICHLET4, MDP_AP_DIRX_SOMMY = 0, 1
+MDP_AP_DIRICHLET4, MDP_AP_DIRX_SOMMY, MDP_AP_DIRX_SOMMY_PAPER = 0, 1, 2
 MDP_OUT_Q, MDP_OUT_P = 0, 1
 MDP_PLAN_HOST_ONLY = 0x1
 MDP_PLAN_GRAPH = 0x2

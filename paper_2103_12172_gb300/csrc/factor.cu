@@ -85,10 +85,11 @@ __device__ ModeRows mode_rows(const SubDesc &d, int q) {
   m.dd = -2.0 * m.a + lam / h2 + k2 + k2 * lam / 12.0;
   m.da = k / 6.0;
   m.ddd = -2.0 * m.da + 2.0 * k + 2.0 * k * lam / 12.0;
-  const double alpha = (1.0 + k2 * h2 / 24.0 + lam / 24.0) / h2;
-  const double beta = k * (1.0 + k2 * h2 / 8.0 + lam / 8.0) / h;           // imaginary part
-  const double dalpha = k / 12.0;
-  const double dbeta = (1.0 + 3.0 * k2 * h2 / 8.0 + lam / 8.0) / h;        // imaginary part
+  const bool paper = d.ap_bc == MDP_AP_DIRX_SOMMY_PAPER;                   // the rows as printed
+  const double alpha = paper ? (1.0 - k2 * h2 / 24.0 - lam / 6.0) / h2 : (1.0 + k2 * h2 / 24.0 + lam / 24.0) / h2;
+  const double beta = k * (1.0 + k2 * h2 / 8.0 + lam / (paper ? 2.0 : 8.0)) / h;           // imaginary part
+  const double dalpha = paper ? -k / 12.0 : k / 12.0;
+  const double dbeta = (1.0 + 3.0 * k2 * h2 / 8.0 + lam / (paper ? 2.0 : 8.0)) / h;        // imaginary part
   m.cp = cmk(alpha, 0.5 * beta);
   m.cm = cmk(-alpha, 0.5 * beta);
   m.tp = cmk(dalpha, 0.5 * dbeta);

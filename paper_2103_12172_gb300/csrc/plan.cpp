@@ -48,13 +48,14 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   SubDesc &d = hs.d;
   std::memset(&d, 0, sizeof d);
   if (in.nx < 9 || in.ny < 9 || !(in.h > 0) || !(in.k > 0) || in.n_modes < 1 ||
-      (in.ap_bc != MDP_AP_DIRICHLET4 && in.ap_bc != MDP_AP_DIRX_SOMMY) || !(in.x1 > in.x0) ||
+      (in.ap_bc != MDP_AP_DIRICHLET4 && in.ap_bc != MDP_AP_DIRX_SOMMY && in.ap_bc != MDP_AP_DIRX_SOMMY_PAPER) ||
+      !(in.x1 > in.x0) ||
       !(in.y1 > in.y0) || !std::isfinite(in.k))
     return MDP_ERR_ARG;
   d.nx = in.nx; d.ny = in.ny; d.Nx = in.nx - 1; d.Nq = d.Nx - 1;
   d.h = in.h; d.k = in.k;
   d.x0 = in.x0; d.x1 = in.x1; d.y0 = in.y0; d.y1 = in.y1; d.ax0 = in.ax0; d.ay0 = in.ay0;
-  d.ap_bc = in.ap_bc; d.cplx = in.ap_bc == MDP_AP_DIRX_SOMMY;
+  d.ap_bc = in.ap_bc; d.cplx = in.ap_bc != MDP_AP_DIRICHLET4;
   d.n_modes = in.n_modes; d.n_cols = 8 * in.n_modes;
   // M+ = M0 nodes strictly inside the open subdomain: an interval along each axis.
   int mlo = -1, mhi = -1, nlo = -1, nhi = -1;
@@ -124,7 +125,8 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
 //     a = 1/h^2 + lambda/(6h^2) + k^2/12,  d = -2a + lambda/h^2 + k^2 + k^2 lambda/12;
 //   Sommerfeld rows (scaled by 1/h): alpha (u_N - u_{N-1}) + beta (u_N + u_{N-1})/2 = 0 with
 //     alpha = (1 + k^2h^2/24 + lambda/24)/h^2,  beta = i k (1 + k^2h^2/8 + lambda/8)/h,
-//   and the mirror image at n = 0.
+//   and the mirror image at n = 0; as printed (MDP_AP_DIRX_SOMMY_PAPER)
+//     alpha = (1 - k^2h^2/24 - lambda/6)/h^2,   beta = i k (1 + k^2h^2/8 + lambda/2)/h.
 // Factorisation: Gaussian elimination with partial pivoting on the band (row swaps create
 // one extra super-diagonal), the textbook algorithm for banded LU.
 // The tridiagonal T_q of sine mode q (rows 0..Nt-1) and, when dT != nullptr, its k-derivative
@@ -138,10 +140,11 @@ static void mode_matrix(const SubDesc &d, int q, cd *dl, cd *dg, cd *du, double 
   const double dd = -2.0 * a + lam / h2 + k2 + k2 * lam / 12.0;
   const double da = k / 6.0;
   const double ddd = -2.0 * da + 2.0 * k + 2.0 * k * lam / 12.0;
-  const cd alpha((1.0 + k2 * h2 / 24.0 + lam / 24.0) / h2, 0.0);
-  const cd beta(0.0, k * (1.0 + k2 * h2 / 8.0 + lam / 8.0) / h);
-  const cd dalpha(k / 12.0, 0.0);
-  const cd dbeta(0.0, (1.0 + 3.0 * k2 * h2 / 8.0 + lam / 8.0) / h);
+  const bool paper = d.ap_bc == MDP_AP_DIRX_SOMMY_PAPER;
+  const cd alpha(paper ? (1.0 - k2 * h2 / 24.0 - lam / 6.0) / h2 : (1.0 + k2 * h2 / 24.0 + lam / 24.0) / h2, 0.0);
+  const cd beta(0.0, k * (1.0 + k2 * h2 / 8.0 + lam / (paper ? 2.0 : 8.0)) / h);
+  const cd dalpha(paper ? -k / 12.0 : k / 12.0, 0.0);
+  const cd dbeta(0.0, (1.0 + 3.0 * k2 * h2 / 8.0 + lam / (paper ? 2.0 : 8.0)) / h);
   for (int i = 0; i < N; ++i) {
     dl[i] = a; dg[i] = dd; du[i] = a;
     cd tsub = da, tdg = ddd, tsup = da;

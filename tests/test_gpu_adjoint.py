@@ -37,7 +37,9 @@ CASES = [("dir4_n65", W.small_subdomain(65, 9.0, W.AP_DIRICHLET4, 2), 8),
          ("somm_n129", W.small_subdomain(129, 20.0, W.AP_DIRX_SOMMY, 3), None),
          # Nx not a power of 2: direct dense-row sums in the adjoint
          ("somm_n61_direct", W.small_subdomain(61, 10.0, W.AP_DIRX_SOMMY, 2), 8),
-         ("dir4_n50_direct_oddNx", W.small_subdomain(50, 8.0, W.AP_DIRICHLET4, 2), None)]
+         ("dir4_n50_direct_oddNx", W.small_subdomain(50, 8.0, W.AP_DIRICHLET4, 2), None),
+         # the Sommerfeld rows as printed in the paper (their own k-derivatives)
+         ("somm_paper_n65", W.small_subdomain(65, 11.0, W.AP_DIRX_SOMMY_PAPER, 2), 8)]
 
 
 @pytest.mark.parametrize("name,sub,tile", CASES, ids=[c[0] for c in CASES])
@@ -83,7 +85,7 @@ def test_grad_k_matches_central_differences_of_gpu_forward(mdp):
     assert abs(gk.item() - fd) < 1e-6 * abs(fd), (gk.item(), fd)
 
 
-@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY, W.AP_DIRX_SOMMY_PAPER])
 def test_dot_product_identity(mdp, ap):
     sub = W.small_subdomain(129, 14.0, ap, 2)
     plan = make_plan(mdp, [sub], 16)

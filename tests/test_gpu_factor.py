@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 CASES = [("somm_n65", W.small_subdomain(65, 11.0, W.AP_DIRX_SOMMY, 3), 14.5),
          ("dir4_n65", W.small_subdomain(65, 9.0, W.AP_DIRICHLET4, 3), 7.25),
          ("somm_n61", W.small_subdomain(61, 10.0, W.AP_DIRX_SOMMY, 2), 12.0),
-         ("somm_n257_k30", W.dd2x2_257().subdomains[0], 31.5)]
+         ("somm_n257_k30", W.dd2x2_257().subdomains[0], 31.5),
+         ("somm_paper_n65", W.small_subdomain(65, 9.0, W.AP_DIRX_SOMMY_PAPER, 2), 10.5)]
 
 
 def cols_close(dev, host, ncomplex):
@@ -63,7 +64,7 @@ def test_device_factorisation_matches_host(mdp, name, sub, k1):
     assert worst < 1e-12
 
 
-@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY, W.AP_DIRX_SOMMY_PAPER])
 def test_projection_after_device_refactor_matches_oracle(mdp, ap):
     sub = W.small_subdomain(65, 9.0, ap, 3)
     plan = mdp.Plan([sub], tile_cols=16)

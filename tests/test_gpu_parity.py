@@ -45,7 +45,7 @@ def make_plan(mdp, subs, tile=None):
                 os.environ["MDP_TILE_COLS"] = old
 
 
-@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY, W.AP_DIRX_SOMMY_PAPER])
 @pytest.mark.parametrize("n,k", [(33, 6.0), (129, 10.0)])
 def test_full_grid_solve_and_adjoint(dev, ap, n, k):
     sub = W.small_subdomain(n, k, ap, 4)
@@ -74,6 +74,9 @@ PROJ_CASES = [
     # grids whose Nx is not a power of 2: the dense rows take the direct sine sums
     ("n61_somm_m3_direct", W.small_subdomain(61, 8.0, W.AP_DIRX_SOMMY, 3), 8),
     ("n50_dir4_m2_direct_oddNx", W.small_subdomain(50, 7.0, W.AP_DIRICHLET4, 2), None),
+    # the Sommerfeld rows as printed in the paper; FFT and direct dense rows
+    ("n65_somm_paper_m3", W.small_subdomain(65, 10.0, W.AP_DIRX_SOMMY_PAPER, 3), 16),
+    ("n61_somm_paper_m2_direct", W.small_subdomain(61, 8.0, W.AP_DIRX_SOMMY_PAPER, 2), None),
 ]
 
 
