@@ -286,162 +286,14 @@ __global__ void __launch_bounds__(256) k_fwd_rows(Batch bt, const SubDesc *subs,
 }
 
 // ---------------------------------------------------------------- k_tri
-// Per (mode q, column b): forward elimination with the stored row swaps from matrix row i0
-// (rows below carry zero right-hand side) to the top, then back substitution down to i0.
-// RHS at grid row n: the dense ring rows read ghat; the middle ring rows have 4 nonzeros
-// (columns mlo, mlo+1, mhi-1, mhi), so their sine transform is 4 products here.
-// CF: complex factors. CIN: complex ring data. Output y[q-1][n - (nlo-1)][b] for the rows
-// nlo-1 .. nhi+1, complex unless neither CF nor CIN (real path).
-// FULL: back substitution down to row 0 and every row stored as y[q-1][i][b] (i = 0..Nt-1),
-// the layout of the gradient pass.
-// Factor rows [rlo, rhi) of a complex AP mode are real to working precision (set by the plan):
-// there the sweeps use real factors, and the forward sweep stays in real arithmetic while the
-// data are still real (real densities, no complex factor row met yet).
-template <bool CF, bool CIN, bool FULL>
-__device__ __forceinline__ void tri_body(const Item &it, const SubDesc &d, const double *tab, const uint8_t *pivtab,
-                                         double *ws, int b, int q) {
-  constexpr bool CD = CF || CIN || FULL;  // complex data in the sweep (the gradient pass stores complex)
-  const int N2 = 2 * d.Nx;
-  const double *S = tab + d.sin_off;
-  const double sm0 = S[(q * d.mlo) % N2], sm1 = S[(q * (d.mlo + 1)) % N2];
-  const double sm2 = S[(q * (d.mhi - 1)) % N2], sm3 = S[(q * d.mhi) % N2];
-  const int par = (q & 1) ? 0 : 1;
-  constexpr int FW = CF ? 8 : 4;
-  const double *F = tab + d.fact_off + (long long)(q - 1) * d.Nt * FW;
-  const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * d.Nt;
-  const double *r = ws + it.r_off;
-  const double *gr = ws + it.gr_off;
-  double *y = ws + it.y_off;
-  const long long ystride = it.ncols;                         // between stored rows
-  const int yrows = FULL ? d.Nt : d.NYf, yfirst = FULL ? 0 : d.i0;
-  const long long ybase = (long long)(q - 1) * yrows * it.ncols + b;
-  const int P = d.Px, nc = it.ncols;
-  int rlo = 0, rhi = d.Nt;  // real factor rows
-  if (CF) {
-    const double *sg = tab + d.seg_off + 5 * (q - 1);
-    rlo = (int)sg[0];
-    rhi = (int)sg[1];
-  }
-  auto rhs = [&](int n) -> cplx {
-    if (n < d.nlo || n > d.nhi) return cmk(0.0, 0.0);
-    int rr = -1;
-    if (n == d.nlo) rr = 0; else if (n == d.nlo + 1) rr = 1; else if (n == d.nhi - 1) rr = 2; else if (n == d.nhi) rr = 3;
-    if (rr >= 0) {
-      const long long o = ((long long)rr * d.Nq + (q - 1)) * nc + b;
-      return CIN ? ld2(gr + 2 * o) : cmk(gr[o], 0.0);
-    }
-    if (d.xsym) {  // (sum, difference) pairs of columns (mlo, mhi) and (mlo+1, mhi-1)
-      const long long base = 8LL * d.Ph + 4 * (n - d.nlo - 2) + par;
-      if (CIN) {
-        const cplx v0 = ld2(r + 2 * (base * nc + b));
-        return caxpy(sm1, ld2(r + 2 * ((base + 2) * nc + b)), cmk(sm0 * v0.re, sm0 * v0.im));
-      }
-      return cmk(fma(sm1, r[(base + 2) * nc + b], sm0 * r[base * nc + b]), 0.0);
-    }
-    const long long ri = 2 * P + 4 * (n - d.nlo - 2);
-    if (CIN) {
-      cplx v = cmk(0.0, 0.0);
-      v = caxpy(sm0, ld2(r + 2 * ((ri + 0) * nc + b)), v);
-      v = caxpy(sm1, ld2(r + 2 * ((ri + 1) * nc + b)), v);
-      v = caxpy(sm2, ld2(r + 2 * ((ri + 2) * nc + b)), v);
-      v = caxpy(sm3, ld2(r + 2 * ((ri + 3) * nc + b)), v);
-      return v;
-    }
-    double v = sm0 * r[(ri + 0) * nc + b];
-    v = fma(sm1, r[(ri + 1) * nc + b], v);
-    v = fma(sm2, r[(ri + 2) * nc + b], v);
-    v = fma(sm3, r[(ri + 3) * nc + b], v);
-    return cmk(v, 0.0);
-  };
-  auto ystore = [&](int i, cplx v) {
-    const long long o = ybase + (long long)(i - yfirst) * ystride;
-    if (CD) st2(y + 2 * o, v); else y[o] = v.re;
-  };
-  auto yload = [&](int i) -> cplx {
-    if (FULL && i < d.i0) return cmk(0.0, 0.0);   // rows below the ring: zero after elimination
-    const long long o = ybase + (long long)(i - yfirst) * ystride;
-    return CD ? ld2(y + 2 * o) : cmk(y[o], 0.0);
-  };
-  // ---- forward sweep: cur holds the eliminated value of row i
-  cplx cur = cmk(0.0, 0.0);
-  const int iend = d.Nt - 1;
-  int i = d.i0;
-  if (CF) {  // complex factor rows below the real run
-    const int e = min(max(rlo, d.i0), iend);
-    for (; i < e; ++i) {
-      const cplx g = rhs(i + 1 + d.nfirst);
-      const cplx l = ld2(F + i * FW);
-      cplx yv;
-      if (pv[i]) { yv = g; cur = cfms(cur, l, g); } else { yv = cur; cur = cfms(g, l, cur); }
-      ystore(i, yv);
-    }
-  }
-  {
-    const int e = min(max(rhi, i), iend);
-    const bool realdata = !CIN && !(CF && i > d.i0);  // nothing complex has entered cur yet
-    if (realdata) {
-      for (; i < e; ++i) {
-        const double g = rhs(i + 1 + d.nfirst).re;
-        const double l = F[i * FW];
-        double yv;
-        if (pv[i]) { yv = g; cur.re = fma(-l, g, cur.re); } else { yv = cur.re; cur.re = fma(-l, cur.re, g); }
-        ystore(i, cmk(yv, 0.0));
-      }
-    } else {
-      for (; i < e; ++i) {
-        const cplx g = rhs(i + 1 + d.nfirst);
-        const double l = F[i * FW];
-        cplx yv;
-        if (pv[i]) { yv = g; cur = caxpy(-l, g, cur); } else { yv = cur; cur = caxpy(-l, cur, g); }
-        ystore(i, yv);
-      }
-    }
-  }
-  if (CF) {  // complex factor rows above the real run
-    for (; i < iend; ++i) {
-      const cplx g = rhs(i + 1 + d.nfirst);
-      const cplx l = ld2(F + i * FW);
-      cplx yv;
-      if (pv[i]) { yv = g; cur = cfms(cur, l, g); } else { yv = cur; cur = cfms(g, l, cur); }
-      ystore(i, yv);
-    }
-  }
-  ystore(iend, cur);
-  // ---- back substitution (keep rows nlo-1 .. nhi+1, or all rows with FULL)
-  const int ikeep = d.nhi + 1 - d.nfirst;
-  const int ilo = FULL ? 0 : d.i0;
-  cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
-  auto back_complex = [&](int i) {
-    const cplx yi = yload(i);
-    const cplx dinv = ld2(F + i * FW + 2), u1 = ld2(F + i * FW + 4);
-    cplx x = cfms(cmul(dinv, yi), u1, x1);
-    if (pv[i]) x = cfms(x, ld2(F + i * FW + 6), x2);
-    if (FULL || i <= ikeep) ystore(i, x);
-    x2 = x1; x1 = x;
-  };
-  auto back_real = [&](int i) {
-    const cplx yi = yload(i);
-    const double dinv = F[i * FW + (CF ? 2 : 1)], u1 = F[i * FW + (CF ? 4 : 2)];
-    cplx x = cmk(fma(-u1, x1.re, dinv * yi.re), CD ? fma(-u1, x1.im, dinv * yi.im) : 0.0);
-    if (pv[i]) {
-      const double u2 = F[i * FW + (CF ? 6 : 3)];
-      x.re = fma(-u2, x2.re, x.re);
-      if (CD) x.im = fma(-u2, x2.im, x.im);
-    }
-    if (FULL || i <= ikeep) ystore(i, x);
-    x2 = x1; x1 = x;
-  };
-  i = d.Nt - 1;
-  if (CF) for (; i >= max(rhi, ilo); --i) back_complex(i);
-  for (; i >= max(rlo, ilo); --i) back_real(i);
-  if (CF) for (; i >= ilo; --i) back_complex(i);
-}
-
 // Asynchronous global -> shared copies (cp.async): operands of rows ahead are in flight while
 // the current row is swept, without holding registers for them.
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
@@ -449,6 +301,217 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// The gradient pass's forward recompute: per (mode q, column b) the full pivoted LU sweep over
+// every row -- forward elimination with the stored row swaps from matrix row i0 (rows below carry
+// zero right-hand side) to the top, then back substitution down to row 0, every row stored as
+// y[q-1][i][b] (complex). RHS at grid row n: the dense ring rows read ghat; the middle ring rows
+// have 4 nonzeros (columns mlo, mlo+1, mhi-1, mhi), so their sine transform is 4 products here.
+// CF: complex factors (Sommerfeld AP). CIN: complex ring data. Factor rows [rlo, rhi) of a
+// complex AP are real to working precision (set by the plan): there the sweeps use real factors,
+// and the forward sweep stays in real arithmetic while the data are still real (real densities,
+// no complex factor row met yet). Operands are staged like the projection sweep's, TRI_STAGES
+// rows ahead: the factor row, the 4-byte word holding the row's swap flag, and the lane's ring
+// values (forward) or stored y (back).
+template <bool CIN>
+__host__ __device__ constexpr int full_stage_bytes() { return 80 + 4 * 32 * (CIN ? 16 : 8); }
+
+template <bool CF, bool CIN>
+__device__ __forceinline__ void tri_full_body(const Item &it, const SubDesc &d, const double *tab, const uint8_t *pivtab,
+                                              double *ws, int b, int q, char *sw, int lane, int nact, unsigned mask) {
+  constexpr int FW = CF ? 8 : 4, VS = CIN ? 16 : 8, SB = full_stage_bytes<CIN>(), RING = 80;
+  constexpr int TRI_D = 2;   // stages per warp
+  // descriptor fields in registers (the copies' memory clobbers would otherwise reload them)
+  const int i0 = d.i0, nfirst = d.nfirst, nlo = d.nlo, nhi = d.nhi, Nq = d.Nq, Ph = d.Ph, Nt = d.Nt;
+  const bool xsym = d.xsym;
+  const int N2 = 2 * d.Nx;
+  const double *S = tab + d.sin_off;
+  const double sm0 = S[(q * d.mlo) % N2], sm1 = S[(q * (d.mlo + 1)) % N2];
+  const double sm2 = S[(q * (d.mhi - 1)) % N2], sm3 = S[(q * d.mhi) % N2];
+  const int par = (q & 1) ? 0 : 1;
+  const double *F = tab + d.fact_off + (long long)(q - 1) * Nt * FW;
+  const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * Nt;
+  const double *r = ws + it.r_off;
+  const double *gr = ws + it.gr_off;
+  double *y = ws + it.y_off;
+  const int P = d.Px, nc = it.ncols;
+  const long long ybase = (long long)(q - 1) * Nt * nc + b;
+  int rlo = 0, rhi = Nt;  // real factor rows
+  if (CF) {
+    const double *sg = tab + d.seg_off + 5 * (q - 1);
+    rlo = (int)sg[0];
+    rhi = (int)sg[1];
+  }
+  auto ystore = [&](int i, cplx v) { st2(y + 2 * (ybase + (long long)i * nc), v); };
+  auto dense = [&](int n) -> int {
+    return n == nlo ? 0 : n == nlo + 1 ? 1 : n == nhi - 1 ? 2 : n == nhi ? 3 : -1;
+  };
+  auto stage = [&](int i) -> char * { return sw + (i & (TRI_D - 1)) * SB; };
+  // the factor row and the word holding the row's swap flag (the flag table is 4-byte aligned
+  // and padded to a multiple of 32 bytes, so the word never leaves it)
+  auto fetch_row = [&](char *st, int i) {
+    const double *src = F + (long long)i * FW;
+    if (nact >= FW / 2) {
+      if (lane < FW / 2) cp_async16(st + 16 * lane, src + 2 * lane);
+    } else {
+      for (int c = lane; c < FW / 2; c += nact) cp_async16(st + 16 * c, src + 2 * c);
+    }
+    if (lane == 0) {
+      const uintptr_t a = reinterpret_cast<uintptr_t>(pv + i);
+      cp_async4(st + 64, reinterpret_cast<const void *>(a & ~(uintptr_t)3));
+    }
+  };
+  auto flag = [&](const char *st, int i) -> bool {
+    const unsigned w = *reinterpret_cast<const unsigned *>(st + 64);
+    return ((w >> (8 * (reinterpret_cast<uintptr_t>(pv + i) & 3))) & 0xffu) != 0;
+  };
+  // ---- forward staging: factor row, flag word, ring values of grid row n = i + 1 + nfirst
+  auto fetch_fwd = [&](int i) {
+    char *st = stage(i);
+    fetch_row(st, i);
+    const int n = i + 1 + nfirst;
+    if (n >= nlo && n <= nhi) {
+      char *rb = st + RING + VS * lane;
+      auto cpv = [&](int slot, const double *base, long long o) {
+        if (CIN) cp_async16(rb + slot * 32 * VS, base + 2 * o); else cp_async8(rb + slot * 32 * VS, base + o);
+      };
+      const int rr = dense(n);
+      if (rr >= 0) {
+        cpv(0, gr, ((long long)rr * Nq + (q - 1)) * nc + b);
+      } else if (xsym) {
+        const long long base = 8LL * Ph + 4 * (n - nlo - 2) + par;
+        cpv(0, r, base * nc + b);
+        cpv(1, r, (base + 2) * nc + b);
+      } else {
+        const long long ri = 2 * P + 4 * (n - nlo - 2);
+        for (int s_ = 0; s_ < 4; ++s_) cpv(s_, r, (ri + s_) * nc + b);
+      }
+    }
+    cp_async_commit();
+  };
+  auto sv = [&](const char *st, int slot) -> cplx {
+    const double *p = reinterpret_cast<const double *>(st + RING + VS * lane + slot * 32 * VS);
+    return CIN ? ld2(p) : cmk(p[0], 0.0);
+  };
+  // right-hand side of grid row n from the staged ring values
+  auto rhs = [&](const char *st, int n) -> cplx {
+    if (n < nlo || n > nhi) return cmk(0.0, 0.0);
+    if (dense(n) >= 0) return sv(st, 0);
+    if (xsym) {
+      const cplx v0 = sv(st, 0);
+      return caxpy(sm1, sv(st, 1), cmk(sm0 * v0.re, sm0 * v0.im));
+    }
+    cplx v = cmk(0.0, 0.0);
+    v = caxpy(sm0, sv(st, 0), v); v = caxpy(sm1, sv(st, 1), v); v = caxpy(sm2, sv(st, 2), v); v = caxpy(sm3, sv(st, 3), v);
+    return v;
+  };
+  const int iend = Nt - 1;
+  auto begin = [&](int i) -> const char * {
+    cp_async_wait<TRI_D - 1>();
+    __syncwarp(mask);
+    return stage(i);
+  };
+  auto end_fwd = [&](int i) {
+    __syncwarp(mask);
+    if (i + TRI_D < iend) fetch_fwd(i + TRI_D); else cp_async_commit();
+  };
+  for (int j = 0; j < TRI_D; ++j) {
+    if (i0 + j < iend) fetch_fwd(i0 + j); else cp_async_commit();
+  }
+  // ---- forward sweep: cur holds the eliminated value of row i
+  cplx cur = cmk(0.0, 0.0);
+  int i = i0;
+  auto fwd_complex = [&](int i) {
+    const char *st = begin(i);
+    const double *row = reinterpret_cast<const double *>(st);
+    const cplx g = rhs(st, i + 1 + nfirst);
+    const cplx l = ld2(row);
+    cplx yv;
+    if (flag(st, i)) { yv = g; cur = cfms(cur, l, g); } else { yv = cur; cur = cfms(g, l, cur); }
+    ystore(i, yv);
+    end_fwd(i);
+  };
+  if (CF) {  // complex factor rows below the real run
+    const int e = min(max(rlo, i0), iend);
+    for (; i < e; ++i) fwd_complex(i);
+  }
+  {
+    const int e = min(max(rhi, i), iend);
+    const bool realdata = !CIN && !(CF && i > i0);  // nothing complex has entered cur yet
+    if (realdata) {
+      for (; i < e; ++i) {
+        const char *st = begin(i);
+        const double g = rhs(st, i + 1 + nfirst).re;
+        const double l = reinterpret_cast<const double *>(st)[0];
+        double yv;
+        if (flag(st, i)) { yv = g; cur.re = fma(-l, g, cur.re); } else { yv = cur.re; cur.re = fma(-l, cur.re, g); }
+        ystore(i, cmk(yv, 0.0));
+        end_fwd(i);
+      }
+    } else {
+      for (; i < e; ++i) {
+        const char *st = begin(i);
+        const cplx g = rhs(st, i + 1 + nfirst);
+        const double l = reinterpret_cast<const double *>(st)[0];
+        cplx yv;
+        if (flag(st, i)) { yv = g; cur = caxpy(-l, g, cur); } else { yv = cur; cur = caxpy(-l, cur, g); }
+        ystore(i, yv);
+        end_fwd(i);
+      }
+    }
+  }
+  if (CF)  // complex factor rows above the real run
+    for (; i < iend; ++i) fwd_complex(i);
+  ystore(iend, cur);
+  // the stored rows are read back below by this thread's asynchronous copies: order them after
+  // its stores
+  __threadfence_block();
+  // ---- back substitution, every row stored (rows below i0 have zero eliminated right-hand side)
+  auto fetch_back = [&](int i) {
+    char *st = stage(i);
+    fetch_row(st, i);
+    if (i >= i0) cp_async16(st + RING + 16 * lane, y + 2 * (ybase + (long long)i * nc));
+    cp_async_commit();
+  };
+  auto end_back = [&](int i) {
+    __syncwarp(mask);
+    if (i - TRI_D >= 0) fetch_back(i - TRI_D); else cp_async_commit();
+  };
+  for (int j = 0; j < TRI_D; ++j) {
+    if (iend - j >= 0) fetch_back(iend - j); else cp_async_commit();
+  }
+  cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
+  auto back_complex = [&](int i) {
+    const char *st = begin(i);
+    const double *row = reinterpret_cast<const double *>(st);
+    const cplx yi = i >= i0 ? ld2(reinterpret_cast<const double *>(st + RING + 16 * lane)) : cmk(0.0, 0.0);
+    const cplx dinv = ld2(row + 2), u1 = ld2(row + 4);
+    cplx x = cfms(cmul(dinv, yi), u1, x1);
+    if (flag(st, i)) x = cfms(x, ld2(row + 6), x2);
+    end_back(i);
+    ystore(i, x);
+    x2 = x1; x1 = x;
+  };
+  auto back_real = [&](int i) {
+    const char *st = begin(i);
+    const double *row = reinterpret_cast<const double *>(st);
+    const cplx yi = i >= i0 ? ld2(reinterpret_cast<const double *>(st + RING + 16 * lane)) : cmk(0.0, 0.0);
+    const double dinv = row[CF ? 2 : 1], u1 = row[CF ? 4 : 2];
+    cplx x = cmk(fma(-u1, x1.re, dinv * yi.re), fma(-u1, x1.im, dinv * yi.im));
+    if (flag(st, i)) {
+      const double u2 = row[CF ? 6 : 3];
+      x.re = fma(-u2, x2.re, x.re);
+      x.im = fma(-u2, x2.im, x.im);
+    }
+    end_back(i);
+    ystore(i, x);
+    x2 = x1; x1 = x;
+  };
+  i = iend;
+  if (CF) for (; i >= rhi; --i) back_complex(i);
+  for (; i >= rlo; --i) back_real(i);
+  if (CF) for (; i >= 0; --i) back_complex(i);
+}
 
 // Staging of the projection sweep: each warp owns TRI_STAGES stages of shared memory and copies
 // the operands of row i + TRI_STAGES while row i is swept. Forward stage: the table row (FSW
@@ -705,16 +768,16 @@ __global__ void __launch_bounds__(32 * TRI_WARPS, 32 / TRI_WARPS) k_tri(Batch bt
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
   const int q = (local / cb) * TRI_WARPS + threadIdx.y + 1;
+  // a warp shares q; its active lanes (columns b < ncols) are lanes 0 .. nact-1
+  extern __shared__ __align__(16) char tri_sm[];
+  const bool act = b < it.ncols && q <= d.Nq;
+  const unsigned mask = __ballot_sync(0xffffffffu, act);
+  if (!act) return;
   if (FULL) {
-    if (b >= it.ncols || q > d.Nq) return;
-    if (d.cplx) tri_body<true, CIN, true>(it, d, tab, pivtab, ws, b, q);
-    else tri_body<false, CIN, true>(it, d, tab, pivtab, ws, b, q);
+    char *sw = tri_sm + threadIdx.y * 2 * full_stage_bytes<CIN>();
+    if (d.cplx) tri_full_body<true, CIN>(it, d, tab, pivtab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
+    else tri_full_body<false, CIN>(it, d, tab, pivtab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
   } else {
-    // a warp shares q; its active lanes (columns b < ncols) are lanes 0 .. nact-1
-    extern __shared__ __align__(16) char tri_sm[];
-    const bool act = b < it.ncols && q <= d.Nq;
-    const unsigned mask = __ballot_sync(0xffffffffu, act);
-    if (!act) return;
     char *sw = tri_sm + threadIdx.y * TRI_STAGES * tri_stage_bytes<CIN>();
     if (d.cplx || CIN) tri_fs_body<true, CIN>(it, d, tab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
     else tri_fs_body<false, CIN>(it, d, tab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
@@ -1378,8 +1441,8 @@ cudaError_t launch_adjoint(mdp_plan *p, const Batch *fb, int out_kind, const dou
     else MDP_LAUNCH(F_RES, k_residual<true, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
     if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
     else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
-    if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true><<<grid1(fb[F_TRI].total_blocks), btri, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
-    else MDP_LAUNCH(F_TRI, k_tri<true, true><<<grid1(fb[F_TRI].total_blocks), btri, 0, st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+    if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true><<<grid1(fb[F_TRI].total_blocks), btri, TRI_WARPS * 2 * full_stage_bytes<false>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+    else MDP_LAUNCH(F_TRI, k_tri<true, true><<<grid1(fb[F_TRI].total_blocks), btri, TRI_WARPS * 2 * full_stage_bytes<true>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
