@@ -286,22 +286,6 @@ __global__ void __launch_bounds__(256) k_fwd_rows(Batch bt, const SubDesc *subs,
 }
 
 // ---------------------------------------------------------------- k_tri
-// Asynchronous global -> shared copies (cp.async): operands of rows ahead are in flight while
-// the current row is swept, without holding registers for them.
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // The gradient pass's forward recompute: per (mode q, column b) the full pivoted LU sweep over
 // every row -- forward elimination with the stored row swaps from matrix row i0 (rows below carry
 // zero right-hand side) to the top, then back substitution down to row 0, every row stored as

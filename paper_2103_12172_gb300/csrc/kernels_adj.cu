@@ -153,13 +153,24 @@ __global__ void __launch_bounds__(256) k_adj_cols(Batch bt, const SubDesc *subs,
 // gamma band carry zero), then the transposed eliminations and row swaps from the top down to
 // row 0. With DK the term Re <muhat, T_q' uhat> is accumulated as rows become final; muhat is
 // kept on the ring rows nlo..nhi (a buffer, rows in matrix numbering).
+// Operands are staged in shared memory by cp.async two rows ahead (sw: the warp's area; the
+// active lanes are 0 .. nact-1): in the forward substitution a ring of 4 factor rows with the
+// words holding their swap flags (row i reads rows i-1 and i-2 too) and 2 stages of right-hand
+// side values; in the back sweep 2 stages of the factor row, the flag word, the stored z~ and
+// the forward field uhat.
+constexpr int ADJ_FR = 80;                      // factor row (<= 64 B) + flag word, per ring slot
+constexpr int ADJ_RV = 5 * 32 * 16;             // right-hand side values [slot][lane], or the back stage
+__host__ __device__ constexpr int adj_warp_smem() { return 4 * ADJ_FR + 2 * ADJ_RV; }
+
 template <bool CF, bool DK>
 __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d, const double *tab,
-                                               const uint8_t *pivtab, double *ws, bool rec, int b, int q) {
+                                               const uint8_t *pivtab, double *ws, bool rec, int b, int q, char *sw,
+                                               int lane, int nact, unsigned mask) {
   constexpr int FW = CF ? 8 : 4;
-  const double *F = tab + d.fact_off + (long long)(q - 1) * d.Nt * FW;
-  const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * d.Nt;
-  auto fl = [&](int i, int w) -> cplx { return CF ? ld2(F + i * FW + 2 * w) : cmk(F[i * FW + w], 0.0); };
+  const int Nt = d.Nt, i0 = d.i0, nfirst = d.nfirst, nlo = d.nlo, nhi = d.nhi, Nq = d.Nq, nrec = d.nrec;
+  const bool xsym = d.xsym;
+  const double *F = tab + d.fact_off + (long long)(q - 1) * Nt * FW;
+  const uint8_t *pv = pivtab + d.piv_off + (long long)(q - 1) * Nt;
   const int N2 = 2 * d.Nx;
   const double *S = tab + d.sin_off;
   const double sg0 = S[(q * (d.mlo - 1)) % N2], sg1 = S[(q * d.mlo) % N2];
@@ -167,80 +178,155 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
   const int nc = it.ncols;
   const double *gr = ws + it.gr_off;
   double *a = ws + it.a_off;
-  const long long abase = (long long)(q - 1) * d.Nt * nc + b;
+  const long long abase = (long long)(q - 1) * Nt * nc + b;
   auto aptr = [&](int i) { return a + 2 * (abase + (long long)i * nc); };
   // middle rows: the cotangent at the 4 gamma columns as gathered by k_adj_cols (column-fastest;
   // (sum, difference) pairs on x-symmetric subdomains: odd q takes the sums, even q the differences)
   const double *cc = ws + it.r_off;
   const int par = (q & 1) ? 0 : 1;
-  auto rhs = [&](int n) -> cplx {
-    if (n < d.nlo - 1 || n > d.nhi + 1) return cmk(0.0, 0.0);
-    const int rr = n == d.nlo - 1 ? 0 : n == d.nlo ? 1 : n == d.nhi ? 2 : n == d.nhi + 1 ? 3 : -1;
-    if (rr >= 0) return ld2(gr + 2 * (((long long)rr * d.Nq + (q - 1)) * nc + b));
-    const long long s0 = 4LL * (n - d.nlo - 1);
-    cplx v = (rec && n == d.nrec) ? ld2(gr + 2 * ((4LL * d.Nq + (q - 1)) * nc + b)) : cmk(0.0, 0.0);
-    if (d.xsym) {
-      v = caxpy(sg0, ld2(cc + 2 * ((s0 + par) * nc + b)), v);
-      v = caxpy(sg1, ld2(cc + 2 * ((s0 + 2 + par) * nc + b)), v);
+  char *fr_ring = sw, *rv = sw + 4 * ADJ_FR;
+  // the factor row and the 4-byte word holding its swap flag (the flag table is 4-byte aligned
+  // and padded to a multiple of 32 bytes, so the word never leaves it)
+  auto fetch_row = [&](char *st, int i) {
+    const double *src = F + (long long)i * FW;
+    if (nact >= FW / 2) {
+      if (lane < FW / 2) cp_async16(st + 16 * lane, src + 2 * lane);
     } else {
-      v = caxpy(sg0, ld2(cc + 2 * (s0 * nc + b)), v);
-      v = caxpy(sg1, ld2(cc + 2 * ((s0 + 1) * nc + b)), v);
-      v = caxpy(sg2, ld2(cc + 2 * ((s0 + 2) * nc + b)), v);
-      v = caxpy(sg3, ld2(cc + 2 * ((s0 + 3) * nc + b)), v);
+      for (int c = lane; c < FW / 2; c += nact) cp_async16(st + 16 * c, src + 2 * c);
+    }
+    if (lane == 0) {
+      const uintptr_t ad = reinterpret_cast<uintptr_t>(pv + i);
+      cp_async4(st + 64, reinterpret_cast<const void *>(ad & ~(uintptr_t)3));
+    }
+  };
+  auto flag = [&](const char *st, int i) -> bool {
+    const unsigned w = *reinterpret_cast<const unsigned *>(st + 64);
+    return ((w >> (8 * (reinterpret_cast<uintptr_t>(pv + i) & 3))) & 0xffu) != 0;
+  };
+  // factor entry w (complex) of a staged row
+  auto flc = [&](const char *st, int w) -> cplx {
+    const double *r = reinterpret_cast<const double *>(st);
+    return CF ? ld2(r + 2 * w) : cmk(r[w], 0.0);
+  };
+  auto flr = [&](const char *st, int w) -> double { return reinterpret_cast<const double *>(st)[CF ? 2 * w : w]; };
+  // ---- forward substitution staging: factor row i, and the right-hand side of grid row i + nfirst
+  auto fetch_fwd = [&](int i) {
+    fetch_row(fr_ring + (i & 3) * ADJ_FR, i);
+    const int n = i + nfirst;
+    if (n >= nlo - 1 && n <= nhi + 1) {
+      char *st = rv + (i & 1) * ADJ_RV + 16 * lane;
+      const int rr = n == nlo - 1 ? 0 : n == nlo ? 1 : n == nhi ? 2 : n == nhi + 1 ? 3 : -1;
+      if (rr >= 0) {
+        cp_async16(st, gr + 2 * (((long long)rr * Nq + (q - 1)) * nc + b));
+      } else {
+        const long long s0 = 4LL * (n - nlo - 1);
+        if (xsym) {
+          cp_async16(st, cc + 2 * ((s0 + par) * nc + b));
+          cp_async16(st + 512, cc + 2 * ((s0 + 2 + par) * nc + b));
+        } else {
+          for (int s_ = 0; s_ < 4; ++s_) cp_async16(st + 512 * s_, cc + 2 * ((s0 + s_) * nc + b));
+        }
+        if (rec && n == nrec) cp_async16(st + 4 * 512, gr + 2 * ((4LL * Nq + (q - 1)) * nc + b));
+      }
+    }
+    cp_async_commit();
+  };
+  auto rhs = [&](int i) -> cplx {
+    const int n = i + nfirst;
+    if (n < nlo - 1 || n > nhi + 1) return cmk(0.0, 0.0);
+    const double *st = reinterpret_cast<const double *>(rv + (i & 1) * ADJ_RV + 16 * lane);
+    const bool dense = n == nlo - 1 || n == nlo || n == nhi || n == nhi + 1;
+    if (dense) return ld2(st);
+    cplx v = (rec && n == nrec) ? ld2(st + 4 * 64) : cmk(0.0, 0.0);
+    if (xsym) {
+      v = caxpy(sg0, ld2(st), v);
+      v = caxpy(sg1, ld2(st + 64), v);
+    } else {
+      v = caxpy(sg0, ld2(st), v);
+      v = caxpy(sg1, ld2(st + 64), v);
+      v = caxpy(sg2, ld2(st + 128), v);
+      v = caxpy(sg3, ld2(st + 192), v);
     }
     return v;
   };
   // Factor rows [rlo, rhi) of a complex mode are exactly real (plan: factor_mode); there the
   // products with the factors are real x complex.
-  int rlo = 0, rhi = d.Nt;
+  int rlo = 0, rhi = Nt;
   if (CF) {
-    const double *sg = tab + d.seg_off + 5 * (q - 1);
-    rlo = (int)sg[0];
-    rhi = (int)sg[1];
+    const double *sgm = tab + d.seg_off + 5 * (q - 1);
+    rlo = (int)sgm[0];
+    rhi = (int)sgm[1];
   }
-  auto fr = [&](int i, int w) -> double { return F[i * FW + (CF ? 2 * w : w)]; };
+  auto begin = [&]() { cp_async_wait<1>(); __syncwarp(mask); };
+  auto end_fwd = [&](int i) {
+    __syncwarp(mask);
+    if (i + 2 < Nt) fetch_fwd(i + 2); else cp_async_commit();
+  };
+  for (int j = 0; j < 2; ++j) {
+    if (i0 + j < Nt) fetch_fwd(i0 + j); else cp_async_commit();
+  }
   // U^H zt = yhat, zt_i = conj(d_i) z_i, from the first nonzero row (i0) up
   cplx t1 = cmk(0.0, 0.0), t2 = cmk(0.0, 0.0);
   auto fstep_c = [&](int i) {
-    cplx v = rhs(i + d.nfirst);
-    if (i - 1 >= d.i0) v = cfms(v, cconj(fl(i - 1, 2)), t1);
-    if (i - 2 >= d.i0 && pv[i - 2]) v = cfms(v, cconj(fl(i - 2, 3)), t2);
-    st2(aptr(i), cmul(cconj(fl(i, 1)), v));
+    begin();
+    const char *r0 = fr_ring + (i & 3) * ADJ_FR, *r1 = fr_ring + ((i - 1) & 3) * ADJ_FR, *r2 = fr_ring + ((i - 2) & 3) * ADJ_FR;
+    cplx v = rhs(i);
+    if (i - 1 >= i0) v = cfms(v, cconj(flc(r1, 2)), t1);
+    if (i - 2 >= i0 && flag(r2, i - 2)) v = cfms(v, cconj(flc(r2, 3)), t2);
+    const cplx z = cmul(cconj(flc(r0, 1)), v);
+    end_fwd(i);
+    st2(aptr(i), z);
     t2 = t1; t1 = v;
   };
   auto fstep_r = [&](int i) {   // rows i-2, i-1, i real
-    cplx v = rhs(i + d.nfirst);
-    if (i - 1 >= d.i0) v = caxpy(-fr(i - 1, 2), t1, v);
-    if (i - 2 >= d.i0 && pv[i - 2]) v = caxpy(-fr(i - 2, 3), t2, v);
-    const double di = fr(i, 1);
+    begin();
+    const char *r0 = fr_ring + (i & 3) * ADJ_FR, *r1 = fr_ring + ((i - 1) & 3) * ADJ_FR, *r2 = fr_ring + ((i - 2) & 3) * ADJ_FR;
+    cplx v = rhs(i);
+    if (i - 1 >= i0) v = caxpy(-flr(r1, 2), t1, v);
+    if (i - 2 >= i0 && flag(r2, i - 2)) v = caxpy(-flr(r2, 3), t2, v);
+    const double di = flr(r0, 1);
+    end_fwd(i);
     st2(aptr(i), cmk(di * v.re, di * v.im));
     t2 = t1; t1 = v;
   };
   {
-    int i = d.i0;
-    if (CF) for (const int e = min(max(rlo + 2, i), d.Nt); i < e; ++i) fstep_c(i);
-    for (const int e = CF ? max(rhi, i) : d.Nt; i < e; ++i) fstep_r(i);
-    for (; i < d.Nt; ++i) fstep_c(i);
+    int i = i0;
+    if (CF) for (const int e = min(max(rlo + 2, i), Nt); i < e; ++i) fstep_c(i);
+    for (const int e = CF ? max(rhi, i) : Nt; i < e; ++i) fstep_r(i);
+    for (; i < Nt; ++i) fstep_c(i);
   }
+  // the stored z~ are read back below by this thread's asynchronous copies: order them after
+  // its stores
+  __threadfence_block();
   // z = P_0 E_0^H ... P_{N-2} E_{N-2}^H z; position i+1 is final after step i
-  const double *dT = tab + d.dT_off + (long long)(q - 1) * d.Nt * 6;
+  const double *dT = tab + d.dT_off + (long long)(q - 1) * Nt * 6;
   const double *y = ws + it.y_off;
-  const long long ybase = (long long)(q - 1) * d.Nt * nc + b;
-  auto uhat = [&](int i) -> cplx {
-    if (i < 0 || i >= d.Nt) return cmk(0.0, 0.0);
-    return ld2(y + 2 * (ybase + (long long)i * nc));
+  const long long ybase = (long long)(q - 1) * Nt * nc + b;
+  // ---- back sweep staging (rows Nt-2 .. 0): factor row, flag word, z~ (rows >= i0) and, with
+  // DK, uhat of the same row
+  auto bst = [&](int i) -> char * { return rv + (i & 1) * ADJ_RV; };
+  auto fetch_back = [&](int i) {
+    char *st = bst(i);
+    fetch_row(st, i);
+    if (i >= i0) cp_async16(st + 80 + 16 * lane, aptr(i));
+    if (DK) cp_async16(st + 80 + 512 + 16 * lane, y + 2 * (ybase + (long long)i * nc));
+    cp_async_commit();
+  };
+  auto end_back = [&](int i) {
+    __syncwarp(mask);
+    if (i - 2 >= 0) fetch_back(i - 2); else cp_async_commit();
   };
   // Re <muhat, T_q' uhat>: T_q' is (da, ddk, da) with real constants on rows 1 .. Nt-2 (the
   // k-derivatives of the interior coefficients), so those rows accumulate
   // s_off = sum Re conj(mu_j)(u_{j-1} + u_{j+1}) and s_dg = sum Re conj(mu_j) u_j; the two end
   // rows (Sommerfeld or Dirichlet) take their tabulated entries.
   double dk = 0.0, s_off = 0.0, s_dg = 0.0;
-  cplx uj1 = cmk(0.0, 0.0), uj = DK ? uhat(d.Nt - 1) : cmk(0.0, 0.0);
-  const int jlo = d.nlo - d.nfirst, jhi = d.nhi - d.nfirst;
-  auto emit = [&](int j, cplx mu) {
+  cplx uj1 = cmk(0.0, 0.0), uj = DK ? ld2(y + 2 * (ybase + (long long)(Nt - 1) * nc)) : cmk(0.0, 0.0);
+  const int jlo = nlo - nfirst, jhi = nhi - nfirst;
+  // ujm: uhat(j - 1)
+  auto emit = [&](int j, cplx mu, cplx ujm) {
     if (DK) {
-      const cplx ujm = uhat(j - 1);
-      if (j == 0 || j == d.Nt - 1) {
+      if (j == 0 || j == Nt - 1) {
         const double *t = dT + 6 * j;
         cplx v = cmul(ld2(t), ujm);
         v = cadd(v, cmul(ld2(t + 2), uj));
@@ -254,27 +340,29 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
     }
     if (j >= jlo && j <= jhi) st2(aptr(j), mu);
   };
-  cplx up = ld2(aptr(d.Nt - 1));
-  auto bstep_c = [&](int i) {
-    const cplx zi0 = i >= d.i0 ? ld2(aptr(i)) : cmk(0.0, 0.0);
-    const cplx zi = cfms(zi0, cconj(fl(i, 0)), up);
-    if (pv[i]) emit(i + 1, zi);
-    else { emit(i + 1, up); up = zi; }
-  };
-  auto bstep_r = [&](int i) {
-    const cplx zi0 = i >= d.i0 ? ld2(aptr(i)) : cmk(0.0, 0.0);
-    const cplx zi = caxpy(-fr(i, 0), up, zi0);
-    if (pv[i]) emit(i + 1, zi);
-    else { emit(i + 1, up); up = zi; }
+  cplx up = ld2(aptr(Nt - 1));
+  for (int j = 0; j < 2; ++j) {
+    if (Nt - 2 - j >= 0) fetch_back(Nt - 2 - j); else cp_async_commit();
+  }
+  auto bstep = [&](int i, bool complex_row) {
+    begin();
+    const char *st = bst(i);
+    const cplx zi0 = i >= i0 ? ld2(reinterpret_cast<const double *>(st + 80 + 16 * lane)) : cmk(0.0, 0.0);
+    const cplx ujm = DK ? ld2(reinterpret_cast<const double *>(st + 80 + 512 + 16 * lane)) : cmk(0.0, 0.0);
+    const cplx zi = complex_row ? cfms(zi0, cconj(flc(st, 0)), up) : caxpy(-flr(st, 0), up, zi0);
+    const bool swp = flag(st, i);
+    end_back(i);
+    if (swp) emit(i + 1, zi, ujm);
+    else { emit(i + 1, up, ujm); up = zi; }
   };
   {
-    int i = d.Nt - 2;
-    if (CF) for (; i >= rhi; --i) bstep_c(i);
-    for (const int e = CF ? rlo : 0; i >= e; --i) bstep_r(i);
-    for (; i >= 0; --i) bstep_c(i);
+    int i = Nt - 2;
+    if (CF) for (; i >= rhi; --i) bstep(i, true);
+    for (const int e = CF ? rlo : 0; i >= e; --i) bstep(i, false);
+    for (; i >= 0; --i) bstep(i, true);
   }
-  emit(0, up);
-  if (DK && d.Nt >= 3) dk = fma(dT[6 + 0], s_off, fma(dT[6 + 2], s_dg, dk));
+  emit(0, up, cmk(0.0, 0.0));
+  if (DK && Nt >= 3) dk = fma(dT[6 + 0], s_off, fma(dT[6 + 2], s_dg, dk));
   return dk;
 }
 
@@ -282,16 +370,23 @@ template <bool DK>
 __global__ void __launch_bounds__(128, 7) k_adj_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
                                                  double *ws, int has_rec) {
   __shared__ double sh[128];
+  extern __shared__ __align__(16) char adj_sm[];
   Item it; int local;
   locate(bt, bt.order ? bt.order[blockIdx.x] : (int)blockIdx.x, it, local);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
   const int q = (local / cb) * 4 + threadIdx.y + 1;
+  const bool act = b < it.ncols && q <= d.Nq;
+  const unsigned mask = __ballot_sync(0xffffffffu, act);   // a warp shares q; its active lanes are 0 .. nact-1
   double dk = 0.0;
-  if (b < it.ncols && q <= d.Nq)
-    dk = d.cplx ? adj_tri_body<true, DK>(it, d, tab, pivtab, ws, has_rec && d.nrec >= 0, b, q)
-                : adj_tri_body<false, DK>(it, d, tab, pivtab, ws, has_rec && d.nrec >= 0, b, q);
+  if (act) {
+    char *sw = adj_sm + threadIdx.y * adj_warp_smem();
+    dk = d.cplx ? adj_tri_body<true, DK>(it, d, tab, pivtab, ws, has_rec && d.nrec >= 0, b, q, sw, threadIdx.x,
+                                         __popc(mask), mask)
+                : adj_tri_body<false, DK>(it, d, tab, pivtab, ws, has_rec && d.nrec >= 0, b, q, sw, threadIdx.x,
+                                          __popc(mask), mask);
+  }
   if (DK) {
     const double s = block_sum<128>(dk * (2.0 / d.Nx), sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) ws[it.red_off + local] = s;   // slot base 0: k_adj_tri
@@ -577,8 +672,8 @@ cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, cons
   } while (0)
   ADJ_LAUNCH(F_AFWD, k_adj_rows<<<g1(fb[F_AFWD].total_blocks), b8, p->fft_smem, st>>>(fb[F_AFWD], ds, tab, ws, cot, cot_rec));
   ADJ_LAUNCH(F_ACOLS, k_adj_cols<<<g1(fb[F_ACOLS].total_blocks), b8, 0, st>>>(fb[F_ACOLS], ds, ws, cot));
-  if (dk) ADJ_LAUNCH(F_ATRI, k_adj_tri<true><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot_rec ? 1 : 0));
-  else ADJ_LAUNCH(F_ATRI, k_adj_tri<false><<<g1(fb[F_ATRI].total_blocks), b4, 0, st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot_rec ? 1 : 0));
+  if (dk) ADJ_LAUNCH(F_ATRI, k_adj_tri<true><<<g1(fb[F_ATRI].total_blocks), b4, 4 * adj_warp_smem(), st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot_rec ? 1 : 0));
+  else ADJ_LAUNCH(F_ATRI, k_adj_tri<false><<<g1(fb[F_ATRI].total_blocks), b4, 4 * adj_warp_smem(), st>>>(fb[F_ATRI], ds, tab, p->d_piv, ws, cot_rec ? 1 : 0));
   if (dk) {
     ADJ_LAUNCH(F_ARING, k_adj_ring_rows<true><<<g1(fb[F_ARING].total_blocks), b8, p->fft_smem, st>>>(fb[F_ARING], ds, tab, ws));
     ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<true><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));

@@ -26,6 +26,23 @@ __device__ __forceinline__ cplx ld2(const double *p) {
 }
 __device__ __forceinline__ void st2(double *p, cplx v) { *reinterpret_cast<double2 *>(p) = make_double2(v.re, v.im); }
 
+// ---------------------------------------------------------------- asynchronous copies
+// Asynchronous global -> shared copies (cp.async): operands of rows ahead are in flight while
+// the current row is swept, without holding registers for them.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // ---------------------------------------------------------------- batch addressing
 __device__ __forceinline__ void locate(const Batch &b, int blk, Item &it, int &local) {
   if (b.items == nullptr) { it = b.one; local = blk; return; }
