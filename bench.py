@@ -364,22 +364,24 @@ def run_ours(args, wl):
 
     # end to end through the public API with host buffers: new wavenumbers from host memory
     # (every mode refactored on the GPU), all columns, every step's result read back to pinned
-    # host memory. The read-back of step i runs on a copy stream while step i+1 refactors and
-    # projects on the compute stream (two output buffers, so step i+1 never overwrites columns
-    # still being copied); the timed region ends when the last copy has landed.
+    # host memory. Three streams form a pipeline: step i+1's upload and refactorisation run on
+    # a factor stream into the plan's second table set (mdp_plan_update_k_async) while step i
+    # projects on the compute stream, and step i's read-back runs on a copy stream (two output
+    # buffers, so a projection never overwrites columns still being copied); the timed region
+    # ends when the last copy has landed.
     host_out = [torch.empty(plan.output_size, dtype=torch.complex128, pin_memory=True) for _ in range(2)]
     outs = [out, torch.empty_like(out)]
-    cs, xs = torch.cuda.Stream(), torch.cuda.Stream()
+    cs, xs, fs = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     copied = [None, None]
     ks = [s.k for s in subs]
     e2e_steps = max(3, min(args.steps, 10))
 
     def e2e_step(i):
         b = i % 2
-        plan.update_k([k * (1.0 + 1e-9 * (i + 1)) for k in ks], stream=cs)
+        plan.update_k_async([k * (1.0 + 1e-9 * (i + 1)) for k in ks], stream=fs)
         if copied[b] is not None:
             cs.wait_event(copied[b])             # the copy of step i-2 has left outs[b]
-        plan.project(out=outs[b], stream=cs)
+        plan.project(out=outs[b], stream=cs)     # waits for step i's tables
         done = torch.cuda.Event()
         done.record(cs)
         xs.wait_event(done)
@@ -396,12 +398,14 @@ def run_ours(args, wl):
         e2e_step(i)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
+    plan.status()                                # no step met a singular mode
     plan.update_k(ks)
     update_bytes = int(plan.L.mdp_plan_update_bytes(plan.handle))
     e2e = {"value": world * n_cols * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": update_bytes,
            "d2h_bytes_per_step": int(plan.output_size * 16),
            "what": "update_k (new k up, every mode refactored on the GPU) + project + D2H of all columns "
-                   "to pinned host memory; the D2H of step i overlaps step i+1 (copy stream, two buffers)"}
+                   "to pinned host memory; pipelined: step i+1's update and refactorisation (second table set) "
+                   "and step i's D2H overlap step i's projection"}
 
     # the same step replayed as one CUDA graph (library graph mode)
     gplan = mdp.Plan(subs, tile_cols=tile, graph=True)

@@ -119,6 +119,17 @@ mdp_status mdp_ap_plan_ex(const mdp_subdomain *subs, int n_subs, unsigned flags,
 mdp_status mdp_plan_update_k(mdp_plan *p, const double *k);
 mdp_status mdp_plan_update_k_stream(mdp_plan *p, const double *k, void *cuda_stream);
 
+/* The same refactorisation without waiting for it, so that it overlaps work already queued on
+ * other streams (a sweep over k: the factorisation for the next k runs while the projection of
+ * the current one does). A device plan keeps a second table set (allocated by the first call,
+ * as large as the first): the new tables are built into the set no queued call is reading, on
+ * cuda_stream, after the compute calls that last read that set; calls made after this one, on
+ * any stream, wait for the new tables and use them. The call returns at once (it may wait on the
+ * host for the upload of two calls earlier). A singular mode sets the sticky status word
+ * (mdp_plan_status: MDP_ERR_SINGULAR) instead of being returned. Host-only plans: as
+ * mdp_plan_update_k. */
+mdp_status mdp_plan_update_k_async(mdp_plan *p, const double *k, void *cuda_stream);
+
 /* leader[i] (host array of n_subs ints): the subdomain whose tables (and, for basis columns,
  * computed block) subdomain i shares; i itself unless MDP_PLAN_DEDUPE found an earlier
  * identical subdomain. */

@@ -277,6 +277,14 @@ class Plan:
         st = None if self.host_only else _stream_ptr(stream)
         _lib.check(self.L.mdp_plan_update_k_stream(self.handle, arr, st), "mdp_plan_update_k_stream")
 
+    def update_k_async(self, ks, stream=None):
+        """New wavenumbers without waiting: the modes are refactored on `stream` (default the
+        current torch stream) into a second table set, overlapping work queued on other streams;
+        later calls on any stream wait for the new tables. A singular mode shows in status()."""
+        arr = (C.c_double * self.n_subs)(*[float(k) for k in ks])
+        st = None if self.host_only else _stream_ptr(stream)
+        _lib.check(self.L.mdp_plan_update_k_async(self.handle, arr, st), "mdp_plan_update_k_async")
+
     def leaders(self) -> list:
         """Per subdomain, the subdomain whose tables and basis columns it shares (dedupe)."""
         a = (C.c_int * self.n_subs)()

@@ -55,6 +55,7 @@ def lib():
         "mdp_ap_plan_ex": (i, [C.POINTER(mdp_subdomain), i, C.c_uint, C.POINTER(mdp_plan_options), C.POINTER(vp)]),
         "mdp_plan_update_k": (i, [vp, C.POINTER(d)]),
         "mdp_plan_update_k_stream": (i, [vp, C.POINTER(d), vp]),
+        "mdp_plan_update_k_async": (i, [vp, C.POINTER(d), vp]),
         "mdp_plan_table_sizes": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
         "mdp_plan_update_bytes": (ll, [vp]),
         "mdp_plan_leaders": (i, [vp, C.POINTER(i)]),

@@ -38,6 +38,17 @@ void free_device(mdp_plan *p) {
   p->d_fstatus = nullptr;
   p->sub_stage.release();
   p->h_fstatus.release();
+  cudaFree(p->alt_subs);
+  cudaFree(p->alt_tables);
+  cudaFree(p->alt_piv);
+  p->alt_subs = nullptr; p->alt_tables = nullptr; p->alt_piv = nullptr;
+  p->alt_stage.release();
+  for (int s_ = 0; s_ < 2; ++s_) {
+    if (p->ready_ev[s_]) cudaEventDestroy(p->ready_ev[s_]);
+    if (p->used_ev[s_]) cudaEventDestroy(p->used_ev[s_]);
+    p->ready_ev[s_] = p->used_ev[s_] = nullptr;
+    p->used_rec[s_] = false;
+  }
   for (int k = 0; k < 3; ++k) {
     for (auto x : p->d_items[k]) cudaFree(x);
     for (auto x : p->d_prefix[k]) cudaFree(x);
@@ -150,6 +161,24 @@ void single_batches(const mdp_plan *p, const Item &it, Batch *fb) {
 
 bool device_ok(const mdp_plan *p) { return p && !(p->flags & MDP_PLAN_HOST_ONLY) && p->device >= 0; }
 
+// Around every compute call once a second table set exists: wait for the refactorisation of the
+// set in use, and afterwards mark the set as read by work queued on st (chained to its earlier
+// readers, so that one event covers them all).
+cudaError_t begin_use(const mdp_plan *p, cudaStream_t st) {
+  if (!p->ready_ev[p->set]) return cudaSuccess;
+  return cudaStreamWaitEvent(st, p->ready_ev[p->set], 0);
+}
+cudaError_t end_use(mdp_plan *p, cudaStream_t st) {
+  if (!p->used_ev[p->set]) return cudaSuccess;
+  if (p->used_rec[p->set]) {
+    const cudaError_t e = cudaStreamWaitEvent(st, p->used_ev[p->set], 0);
+    if (e != cudaSuccess) return e;
+  }
+  p->used_rec[p->set] = true;
+  return cudaEventRecord(p->used_ev[p->set], st);
+}
+mdp::HostBuf<SubDesc> &stage_of(mdp_plan *p, int set) { return set == 0 ? p->sub_stage : p->alt_stage; }
+
 void destroy_prof(mdp_plan *p) {
   for (int f = 0; f < 16; ++f) {
     for (auto &e : p->prof_ev[f]) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -243,14 +272,57 @@ mdp_status mdp_plan_update_k_stream(mdp_plan *p, const double *k, void *cuda_str
   CK(cudaSetDevice(p->device));
   cudaStream_t s = (cudaStream_t)cuda_stream;
   CK(cudaStreamSynchronize(s));   // the stage may still feed an upload of an earlier call
-  for (size_t i = 0; i < p->subs.size(); ++i) p->sub_stage[i] = p->subs[i].d;
-  CK(cudaMemcpyAsync(p->d_subs, p->sub_stage.data(), p->subs.size() * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
+  if (p->ready_ev[p->set]) CK(cudaEventSynchronize(p->ready_ev[p->set]));
+  if (p->used_rec[p->set]) CK(cudaStreamWaitEvent(s, p->used_ev[p->set], 0));   // readers on other streams
+  HostBuf<SubDesc> &stage = stage_of(p, p->set);
+  for (size_t i = 0; i < p->subs.size(); ++i) stage[i] = p->subs[i].d;
+  CK(cudaMemcpyAsync(p->d_subs, stage.data(), p->subs.size() * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(p->d_fstatus, 0, sizeof(int), s));
   CK(launch_factor(p, p->d_fstatus, s));
   CK(cudaMemcpyAsync(p->h_fstatus.data(), p->d_fstatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (p->ready_ev[p->set]) CK(cudaEventRecord(p->ready_ev[p->set], s));
   CK(cudaStreamSynchronize(s));
   p->host_stale = true;
   return (mdp_status)p->h_fstatus[0];
+}
+
+// The refactorisation into the other table set, then the sets swap roles (see include/mdp.h).
+mdp_status mdp_plan_update_k_async(mdp_plan *p, const double *k, void *cuda_stream) {
+  if (!p || !k) return MDP_ERR_ARG;
+  if (!device_ok(p)) return refactor_host(p, k);
+  mdp_status st = set_k_fields(p, k);
+  if (st != MDP_OK) return st;
+  CK(cudaSetDevice(p->device));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (!p->alt_tables) {   // first call: the second set starts as a copy of the first (k-independent tables)
+    const size_t nt = std::max<size_t>(p->host_tables.size() * sizeof(double), 256);
+    const size_t np = std::max<size_t>(p->host_piv.size(), 256);
+    const size_t ns = std::max<size_t>(p->subs.size() * sizeof(SubDesc), 256);
+    if (cudaMalloc((void **)&p->alt_tables, nt) != cudaSuccess || cudaMalloc((void **)&p->alt_piv, np) != cudaSuccess ||
+        cudaMalloc((void **)&p->alt_subs, ns) != cudaSuccess || !p->alt_stage.alloc(p->subs.size(), true))
+      return MDP_ERR_NOMEM;
+    for (int s_ = 0; s_ < 2; ++s_) {
+      CK(cudaEventCreateWithFlags(&p->ready_ev[s_], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&p->used_ev[s_], cudaEventDisableTiming));
+    }
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(p->alt_tables, p->d_tables, nt, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(p->alt_piv, p->d_piv, np, cudaMemcpyDeviceToDevice));
+  }
+  const int b = 1 - p->set;
+  HostBuf<SubDesc> &stage = stage_of(p, b);
+  CK(cudaEventSynchronize(p->ready_ev[b]));   // the stage fed the upload of the last refactorisation into set b
+  if (p->used_rec[b]) CK(cudaStreamWaitEvent(s, p->used_ev[b], 0));   // queued calls still reading set b
+  for (size_t i = 0; i < p->subs.size(); ++i) stage[i] = p->subs[i].d;
+  CK(cudaMemcpyAsync(p->alt_subs, stage.data(), p->subs.size() * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
+  CK(launch_factor_to(p, p->alt_subs, p->alt_tables, p->alt_piv, p->d_status, s));
+  CK(cudaEventRecord(p->ready_ev[b], s));
+  std::swap(p->d_subs, p->alt_subs);
+  std::swap(p->d_tables, p->alt_tables);
+  std::swap(p->d_piv, p->alt_piv);
+  p->set = b;
+  p->host_stale = true;
+  return MDP_OK;
 }
 
 // The host tables are a cache of the device ones for introspection: rebuilt for the current
@@ -329,6 +401,7 @@ mdp_status mdp_project_batch_rec(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, m
   if (xi && (const void *)xi == (const void *)out) return MDP_ERR_ARG;
   CK(cudaSetDevice(p->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(begin_use(p, st));
   // basis columns without receivers: with duplicates, only the distinct subdomains are solved
   // and their blocks copied to the duplicates
   const bool dedupe = !xi && !out_rec && !p->sched[S_BASIS].empty();
@@ -353,12 +426,14 @@ mdp_status mdp_project_batch_rec(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, m
   };
   if (!(p->flags & MDP_PLAN_GRAPH) || st == nullptr) {
     CK(launch_all());
+    CK(end_use(p, st));
     return MDP_OK;
   }
   for (auto &g : p->graphs)
     if (g.xi == (const void *)xi && g.out == (void *)out && g.out_rec == (void *)out_rec && g.kind == out_kind &&
-        g.st == st) {
+        g.st == st && g.tab == p->d_tables) {
       CK(cudaGraphLaunch(g.exec, st));
+      CK(end_use(p, st));
       return MDP_OK;
     }
   // capture every launch of this call into one graph
@@ -381,8 +456,9 @@ mdp_status mdp_project_batch_rec(mdp_plan *p, const mdp_c64 *xi, mdp_c64 *out, m
     cudaGraphExecDestroy(p->graphs.front().exec);
     p->graphs.erase(p->graphs.begin());
   }
-  p->graphs.push_back({(const void *)xi, (void *)out, (void *)out_rec, out_kind, st, exec});
+  p->graphs.push_back({(const void *)xi, (void *)out, (void *)out_rec, out_kind, st, p->d_tables, exec});
   CK(cudaGraphLaunch(exec, st));
+  CK(end_use(p, st));
   return MDP_OK;
 }
 
@@ -394,6 +470,7 @@ mdp_status mdp_project_columns(mdp_plan *p, int sub, int col0, int ncols, const 
   if (!device_ok(p)) return MDP_ERR_STATE;
   CK(cudaSetDevice(p->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(begin_use(p, st));
   for (int c = 0; c < ncols; c += p->tile_cols) {
     Item it;
     std::memset(&it, 0, sizeof it);
@@ -406,6 +483,7 @@ mdp_status mdp_project_columns(mdp_plan *p, int sub, int col0, int ncols, const 
     single_batches(p, it, fb);
     CK(launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, nullptr, st));
   }
+  CK(end_use(p, st));
   return MDP_OK;
 }
 
@@ -414,7 +492,10 @@ mdp_status mdp_potential(mdp_plan *p, int sub, int ncols, const mdp_c64 *xi, mdp
   if (!device_ok(p)) return MDP_ERR_STATE;
   if ((const void *)xi == (const void *)u) return MDP_ERR_ARG;
   CK(cudaSetDevice(p->device));
-  CK(launch_potential(p, sub, ncols, (const double2 *)xi, (double2 *)u, (cudaStream_t)cuda_stream));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(begin_use(p, st));
+  CK(launch_potential(p, sub, ncols, (const double2 *)xi, (double2 *)u, st));
+  CK(end_use(p, st));
   return MDP_OK;
 }
 
@@ -424,10 +505,13 @@ mdp_status mdp_source_terms(mdp_plan *p, int sub, const mdp_c64 *f, const mdp_c6
   if ((const void *)f == (const void *)u) return MDP_ERR_ARG;
   if (!device_ok(p)) return MDP_ERR_STATE;
   CK(cudaSetDevice(p->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(begin_use(p, st));
   const cudaError_t e = launch_source_terms(p, sub, (const double2 *)f, (const double2 *)src4, (double2 *)F,
-                                            (double2 *)u, (cudaStream_t)cuda_stream);
+                                            (double2 *)u, st);
   if (e == cudaErrorMemoryAllocation) return MDP_ERR_NOMEM;
   CK(e);
+  CK(end_use(p, st));
   return MDP_OK;
 }
 
@@ -437,7 +521,10 @@ mdp_status mdp_basis_densities(mdp_plan *p, int sub, int col0, int ncols, mdp_c6
   if (col0 < 0 || ncols < 1 || col0 + ncols > d.n_cols) return MDP_ERR_ARG;
   if (!device_ok(p)) return MDP_ERR_STATE;
   CK(cudaSetDevice(p->device));
-  CK(launch_basis_densities(p, sub, col0, ncols, (double2 *)out, (cudaStream_t)cuda_stream));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(begin_use(p, st));
+  CK(launch_basis_densities(p, sub, col0, ncols, (double2 *)out, st));
+  CK(end_use(p, st));
   return MDP_OK;
 }
 
@@ -455,12 +542,14 @@ mdp_status mdp_ap_adjoint_rec(mdp_plan *p, const mdp_c64 *xi, const mdp_c64 *cot
     return MDP_ERR_ARG;
   CK(cudaSetDevice(p->device));
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(begin_use(p, st));
   for (size_t w = 0; w < p->sched[S_GRAD].size(); ++w) {
     Batch fb[NFAM];
     wave_batches(p, w, fb, S_GRAD);
     CK(launch_adjoint(p, fb, out_kind, (const double2 *)xi, (const double2 *)cot, (const double2 *)cot_rec,
                       (double2 *)grad_xi, grad_k, st));
   }
+  CK(end_use(p, st));
   return MDP_OK;
 }
 
@@ -471,7 +560,10 @@ mdp_status mdp_ap_solve_batch(mdp_plan *p, int sub, int nrhs, const mdp_c64 *g, 
   if (!device_ok(p)) return MDP_ERR_STATE;
   if (nrhs == 0) return MDP_OK;
   CK(cudaSetDevice(p->device));
-  CK(launch_solve(p, sub, nrhs, (const double2 *)g, (double2 *)u, adjoint, (cudaStream_t)cuda_stream));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  CK(begin_use(p, st));
+  CK(launch_solve(p, sub, nrhs, (const double2 *)g, (double2 *)u, adjoint, st));
+  CK(end_use(p, st));
   return MDP_OK;
 }
 

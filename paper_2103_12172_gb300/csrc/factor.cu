@@ -414,13 +414,17 @@ __global__ void k_probe_rcp(const double *x, double *y, int n) {
 // The chains: one thread each, warps spread one per block so that they do not share an SM's
 // FP64 unit while there are fewer warps than SMs. The row kernel: one block per mode.
 cudaError_t launch_factor(const mdp_plan *p, int *status, cudaStream_t st) {
+  return launch_factor_to(p, p->d_subs, p->d_tables, p->d_piv, status, st);
+}
+
+cudaError_t launch_factor_to(const mdp_plan *p, const SubDesc *ds, double *tab, uint8_t *piv, int *status,
+                             cudaStream_t st) {
   int n_modes = 0;
   for (size_t i = 0; i < p->subs.size(); ++i)
     if (p->subs[i].d.leader == (int)i) n_modes += p->subs[i].d.Nq;
   const int threads = 2 * n_modes;
-  k_factor_chain<<<(threads + 31) / 32, 32, 0, st>>>(p->d_subs, (int)p->subs.size(), n_modes, p->d_tables,
-                                                      p->d_piv, status);
-  k_factor_rows<<<n_modes, kRowsThreads, 0, st>>>(p->d_subs, (int)p->subs.size(), p->d_tables);
+  k_factor_chain<<<(threads + 31) / 32, 32, 0, st>>>(ds, (int)p->subs.size(), n_modes, tab, piv, status);
+  k_factor_rows<<<n_modes, kRowsThreads, 0, st>>>(ds, (int)p->subs.size(), tab);
   return cudaGetLastError();
 }
 

@@ -167,13 +167,26 @@ struct mdp_plan {
   mdp::HostBuf<mdp::SubDesc> sub_stage;  // pinned copy of the subdomain descriptors (async upload)
   mdp::HostBuf<int> h_fstatus;           // pinned read-back of d_fstatus
   bool host_stale = false;               // device tables refactored since the host tables were built
+  // second table set of mdp_plan_update_k_async (allocated by its first call). d_subs, d_tables
+  // and d_piv name physical set `set`; the alt_* pointers the other. ready_ev[s]: after the last
+  // refactorisation into set s; used_ev[s]: after the last compute call that read it.
+  mdp::SubDesc *alt_subs = nullptr;
+  double *alt_tables = nullptr;
+  uint8_t *alt_piv = nullptr;
+  mdp::HostBuf<mdp::SubDesc> alt_stage;  // pinned descriptor stage of set 1 (sub_stage: set 0)
+  int set = 0;
+  cudaEvent_t ready_ev[2] = {nullptr, nullptr};
+  cudaEvent_t used_ev[2] = {nullptr, nullptr};
+  bool used_rec[2] = {false, false};
   // per schedule and wave: device items and prefix arrays (one prefix array per kernel family)
   std::vector<mdp::Item *> d_items[3];
   std::vector<int *> d_order[3];         // [wave] -> device int [k_tri + k_adj_tri blocks]: launch orders
   std::vector<int *> d_prefix[3];        // [wave] -> device int [NFAM][n_items + 1]
   std::vector<std::vector<int>> h_prefix[3];
-  // CUDA graphs of mdp_project_batch, keyed by (xi, out, kind, stream)
-  struct GraphEntry { const void *xi; void *out; void *out_rec; int kind; cudaStream_t st; cudaGraphExec_t exec; };
+  // CUDA graphs of mdp_project_batch, keyed by (xi, out, kind, stream, table set)
+  struct GraphEntry {
+    const void *xi; void *out; void *out_rec; int kind; cudaStream_t st; const double *tab; cudaGraphExec_t exec;
+  };
   std::vector<GraphEntry> graphs;
   // per-kernel event timing (mdp_plan_profile)
   bool prof_on = false;
@@ -236,6 +249,9 @@ mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n);
 mdp_status refactor_host(mdp_plan *p, const double *k);
 mdp_status set_k_fields(mdp_plan *p, const double *k);   // validate k, update the k-dependent SubDesc fields
 cudaError_t launch_factor(const mdp_plan *p, int *status, cudaStream_t st);   // factor.cu
+// the same into an explicit table set (descriptors ds, tables tab, pivot flags piv)
+cudaError_t launch_factor_to(const mdp_plan *p, const SubDesc *ds, double *tab, uint8_t *piv, int *status,
+                             cudaStream_t st);
 void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long long &r, long long &gr,
                     long long &y, long long &a, long long &s, long long &red, long long &total);
 void host_mode_solve(const HostSub &hs, int q, int adjoint, const double *b, double *x);

@@ -120,3 +120,52 @@ def test_factor_reciprocal_is_accurate_to_an_ulp(mdp):
     r = 1.0 / x                                   # correctly rounded
     ulps = np.abs(y - r) / np.spacing(r)
     assert ulps.max() <= 2.0, ulps.max()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_async_updates_overlap_and_match_synchronous_ones(mdp, graph):
+    """mdp_plan_update_k_async: a sweep over k with each refactorisation queued on its own stream
+    while the previous projection still runs on another (two table sets). Every step's columns
+    equal those of a plan refactored synchronously to the same k, bit for bit; with a graph plan
+    the captured graphs follow the table set in use; the gradient after an async update is that of
+    the synchronous plan; a singular k shows in the status word."""
+    from paper_2103_12172_gb300 import MdpError
+    subs = [W.small_subdomain(65, 11.0, W.AP_DIRX_SOMMY, 3), W.small_subdomain(65, 9.0, W.AP_DIRICHLET4, 2)]
+    ks = [[11.0, 9.0], [12.5, 9.75], [10.25, 8.5], [13.0, 10.5], [11.75, 9.25]]
+    ref = mdp.Plan(subs, tile_cols=32)
+    want = []
+    for k in ks:
+        ref.update_k(k)
+        want.append(ref.project().cpu().numpy())
+    plan = mdp.Plan(subs, tile_cols=32, graph=graph)
+    fs, cs = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [torch.empty(plan.output_size, dtype=torch.complex128, device="cuda") for _ in ks]
+    for i, k in enumerate(ks):
+        plan.update_k_async(k, stream=fs)          # queued behind nothing on fs: overlaps step i-1 on cs
+        plan.project(out=outs[i], stream=cs)
+    torch.cuda.synchronize()
+    plan.status()
+    for o, w in zip(outs, want):
+        assert np.array_equal(o.cpu().numpy(), w)
+    # a synchronous update after async ones, then the gradient equals the reference's
+    plan.update_k(ks[2])
+    ref.update_k(ks[2])
+    cot = torch.from_numpy(W.random_complex(plan.output_size, seed=5)).cuda()
+    g1, k1 = plan.adjoint(cot)
+    g2, k2 = ref.adjoint(cot)
+    assert torch.equal(g1, g2) and torch.equal(k1, k2)
+    # a singular k (a discrete Dirichlet eigenvalue of the second subdomain) is reported late
+    n, nc = 65, 64
+    h = 1.2 / nc
+    lp, lq = -4 * np.sin(np.pi * np.array([2, 3]) / (2 * nc)) ** 2
+    kres = float(np.sqrt(-((lp + lq) / h**2 + lp * lq / (6 * h**2)) / (1 + (lp + lq) / 12)))
+    plan.update_k_async([11.0, kres], stream=fs)
+    torch.cuda.synchronize()
+    with pytest.raises(MdpError) as e:
+        plan.status()
+    assert e.value.code == 4  # MDP_ERR_SINGULAR
+    plan.update_k_async(ks[0], stream=fs)
+    plan.project(out=outs[0], stream=cs)
+    torch.cuda.synchronize()
+    plan.status()
+    assert np.array_equal(outs[0].cpu().numpy(), want[0])

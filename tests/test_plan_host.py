@@ -159,6 +159,12 @@ def test_host_refactor_equals_fresh_plan_and_table_readback(mdp):
     with pytest.raises(MdpError) as e:
         p1.read_tables(True)
     assert e.value.code == 6  # MDP_ERR_STATE
+    # on a host-only plan the asynchronous update is the synchronous one
+    p3 = mdp.Plan([sub], host_only=True)
+    p3.update_k_async([8.5])
+    t3, v3 = p3.read_tables(False)
+    np.testing.assert_array_equal(v3, v2)
+    np.testing.assert_array_equal(t3, t2)
 
 
 def test_dedupe_groups_identical_subdomains_and_shares_tables(mdp):
