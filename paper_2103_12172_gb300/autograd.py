@@ -4,9 +4,10 @@
 
 k: real tensor [n_subs] of per-subdomain wavenumbers (may require grad); xi: optional complex128
 CUDA tensor of user densities (layout of the output, may require grad). The forward refactors
-the plan when k differs from the plan's current wavenumbers (host LU of every mode, table
-upload) and runs mdp_project_batch; the backward runs mdp_ap_adjoint (conjugate-transposed AP
-solve, and the dG/dk second solve for the wavenumber gradient).
+the plan when k differs from the plan's current wavenumbers (mdp_plan_update_k: every mode's
+pivoted LU, dT/dk rows and sweep table rebuilt by the device factorisation kernels, only the
+subdomain descriptors uploaded) and runs mdp_project_batch; the backward runs mdp_ap_adjoint
+(conjugate-transposed AP solve, and the dG/dk second solve for the wavenumber gradient).
 """
 from __future__ import annotations
 

@@ -198,7 +198,10 @@ __device__ __forceinline__ void fft_r2_stages(double2 *sm, int nf, int Nx, int l
 // the part of y symmetric under j -> N - j gives cosine sums, and 2 sin(pi j/N) cos(2 pi j k/N)
 // = sin(pi j (2k+1)/N) - sin(pi j (2k-1)/N) makes them differences of consecutive odd outputs;
 // the antisymmetric part gives the sine sums at the even outputs. The odd outputs are a prefix
-// sum over k (a tree scan: rounding grows like log N).
+// sum over k (a tree scan: rounding grows like log N). This is the classical reduction of the
+// sine transform to a real-input FFT of the same length (Press, Teukolsky, Vetterling and
+// Flannery, Numerical Recipes, the section on the fast sine transform), applied here to
+// complex data with a full complex FFT, the running sum done as a segmented warp scan.
 
 // y_j and y_{N-j} from the pair xa = x_j, xb = x_{N-j} (j = 1 .. N/2 - 1)
 __device__ __forceinline__ void dst1_twist(cplx xa, cplx xb, double s, cplx &ya, cplx &yb) {

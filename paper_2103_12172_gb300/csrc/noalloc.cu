@@ -59,14 +59,21 @@ extern "C" mdp_status mdp_ap_solve_noalloc(const mdp_subdomain *sub, int nrhs, c
   const size_t per_rhs = (size_t)hd.Nq * hd.Nt * 2 * sizeof(double);
   if (off_buf + per_rhs > kNoAllocScratchBytes) return MDP_ERR_ARG;  // grid too large for the fixed scratch
   if (nrhs == 0) return MDP_OK;
+  // The descriptor and the host tables are copied from pageable memory that is freed on return:
+  // a captured copy node would read freed memory at replay, so a capturing stream is refused
+  // before anything is enqueued.
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return MDP_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return MDP_ERR_STATE;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return MDP_ERR_CUDA;
   void *base = nullptr;
   st = scratch_address(dev, &base);
   if (st != MDP_OK) return st;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   unsigned char *b = (unsigned char *)base;
-  // pageable-source copies are staged before these calls return, so the host tables may go
+  // pageable-source copies are staged before these calls return, so the host tables may go (and
+  // each call waits on the host for the work already queued on `s`)
   if (cudaMemcpyAsync(b, &hd, sizeof hd, cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(b + off_tab, hp.host_tables.data(), hp.host_tables.size() * sizeof(double),
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||

@@ -38,9 +38,28 @@ def test_noalloc_rejects_grids_beyond_its_scratch(mdp):
     from paper_2103_12172_gb300 import _lib
     L = _lib.lib()
     assert L.mdp_ap_solve_noalloc_limit_bytes() == 32 << 20
-    big = W.small_subdomain(1025, 40.0, W.AP_DIRX_SOMMY, 2)   # tables alone exceed 32 MiB
-    rc = L.mdp_ap_solve_noalloc(c_sub(mdp, big), 1, ctypes.c_void_p(0), ctypes.c_void_p(0), 0, ctypes.c_void_p(0))
-    assert rc == _lib.MDP_ERR_ARG
+    for n in (385, 1025):                                      # tables alone exceed 32 MiB
+        big = W.small_subdomain(n, 40.0, W.AP_DIRX_SOMMY, 2)
+        rc = L.mdp_ap_solve_noalloc(c_sub(mdp, big), 1, ctypes.c_void_p(0), ctypes.c_void_p(0), 0,
+                                    ctypes.c_void_p(0))
+        assert rc == _lib.MDP_ERR_ARG
+    fits = W.small_subdomain(321, 40.0, W.AP_DIRX_SOMMY, 2)    # zero right-hand sides: size check only
+    assert L.mdp_ap_solve_noalloc(c_sub(mdp, fits), 0, ctypes.c_void_p(0), ctypes.c_void_p(0), 0,
+                                  ctypes.c_void_p(0)) == 0
+
+
+def scratch_chunk(mdp, sub):
+    """Right-hand sides per chunk of the scratch's mode-space buffer (an estimate within one
+    of the library's own, from the host tables of the same subdomain)."""
+    from paper_2103_12172_gb300 import _lib
+    p = mdp.Plan([sub], host_only=True)
+    nd, npv = ctypes.c_longlong(), ctypes.c_longlong()
+    p.L.mdp_plan_table_sizes(p.handle, ctypes.byref(nd), ctypes.byref(npv))
+    info = p.sub_info(0)
+    p.close()
+    a = lambda v: (v + 255) // 256 * 256                      # noqa: E731
+    used = a(512) + a(nd.value * 8) + a(npv.value)
+    return (_lib.lib().mdp_ap_solve_noalloc_limit_bytes() - used) // (info["Nq"] * info["Nt"] * 16)
 
 
 @pytest.mark.gpu
@@ -60,4 +79,50 @@ def test_noalloc_matches_plan_solve_on_two_calls(mdp):
     # and the first case again after the second overwrote the scratch
     sub, seed, adjoint = cases[0]
     g = torch.from_numpy(W.random_complex((2, sub.ny, sub.nx), seed=9)).cuda()
+    assert rel_err(call_noalloc(mdp, sub, g, 0).cpu().numpy(), mdp.Plan([sub]).solve(0, g).cpu().numpy()) < TOL
+
+
+@pytest.mark.gpu
+def test_noalloc_chunks_and_in_place(mdp):
+    """More right-hand sides than one chunk of the scratch buffer (the per-chunk offsets into g
+    and u), solved in place (u == g), against the plan's solve."""
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2103_12172_gb300 import _lib
+    sub = W.small_subdomain(257, 30.0, W.AP_DIRX_SOMMY, 2)
+    chunk = scratch_chunk(mdp, sub)
+    assert 1 <= chunk < 64
+    g = torch.from_numpy(W.random_complex((chunk + 2, sub.ny, sub.nx), seed=5)).cuda()
+    ref = mdp.Plan([sub]).solve(0, g)
+    u = g.clone()
+    rc = _lib.lib().mdp_ap_solve_noalloc(c_sub(mdp, sub), u.shape[0], ctypes.c_void_p(u.data_ptr()),
+                                         ctypes.c_void_p(u.data_ptr()), 0,
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, _lib.status_string(rc)
+    torch.cuda.synchronize()
+    assert rel_err(u.cpu().numpy(), ref.cpu().numpy()) < TOL
+
+
+@pytest.mark.gpu
+def test_noalloc_refuses_a_capturing_stream(mdp):
+    """A call on a stream that is capturing a CUDA graph returns MDP_ERR_STATE and enqueues
+    nothing; the same call outside the capture still solves."""
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2103_12172_gb300 import _lib
+    sub = W.small_subdomain(65, 7.0, W.AP_DIRX_SOMMY, 2)
+    g = torch.from_numpy(W.random_complex((2, sub.ny, sub.nx), seed=11)).cuda()
+    u = torch.zeros_like(g)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.graph(graph, stream=s):
+        u.add_(0.0)                                  # keeps the captured graph non-empty
+        rc = _lib.lib().mdp_ap_solve_noalloc(c_sub(mdp, sub), g.shape[0], ctypes.c_void_p(g.data_ptr()),
+                                             ctypes.c_void_p(u.data_ptr()), 0, ctypes.c_void_p(s.cuda_stream))
+    torch.cuda.synchronize()
+    assert rc == _lib.MDP_ERR_STATE
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(u.abs().max()) == 0.0               # nothing of the refused call was captured
     assert rel_err(call_noalloc(mdp, sub, g, 0).cpu().numpy(), mdp.Plan([sub]).solve(0, g).cpu().numpy()) < TOL
