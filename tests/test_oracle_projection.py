@@ -203,3 +203,80 @@ def test_wavenumber_gradient_matches_central_differences(ap, kind, basis):
     d = 1e-4 * sub.k   # fourth-order central difference (the loss is curved near resonances)
     fd = (8 * (loss(sub.k + d) - loss(sub.k - d)) - (loss(sub.k + 2 * d) - loss(sub.k - 2 * d))) / (12 * d)
     assert abs(gk - fd) < 1e-6 * max(abs(fd), 1e-30), (gk, fd)
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+def test_receivers_reproduce_a_discrete_plane_wave(ap):
+    """Receiver rows (Eq. potential_solution_homo at interior nodes): for the trace of an exact
+    discrete solution v, the difference potential at the receiver nodes (row, m), m = mlo+1 ..
+    mhi-1, is v there -- which pins the receiver index range against a closed form -- and those
+    nodes are exactly the nodes of M+ in that row that are not on gamma."""
+    sub = W.small_subdomain(33, 6.0, ap, 4)
+    S = APSystem(sub)
+    v = discrete_plane_wave(sub, 0.3)
+    mlo, mhi, nlo, nhi = S.mplus_range()
+    on_gamma = np.zeros_like(S.gs.Mp)
+    on_gamma[S.gs.gamma_n, S.gs.gamma_m] = True
+    for row in (nlo + 1, (nlo + nhi) // 2, nhi - 1):
+        rec = S.receivers(row, xi=[S.trace(v)])[0]
+        want = np.nonzero(S.gs.Mp[row] & ~on_gamma[row])[0]
+        np.testing.assert_array_equal(want, np.arange(mlo + 1, mhi))
+        assert np.abs(rec - v[row, want]).max() < 1e-11 * np.abs(v).max()
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("kind", ["Q", "P"])
+def test_receiver_adjoint_dot_product(ap, kind):
+    """P9 with a receiver cotangent: <c, out(xi)> + <c_rec, receivers(xi)> = <grad_xi, xi>, and
+    with the gamma cotangent zero, <c_rec, receivers(xi)> = <grad_xi, xi> alone (the receiver
+    term R_rec^T c_rec of the adjoint right-hand side is the transpose of the forward gather)."""
+    S = APSystem(W.small_subdomain(33, 6.0, ap, 4))
+    ng = S.n_gamma
+    _, _, nlo, nhi = S.mplus_range()
+    row = (nlo + nhi) // 2 + 1
+    xi = W.random_complex((3, ng), seed=12)
+    c = W.random_complex((3, ng), seed=13)
+    rec = S.receivers(row, xi=xi)
+    c_rec = W.random_complex(rec.shape, seed=14)
+    out = S.columns(xi=xi, kind=kind)
+    gx, _ = S.adjoint(c, kind=kind, xi=xi, cot_rec=c_rec, rec_row=row)
+    lhs = np.vdot(c, out) + np.vdot(c_rec, rec)
+    assert abs(lhs - np.vdot(gx, xi)) < 1e-10 * abs(lhs)
+    gx0, _ = S.adjoint(np.zeros_like(c), kind="Q", xi=xi, cot_rec=c_rec, rec_row=row)
+    lhs0 = np.vdot(c_rec, rec)
+    assert abs(lhs0 - np.vdot(gx0, xi)) < 1e-10 * abs(lhs0)
+
+
+@pytest.mark.parametrize("ap", [W.AP_DIRICHLET4, W.AP_DIRX_SOMMY])
+@pytest.mark.parametrize("basis", [True, False])
+def test_receiver_wavenumber_gradient_matches_central_differences(ap, basis):
+    """P9 with a receiver cotangent: dLoss/dk of Loss = Re <c_rec, receivers(k)> (the gamma
+    cotangent zero, and then both together) from the adjoint equals a fourth-order central
+    difference of the forward receivers in k; basis columns carry Ex's own k-dependence."""
+    sub = W.small_subdomain(33, 6.0, ap, 3)
+    S0 = APSystem(sub)
+    _, _, nlo, nhi = S0.mplus_range()
+    row = nlo + 3
+    cols = [0, 5, 14, 23]
+    ng = S0.n_gamma
+    xi = None if basis else W.random_complex((len(cols), ng), seed=15)
+    npx = S0.receivers(row, cols=[0]).shape[1]
+    c_rec = W.random_complex((len(cols), npx), seed=16)
+    c = W.random_complex((len(cols), ng), seed=17)
+
+    def loss(k, with_gamma):
+        S = APSystem(sub.with_k(k))
+        rec = S.receivers(row, cols=cols) if basis else S.receivers(row, xi=xi)
+        val = np.real(np.vdot(c_rec, rec))
+        if with_gamma:
+            out = S.columns(cols=cols) if basis else S.columns(xi=xi)
+            val += np.real(np.vdot(c, out))
+        return val
+
+    d = 1e-4 * sub.k
+    for with_gamma in (False, True):
+        cot = c if with_gamma else np.zeros_like(c)
+        _, gk = S0.adjoint(cot, xi=xi, cols=cols, cot_rec=c_rec, rec_row=row)
+        f = lambda k: loss(k, with_gamma)   # noqa: E731
+        fd = (8 * (f(sub.k + d) - f(sub.k - d)) - (f(sub.k + 2 * d) - f(sub.k - 2 * d))) / (12 * d)
+        assert abs(gk - fd) < 1e-6 * max(abs(fd), 1e-30), (with_gamma, gk, fd)
