@@ -4,7 +4,11 @@ One step = one mdp_project_batch over every basis column of every subdomain of t
 (extension, ring residual, sine transforms, per-mode tridiagonal solves, trace gather: the
 whole forward hot path), inputs resident in HBM. Prints ONE JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload dd2x2_257] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload dd8x8] [--impl ours|reference]
+
+The headline workload is the largest single-GPU one, the 8 x 8 decomposition (64 subdomains,
+257^2 / 513^2 / 1025^2 grids, 32768 columns); the other workloads are measured more briefly
+and reported in the same line under "configs".
 
 --impl reference times the CPU oracle (SciPy SuperLU, the test oracle) on the host cores on a
 bounded sample of the same workload; it is the deliberately slow baseline, not a target.
@@ -13,7 +17,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import multiprocessing as mp
 import os
 import statistics
@@ -30,6 +33,18 @@ METRIC = "batched AP solves/s (FP64 complex), % HBM roofline vs per-RHS path at 
 UNIT = "AP solves/s"
 NOMINAL_FP64_GFLOPS = 152 * 2 * 2 * 2.070  # SMs x DFMA/clk/SM x flops/DFMA x max GHz = 1258.6
 L2_FLUSH_BYTES = 512 << 20
+HEADLINE = "dd8x8"
+SUB_CONFIGS = ("single_129", "dd2x2_257", "checker2x2", "strip4x1")
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline: the measured copy bandwidth when the measured-peaks
+    file is present, else the recipe's fallback figure."""
+    try:
+        v = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        return v, "measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, "fallback"
 
 
 # ------------------------------------------------------------------ oracle timing (CPU)
@@ -46,23 +61,113 @@ def _oracle_worker_cols(cols):
     return len(cols), time.perf_counter() - t
 
 
-def oracle_throughput(sub, workers, min_seconds=10.0):
-    """Columns/s of the oracle over `workers` spawned processes, each factoring `sub` once
-    (untimed, like plan creation) and solving basis columns in rounds of one column per
-    worker until at least `min_seconds` of wall time have passed."""
-    import dataclasses
-    ctx = mp.get_context("spawn")
-    ncol = 8 * sub.n_modes
-    with ctx.Pool(workers, initializer=_oracle_worker_init, initargs=(dataclasses.asdict(sub),)) as pool:
-        pool.map(_oracle_worker_cols, [[0]] * workers)  # warm: factor in every worker
-        done, c = 0, 0
-        t = time.perf_counter()
-        while time.perf_counter() - t < min_seconds:
-            chunks = [[(c + i) % ncol] for i in range(workers)]
-            c += workers
-            done += sum(r[0] for r in pool.map(_oracle_worker_cols, chunks))
-        wall = time.perf_counter() - t
-    return done / wall, done, wall
+def grid_classes(wl):
+    """{nx: (index of the first subdomain with that grid, number of subdomains)}."""
+    cls = {}
+    for i, s in enumerate(wl.subdomains):
+        first, cnt = cls.get(s.nx, (i, 0))
+        cls[s.nx] = (first, cnt + 1)
+    return dict(sorted(cls.items()))
+
+
+def class_workers(cls, workers):
+    """Host processes per grid class: about in proportion to the class's share of the oracle's
+    work (columns x n^2 log n), at least one each, at most 6 on the largest grids (a SuperLU
+    factorisation of a 1025^2 AP holds about 5 GB)."""
+    import math
+    wt = {nx: cnt * nx * nx * math.log2(nx) for nx, (_, cnt) in cls.items()}
+    tot = sum(wt.values())
+    alloc = {nx: 1 for nx in cls}
+    spare = max(0, workers - len(cls))
+    for nx in sorted(cls, key=lambda n: -wt[n]):
+        extra = min(spare, int(round(spare * wt[nx] / tot)) if tot else 0)
+        alloc[nx] += extra
+    big = max(cls)
+    if big >= 1025 and alloc[big] > 6 and len(cls) > 1:
+        nxt = max((n for n in cls if n != big), key=lambda n: wt[n])
+        alloc[nxt] += alloc[big] - 6
+        alloc[big] = 6
+    return alloc
+
+
+class OracleClasses:
+    """One spawned process pool per grid class of a workload, each worker holding one SuperLU
+    factorisation of the class's first subdomain (made in the pool's initializer: untimed, like
+    plan creation). `round(cols_per_worker)` solves that many basis columns in every worker of
+    every class at once and returns the per-class busy seconds and column counts."""
+
+    def __init__(self, wl, workers):
+        import dataclasses
+        self.wl = wl
+        self.cls = grid_classes(wl)
+        self.alloc = class_workers(self.cls, workers)
+        ctx = mp.get_context("spawn")
+        self.pools = {nx: ctx.Pool(self.alloc[nx], initializer=_oracle_worker_init,
+                                   initargs=(dataclasses.asdict(wl.subdomains[first]),))
+                      for nx, (first, _) in self.cls.items()}
+        self.next = {nx: 0 for nx in self.cls}
+        warm = [self.pools[nx].map_async(_oracle_worker_cols, [[0]] * self.alloc[nx]) for nx in self.cls]
+        for w in warm:
+            w.get()
+
+    @property
+    def cores(self):
+        return sum(self.alloc.values())
+
+    def round(self, cols_per_worker=1):
+        jobs = {}
+        for nx, (first, _) in self.cls.items():
+            ncol = 8 * self.wl.subdomains[first].n_modes
+            chunks = []
+            for _ in range(self.alloc[nx]):
+                chunks.append([(self.next[nx] + j) % ncol for j in range(cols_per_worker)])
+                self.next[nx] += cols_per_worker
+            jobs[nx] = self.pools[nx].map_async(_oracle_worker_cols, chunks)
+        res = {}
+        for nx, j in jobs.items():
+            r = j.get()
+            res[nx] = (sum(x[1] for x in r), sum(x[0] for x in r))
+        return res
+
+    def close(self):
+        for p in self.pools.values():
+            p.close()
+            p.join()
+
+
+def extrapolated_rate(wl, busy, cores):
+    """Columns/s of the whole workload on `cores` host cores from the per-class seconds per
+    column (busy[nx] = (seconds, columns) summed over that class's workers): the single-core
+    time of every column of the workload, divided over the cores."""
+    total = 0.0
+    for nx, (_, cnt) in grid_classes(wl).items():
+        sec, cols = busy[nx]
+        first = grid_classes(wl)[nx][0]
+        total += cnt * 8 * wl.subdomains[first].n_modes * sec / cols
+    return wl.n_columns * cores / total
+
+
+def oracle_baseline(wl, workers, min_seconds=10.0):
+    """cpu_baseline: the oracle on a bounded sample of the workload (one subdomain per grid
+    class, one column per worker per round, rounds until min_seconds of wall time), the rate
+    extrapolated to the workload's mix of grids."""
+    oc = OracleClasses(wl, workers)
+    busy = {nx: (0.0, 0) for nx in oc.cls}
+    t = time.perf_counter()
+    while time.perf_counter() - t < min_seconds:
+        for nx, (s, c) in oc.round(1).items():
+            busy[nx] = (busy[nx][0] + s, busy[nx][1] + c)
+    wall = time.perf_counter() - t
+    oc.close()
+    value = extrapolated_rate(wl, busy, oc.cores)
+    per = ", ".join(f"{nx}^2: {busy[nx][1]} columns on {oc.alloc[nx]} processes, "
+                    f"{1e3 * busy[nx][0] / busy[nx][1]:.1f} ms/column" for nx in oc.cls)
+    multi = len(oc.cls) > 1
+    sample = (f"{'extrapolated: ' if multi else ''}one subdomain per grid class of {wl.name} ({per}); "
+              f"SuperLU factorisation per process untimed; {wall:.1f} s wall"
+              + ("; rate = the workload's columns x cores / its single-core time at the measured "
+                 "per-class seconds per column" if multi else ""))
+    return value, oc.cores, sample
 
 
 # ------------------------------------------------------------------ clocks
@@ -85,7 +190,7 @@ class ClockSampler:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-        time.sleep(0.3)
+        time.sleep(1.0)   # nvidia-smi's start-up (driver queries) stays out of the timed region
         return self
 
     def __exit__(self, *a):
@@ -181,7 +286,8 @@ def kernel_source_sha():
 
 def recorded_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from profiles/traffic.json (an ncu
-    capture), or None when absent or taken on a different kernel source."""
+    capture, or a smaller capture scaled by the units processed, as recorded there), or None
+    when absent or taken on a different kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[workload][kernel]
@@ -192,35 +298,37 @@ def recorded_traffic(kernel, workload):
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, wl):
+    """The oracle on the host cores: every step solves one basis column per process of one
+    subdomain per grid class (factorisations untimed); value = the per-class seconds per
+    column extrapolated to the workload's mix (a single grid class: plain columns/s)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    sub = wl.subdomains[0]
     workers = max(1, min(16, os.cpu_count() or 1))
-    per_step = workers * max(1, int(os.environ.get("MDP_REF_COLS_PER_WORKER", "2")))
-    import dataclasses
-    ctx = mp.get_context("spawn")
-    times, cols = [], 0
-    with ctx.Pool(workers, initializer=_oracle_worker_init, initargs=(dataclasses.asdict(sub),)) as pool:
-        pool.map(_oracle_worker_cols, [[0]] * workers)
-        for s in range(args.warmup + args.steps):
-            chunks = [[(s * per_step + i + j * workers) % (8 * sub.n_modes) for j in range(per_step // workers)]
-                      for i in range(workers)]
-            t = time.perf_counter()
-            res = pool.map(_oracle_worker_cols, chunks)
-            dt = time.perf_counter() - t
-            if s >= args.warmup:
-                times.append(dt)
-                cols += sum(r[0] for r in res)
-    total = sum(times)
-    value = cols / total
-    sample = (f"{per_step} basis columns per step of subdomain 0 ({sub.nx}x{sub.ny}, k={sub.k}) of {wl.name}; "
-              f"SuperLU factorisation per worker outside the timed region")
+    oc = OracleClasses(wl, workers)
+    busy = {nx: (0.0, 0) for nx in oc.cls}
+    times = []
+    for s in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        r = oc.round(1)
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            times.append(dt)
+            for nx, (sec, c) in r.items():
+                busy[nx] = (busy[nx][0] + sec, busy[nx][1] + c)
+    oc.close()
+    value = extrapolated_rate(wl, busy, oc.cores)
+    cols = sum(c for (_, c) in busy.values())
+    multi = len(oc.cls) > 1
+    sample = (f"{'extrapolated: ' if multi else ''}one basis column per process per step of one subdomain per "
+              f"grid class of {wl.name} (" + ", ".join(f"{nx}^2 on {oc.alloc[nx]} processes" for nx in oc.cls)
+              + f"), {cols} columns timed; SuperLU factorisation per process outside the timed region")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "description": wl.description, "columns_per_step": per_step},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
+            "config": {"workload": wl.name, "description": wl.description,
+                       "columns_per_step": cols // max(1, args.steps)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oc.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -288,79 +396,103 @@ def dd_legs(reps=5):
 
 
 # ------------------------------------------------------------------ our arm
-def run_ours(args, wl):
+def event_time(fn, reps, stream):
+    """Mean milliseconds of fn() over reps calls on `stream` (CUDA events, after one warm call)."""
     import torch
-    import torch.distributed as dist
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
-    import paper_2103_12172_gb300 as mdp
-    from paper_2103_12172_gb300 import _build
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    _build.build()
-    dev = torch.device("cuda", local)
+def measure(mdp, wl, steps, warmup, world=1, barrier=None, clocks=None, full=True):
+    """Throughput of one workload: `steps` timed mdp_project_batch passes over every column
+    (CUDA events on the launching stream, L2 flushed between steps, per-kernel events for the
+    roofline), then the side legs: end to end through host buffers, the gradient pass, the
+    per-RHS comparator and (full) the graph-replayed and deduplicated variants."""
+    import torch
 
-    subs = list(wl.subdomains)
     from paper_2103_12172_gb300.autotune import tune_tile
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    subs = list(wl.subdomains)
+    n_cols = wl.n_columns
     tile = tune_tile(subs)                     # untimed: columns per work item for this GPU and shape
     plan = mdp.Plan(subs, tile_cols=tile)
-    n_cols = sum(8 * s.n_modes for s in subs)
     out = torch.empty(plan.output_size, dtype=torch.complex128, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    fp64_probe = mdp.probe_fp64_gflops()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.project(out=out)
     torch.cuda.synchronize()
     plan.status()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     plan.profile(True)
-    with ClockSampler(local) as clk:
+    if barrier:
         barrier()
-        torch.cuda.synchronize()
-        wall0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(float(i))                  # evict L2 between timed steps (not timed)
-            starts[i].record(stream)
-            plan.project(out=out)
-            ends[i].record(stream)
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(steps):
+        flush.fill_(float(i))                  # evict L2 between timed steps (not timed)
+        starts[i].record(stream)
+        plan.project(out=out)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if barrier:
         barrier()
-        wall = time.perf_counter() - wall0
+    wall = time.perf_counter() - wall0
     plan.profile(False)
     prof = plan.profile_read()
     plan.status()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     if world > 1:
+        import torch.distributed as dist
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * n_cols * args.steps / (total_ms / 1e3)
+    value = world * n_cols * steps / (total_ms / 1e3)
+    # host cost of issuing one step (profiling off, nothing waited for): the timed loop's wall
+    # time minus its device time is this issue time, the L2 fills, and the per-launch event
+    # records of the profiling
+    t0 = time.perf_counter()
+    plan.project(out=out)
+    issue_ms = 1e3 * (time.perf_counter() - t0)
+    torch.cuda.synchronize()
 
     # roofline of the dominant kernel (live CUDA events around its launches, timed region)
-    items = []
-    for s in range(len(subs)):
-        items.append((s, 8 * subs[s].n_modes))
-    flops = kernel_flops(plan, items)
+    flops = kernel_flops(plan, [(s, 8 * subs[s].n_modes) for s in range(len(subs))])
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
-    launches_per_step = dom_launches / args.steps
+    launches_per_step = dom_launches / steps
     flops_per_launch = flops.get(dom, 0.0) / launches_per_step
-    achieved = flops_per_launch / (dom_ms / dom_launches / 1e3) / 1e12
+    launch_s = dom_ms / dom_launches / 1e3
+    achieved = flops_per_launch / launch_s / 1e12
     peak = NOMINAL_FP64_GFLOPS / 1e3
-    gpu_launches = sum(n for (_, n) in prof.values())
+    traffic = recorded_traffic(dom, wl.name)
+    hbm, hbm_src = hbm_peak()
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_note": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived from unit counts and "
+                         "clock; the DFMA rate per SM is measured by the probe)",
+            "step_flop_frac": sum(flops.values()) / (total_ms / steps / 1e3) / 1e12 / peak,
+            "launches_per_step": launches_per_step}
+    if traffic:
+        roof["dram_gbs"] = traffic / launch_s / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / hbm
+        roof["dram_peak_gbs"] = hbm
+        roof["dram_peak_note"] = f"{hbm_src} HBM copy bandwidth; DRAM fraction is context, the path is FP64-bound"
+    res = {"value": value, "unit": UNIT, "ms_per_step": total_ms / steps, "columns_per_step": n_cols,
+           "tile_cols": tile, "roofline": roof,
+           "kernels_ms_per_step": {k: v[0] / steps for k, v in sorted(prof.items())},
+           "gpu_launches": sum(n for (_, n) in prof.values()),
+           "wall_s_timed": wall, "host_issue_ms_per_step": issue_ms}
 
     # end to end through the public API with host buffers: new wavenumbers from host memory
     # (every mode refactored on the GPU), all columns, every step's result read back to pinned
@@ -374,7 +506,7 @@ def run_ours(args, wl):
     cs, xs, fs = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     copied = [None, None]
     ks = [s.k for s in subs]
-    e2e_steps = max(3, min(args.steps, 10))
+    e2e_steps = max(3, min(steps, 10))
 
     def e2e_step(i):
         b = i % 2
@@ -392,115 +524,148 @@ def run_ours(args, wl):
 
     e2e_step(-1)                                 # untimed warm-up of the same step
     torch.cuda.synchronize()
+    plan.status()                                # the warm-up's refactorisation met no singular mode
     copied = [None, None]
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         e2e_step(i)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    plan.status()                                # no step met a singular mode
+    plan.status()                                # sticky: no timed step met a singular mode either
     plan.update_k(ks)
     update_bytes = int(plan.L.mdp_plan_update_bytes(plan.handle))
-    e2e = {"value": world * n_cols * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": update_bytes,
-           "d2h_bytes_per_step": int(plan.output_size * 16),
-           "what": "update_k (new k up, every mode refactored on the GPU) + project + D2H of all columns "
-                   "to pinned host memory; pipelined: step i+1's update and refactorisation (second table set) "
-                   "and step i's D2H overlap step i's projection"}
-
-    # the same step replayed as one CUDA graph (library graph mode)
-    gplan = mdp.Plan(subs, tile_cols=tile, graph=True)
-    gs = torch.cuda.Stream()
-    with torch.cuda.stream(gs):
-        for _ in range(2):
-            gplan.project(out=out)
-        ge0, ge1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ge0.record(gs)
-        for _ in range(args.steps):
-            gplan.project(out=out)
-        ge1.record(gs)
-    gs.synchronize()
-    graph_ms = ge0.elapsed_time(ge1) / args.steps
-    gplan.close()
-
-    # identical subdomains solved once (MDP_PLAN_DEDUPE), reported separately: the same columns
-    # of every subdomain, the distinct problems solved and their blocks copied
-    dplan = mdp.Plan(subs, tile_cols=tile, dedupe=True)
-    n_distinct = len(set(dplan.leaders()))
-    for _ in range(2):
-        dplan.project(out=out)
-    de0, de1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    de0.record(stream)
-    for _ in range(args.steps):
-        dplan.project(out=out)
-    de1.record(stream)
-    torch.cuda.synchronize()
-    dedupe_ms = de0.elapsed_time(de1) / args.steps
-    dplan.close()
+    res["e2e"] = {"value": world * n_cols * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": update_bytes,
+                  "d2h_bytes_per_step": int(plan.output_size * 16),
+                  "what": "update_k (new k up, every mode refactored on the GPU) + project + D2H of all columns "
+                          "to pinned host memory; pipelined: step i+1's update and refactorisation (second table "
+                          "set) and step i's D2H overlap step i's projection"}
+    del host_out, outs
 
     # adjoint: dLoss/dk for every subdomain through mdp_ap_adjoint (forward recompute + G^H)
     cot = out.clone()
     gk = torch.zeros(len(subs), dtype=torch.float64, device=dev)
-    for _ in range(2):
-        plan.adjoint(cot, grad_xi=False, grad_k=gk)
-    ae0, ae1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ae0.record(stream)
-    for _ in range(args.steps):
-        plan.adjoint(cot, grad_xi=False, grad_k=gk)
-    ae1.record(stream)
-    torch.cuda.synchronize()
-    adj_ms = ae0.elapsed_time(ae1) / args.steps
+    adj_ms = event_time(lambda: plan.adjoint(cot, grad_xi=False, grad_k=gk), max(2, min(steps, 5)), stream)
+    plan.status()
+    res["adjoint_grad_k"] = {"value": n_cols / (adj_ms / 1e3), "unit": UNIT, "ms_per_step": adj_ms}
+    del cot
 
-    # per-RHS comparator: the same kernels one column per launch sequence, no batching
-    per_rhs_cols = min(64, n_cols)
-    one = torch.empty(plan.layout(0)[0], dtype=torch.complex128, device=dev)
-    for c in range(4):
-        plan.project_columns(0, c, 1, out=one)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for c in range(per_rhs_cols):
-        plan.project_columns(0, c % (8 * subs[0].n_modes), 1, out=one)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    per_rhs = per_rhs_cols / (e0.elapsed_time(e1) / 1e3)
+    # per-RHS comparator: the same kernels, one column per launch sequence, no batching; per grid
+    # class on its first subdomain, extrapolated to the workload's mix
+    per_col_ms = {}
+    for nx, (first, cnt) in grid_classes(wl).items():
+        one = torch.empty(plan.layout(first)[0], dtype=torch.complex128, device=dev)
+        ncol = 8 * subs[first].n_modes
+        reps = 16 if nx <= 513 else 8
+        c = [0]
 
+        def one_col():
+            plan.project_columns(first, c[0] % ncol, 1, out=one)
+            c[0] += 37
+
+        per_col_ms[nx] = event_time(one_col, reps, stream)
+    t_per_rhs = sum(cnt * 8 * subs[first].n_modes * per_col_ms[nx] for nx, (first, cnt) in grid_classes(wl).items())
+    per_rhs = n_cols / (t_per_rhs / 1e3)
+    res["per_rhs"] = {"value": per_rhs, "unit": UNIT, "speedup_batched": value / world / per_rhs,
+                      "ms_per_column": per_col_ms}
+
+    if full:
+        # the same step replayed as one CUDA graph (library graph mode): the difference is what
+        # the per-kernel, per-wave launches cost
+        gplan = mdp.Plan(subs, tile_cols=tile, graph=True)
+        gs = torch.cuda.Stream()
+        with torch.cuda.stream(gs):
+            graph_ms = event_time(lambda: gplan.project(out=out), max(3, min(steps, 10)), gs)
+        gplan.close()
+        res["graph"] = {"ms_per_step": graph_ms, "launches_per_step": 1, "tile_cols": tile,
+                        "launch_overhead_frac": max(0.0, 1.0 - graph_ms / res["ms_per_step"])}
+        # identical subdomains solved once (MDP_PLAN_DEDUPE), reported separately: the same columns
+        # of every subdomain, the distinct problems solved and their blocks copied
+        dplan = mdp.Plan(subs, tile_cols=tile, dedupe=True)
+        n_distinct = len(set(dplan.leaders()))
+        if n_distinct < len(subs):
+            dedupe_ms = event_time(lambda: dplan.project(out=out), max(3, min(steps, 10)), stream)
+            res["dedupe"] = {"value": world * n_cols / (dedupe_ms / 1e3), "unit": UNIT, "ms_per_step": dedupe_ms,
+                             "distinct_subdomains": n_distinct,
+                             "what": "identical subdomains solved once, blocks copied (not the headline value)"}
+        dplan.close()
+    plan.close()
+    del out, flush
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2103_12172_gb300 as mdp
+    from paper_2103_12172_gb300 import _build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    fp64_probe = mdp.probe_fp64_gflops()
+    with ClockSampler(local) as clk:
+        head = measure(mdp, wl, args.steps, args.warmup, world=world, barrier=barrier, full=True)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "description": wl.description, "columns_per_step": n_cols,
-                   "tile_cols": tile,
-                   "l2": "flushed between timed steps (512 MiB write, untimed)", "parallelism": f"replicas{world}"},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(dom, wl.name),
-                     "peak_note": "FP64 FMA: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (DFMA rate per SM measured)",
-                     "fp64_probe_tflops": fp64_probe / 1e3},
-        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof.items())},
-        "gpu_launches": gpu_launches,
-        "per_rhs": {"value": per_rhs, "unit": UNIT, "speedup_batched": value / world / per_rhs},
-        "graph": {"ms_per_step": graph_ms, "launches_per_step": 1, "tile_cols": tile},
-        "dedupe": {"value": world * n_cols / (dedupe_ms / 1e3), "unit": UNIT, "ms_per_step": dedupe_ms,
-                   "distinct_subdomains": n_distinct,
-                   "what": "identical subdomains solved once, blocks copied (not the headline value)"},
-        "adjoint_grad_k": {"value": n_cols / (adj_ms / 1e3), "unit": UNIT, "ms_per_step": adj_ms},
-        "e2e": e2e,
-        "wall_s_timed": wall,
+        "config": {"workload": wl.name, "description": wl.description, "columns_per_step": head["columns_per_step"],
+                   "tile_cols": head["tile_cols"],
+                   "l2": "flushed between timed steps (512 MiB write, untimed); every wave's workspace also "
+                         "exceeds L2", "parallelism": f"replicas{world}"},
+        "roofline": dict(head["roofline"], fp64_probe_tflops=fp64_probe / 1e3),
+        "kernels_ms_per_step": head["kernels_ms_per_step"],
+        "gpu_launches": head["gpu_launches"],
+        "per_rhs": head["per_rhs"],
+        "graph": head.get("graph"),
+        "adjoint_grad_k": head["adjoint_grad_k"],
+        "e2e": head["e2e"],
+        "wall_s_timed": head["wall_s_timed"],
+        "host_issue_ms_per_step": head["host_issue_ms_per_step"],
+        "wall_note": "wall_s_timed spans the timed loop on the host: the device time of the timed steps, "
+                     "the untimed L2-flush fills between them and, where the host is slower than the GPU, "
+                     "the issue of each step (host_issue_ms_per_step, measured with profiling off)",
     }
+    if "dedupe" in head:
+        line["dedupe"] = head["dedupe"]
+    line["clocks"] = clk.summary()
+
+    if not args.no_configs and world == 1:
+        cfgs = {}
+        for name in SUB_CONFIGS:
+            if W.WORKLOADS[name]().name == wl.name:
+                continue
+            sub_wl = W.WORKLOADS[name]()
+            r = measure(mdp, sub_wl, max(5, min(args.steps, 10)), 3, full=False)
+            cfgs[name] = {"workload": sub_wl.name, "value": r["value"], "unit": UNIT,
+                          "ms_per_step": r["ms_per_step"], "columns_per_step": r["columns_per_step"],
+                          "tile_cols": r["tile_cols"], "roofline_kernel": r["roofline"]["kernel"],
+                          "roofline_frac": r["roofline"]["frac"],
+                          "step_flop_frac": r["roofline"]["step_flop_frac"],
+                          "dram_frac": r["roofline"].get("dram_frac"),
+                          "kernels_ms_per_step": r["kernels_ms_per_step"],
+                          "adjoint_grad_k": r["adjoint_grad_k"]["value"], "e2e": r["e2e"]["value"],
+                          "per_rhs_speedup": r["per_rhs"]["speedup_batched"]}
+        line["configs"] = cfgs
     if rank == 0 and not args.no_dd_legs:
         line["dd_pipeline"] = dd_legs()
 
     # CPU baseline: the oracle as it stands, on the host cores, bounded sample (rank 0 at N=1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         workers = max(1, min(16, os.cpu_count() or 1))
-        sub = subs[0]
-        cps, done, wall_c = oracle_throughput(sub, workers)
-        line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": workers, "kind": "oracle",
-                                "sample": f"{done} basis columns of subdomain 0 ({sub.nx}x{sub.ny}, k={sub.k}) over "
-                                          f"{workers} spawned processes, SuperLU factor per process untimed, "
-                                          f"{wall_c:.2f} s wall"}
-    line["clocks"] = clk.summary()
+        cps, cores, sample = oracle_baseline(wl, workers)
+        line["cpu_baseline"] = {"value": cps, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -513,10 +678,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="dd2x2_257", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(W.WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dd-legs", action="store_true", help="skip the layered-strip pipeline timings")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads' sub-lines")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

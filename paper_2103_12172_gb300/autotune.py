@@ -32,6 +32,9 @@ def tune_tile(subdomains, candidates=(32, 64, 128, 256, 512), reps=3, cache_path
     if not force and key in cache:
         return int(cache[key]["tile_cols"])
     max_cols = max(8 * s.n_modes for s in subdomains)
+    if sum(8 * s.n_modes for s in subdomains) >= 8192:
+        # large batches fill the GPU at any tile: skip the small tiles (each candidate is a plan)
+        candidates = [c for c in candidates if c >= 128] or list(candidates)
     cands = sorted({min(c, max_cols) for c in candidates})
     times = {}
     for tile in cands:

@@ -122,3 +122,70 @@ def test_multi_subdomain_gradient_is_deterministic_and_per_subdomain(mdp):
     for i, s in enumerate(subs):
         _, ref = APSystem(s).adjoint(blocks[i].cpu().numpy(), kind="Q")
         assert abs(g1[i].item() - ref) < 1e-9 * abs(ref)
+
+
+def _sampled_adjoint_against_oracle(mdp, subs, picks, tile, seed):
+    """One batched gradient pass over every basis column of `subs` (the launch shape the bench
+    times), checked on sampled columns: picks[i] lists the columns of subdomain i checked (an
+    empty list skips it). grad_xi of the picked columns, for a cotangent on every column,
+    against the oracle's; grad_k of each checked subdomain, for the cotangent restricted to
+    its picked columns (zero on every other column, so the oracle needs only those), against
+    the oracle's; and grad_xi of a zero cotangent column is exactly zero."""
+    plan = mdp.Plan(subs, tile_cols=tile)
+    n = plan.output_size
+    cot = W.random_complex(n, seed=seed)
+    gx, _ = plan.adjoint(torch.from_numpy(cot).cuda(), grad_k=False)
+    masked = np.zeros_like(cot)
+    for i, cols in enumerate(picks):
+        G, nc, off, _ = plan.layout(i)
+        for c in cols:
+            masked[off + c * G: off + (c + 1) * G] = cot[off + c * G: off + (c + 1) * G]
+    gx0, gk = plan.adjoint(torch.from_numpy(masked).cuda())
+    torch.cuda.synchronize()
+    plan.status()
+    gxb = [b.cpu().numpy() for b in plan.blocks(gx)]
+    gx0b = [b.cpu().numpy() for b in plan.blocks(gx0)]
+    cotb = [b.cpu().numpy() for b in plan.blocks(torch.from_numpy(cot))]
+    for i, cols in enumerate(picks):
+        if not cols:
+            continue
+        ref_x, ref_k = APSystem(subs[i]).adjoint(cotb[i][cols], kind="Q", cols=cols)
+        assert rel_col_err(gxb[i][cols], ref_x) < 1e-10, i
+        assert rel_col_err(gx0b[i][cols], ref_x) < 1e-10, i
+        others = np.setdiff1d(np.arange(gx0b[i].shape[0]), cols)
+        assert np.all(gx0b[i][others] == 0), i
+        assert abs(gk[i].item() - ref_k) < 1e-9 * abs(ref_k), (i, gk[i].item(), ref_k)
+
+
+@pytest.mark.slow
+def test_adjoint_at_dd2x2_257_sampled(mdp):
+    """The bench's gradient shape: 2x2 subdomains at 257^2, k = 30, mixed AP, M* = 32, tile of
+    256 columns, all 1024 columns in one pass; 24 sampled columns of each subdomain (every side
+    and both kinds, the highest Chebyshev mode included)."""
+    wl = W.dd2x2_257()
+    rng = np.random.default_rng(3)
+    picks = []
+    for s in wl.subdomains:
+        nc = 8 * s.n_modes
+        hi = [s.n_modes * j + s.n_modes - 1 for j in range(8)]          # T_31 of every side and kind
+        rest = rng.choice(np.setdiff1d(np.arange(nc), hi), 16, replace=False).tolist()
+        picks.append(sorted(hi + rest))
+    _sampled_adjoint_against_oracle(mdp, list(wl.subdomains), picks, 256, seed=31)
+
+
+@pytest.mark.slow
+def test_adjoint_at_checker2x2_513_k100_sampled(mdp):
+    """The checkerboard batch (129^2 at k = 10 and 513^2 at k = 100, M* = 48) in one gradient
+    pass; checked on the first 513^2, k = 100 subdomain (the most near-propagating modes) at 16
+    columns: T_47 of every side and kind, and 8 random ones, and on one 129^2 subdomain."""
+    wl = W.checker2x2()
+    subs = list(wl.subdomains)
+    rng = np.random.default_rng(4)
+    picks = [[] for _ in subs]
+    big = next(i for i, s in enumerate(subs) if s.nx == 513)
+    small = next(i for i, s in enumerate(subs) if s.nx == 129)
+    M = subs[big].n_modes
+    hi = [M * j + M - 1 for j in range(8)]
+    picks[big] = sorted(hi + rng.choice(np.setdiff1d(np.arange(8 * M), hi), 8, replace=False).tolist())
+    picks[small] = sorted(rng.choice(8 * M, 8, replace=False).tolist())
+    _sampled_adjoint_against_oracle(mdp, subs, picks, 256, seed=32)

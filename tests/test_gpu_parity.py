@@ -149,14 +149,20 @@ def test_dd2x2_257_workload(dev):
 
 
 def test_checkerboard_workload_sampled(dev):
-    """2x2 checkerboard with 129^2 (k = 10) and 513^2 (k = 100) subdomains in one batch."""
+    """2x2 checkerboard with 129^2 (k = 10) and 513^2 (k = 100) subdomains in one batch: every
+    subdomain on 12 random columns, and each 513^2, k = 100 subdomain (the most near-propagating
+    modes) also on the highest Chebyshev mode T_47 of every side and both kinds."""
     wl = W.checker2x2()
     plan = dev.Plan(list(wl.subdomains))
     out = plan.project()
     blocks = plan.blocks(out)
     rng = np.random.default_rng(1)
-    for i, sub in enumerate(wl.subdomains[:2]):
-        cols = sorted(rng.choice(8 * sub.n_modes, 12, replace=False).tolist())
+    for i, sub in enumerate(wl.subdomains):
+        M = sub.n_modes
+        cols = set(rng.choice(8 * M, 12, replace=False).tolist())
+        if sub.nx == 513:
+            cols |= {M * j + M - 1 for j in range(8)}
+        cols = sorted(cols)
         ref = APSystem(sub).columns(cols=cols)
         assert rel_col_err(blocks[i].cpu().numpy()[cols], ref) < TOL, i
 
