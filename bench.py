@@ -614,6 +614,7 @@ def run_ours(args, wl):
             dist.barrier()
 
     fp64_probe = mdp.probe_fp64_gflops()
+    dmma_probe = mdp.probe_dmma_gflops()         # the FP64 tensor-core path, for comparison
     with ClockSampler(local) as clk:
         head = measure(mdp, wl, args.steps, args.warmup, world=world, barrier=barrier, full=True)
     line = {
@@ -624,7 +625,8 @@ def run_ours(args, wl):
                    "tile_cols": head["tile_cols"],
                    "l2": "flushed between timed steps (512 MiB write, untimed); every wave's workspace also "
                          "exceeds L2", "parallelism": f"replicas{world}"},
-        "roofline": dict(head["roofline"], fp64_probe_tflops=fp64_probe / 1e3),
+        "roofline": dict(head["roofline"], fp64_probe_tflops=fp64_probe / 1e3,
+                         fp64_dmma_probe_tflops=dmma_probe / 1e3),
         "kernels_ms_per_step": head["kernels_ms_per_step"],
         "gpu_launches": head["gpu_launches"],
         "per_rhs": head["per_rhs"],

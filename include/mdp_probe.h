@@ -16,6 +16,12 @@ extern "C" {
  * a small device buffer. Returns MDP_ERR_CUDA on a CUDA failure. */
 mdp_status mdp_probe_dfma_gflops(int iters, double *gflops, void *cuda_stream);
 
+/* The same for the FP64 tensor-core path: 8 independent chains of mma.sync m8n8k4 FP64 MMAs
+ * (512 flops each) per warp, 8 resident blocks of 256 threads per SM, `iters` iterations (0
+ * selects 2048). Writes the achieved FP64 GFLOP/s. It decides whether a dense FP64 contraction
+ * of the path belongs on the tensor cores or on the FMA pipe (no counterpart in the paper). */
+mdp_status mdp_probe_dmma_gflops(int iters, double *gflops, void *cuda_stream);
+
 /* Per-kernel timing of a plan's launches (tracing). enable = 1 starts recording a CUDA event
  * pair around every kernel launch of mdp_project_batch / mdp_project_columns / mdp_ap_adjoint
  * on the launch stream (events are created on demand; no device memory is allocated);

@@ -349,3 +349,10 @@ def probe_fp64_gflops(iters: int = 0, stream=None) -> float:
     v = C.c_double()
     _lib.check(_lib.lib().mdp_probe_dfma_gflops(int(iters), C.byref(v), _stream_ptr(stream)), "mdp_probe_dfma_gflops")
     return v.value
+
+
+def probe_dmma_gflops(iters: int = 0, stream=None) -> float:
+    """Measured FP64 tensor-core (mma.sync m8n8k4) throughput (GFLOP/s) of the current device."""
+    v = C.c_double()
+    _lib.check(_lib.lib().mdp_probe_dmma_gflops(int(iters), C.byref(v), _stream_ptr(stream)), "mdp_probe_dmma_gflops")
+    return v.value

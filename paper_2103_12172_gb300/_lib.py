@@ -17,7 +17,7 @@ MDP_PLAN_DEDUPE = 0x4
 EXPORTED = [
     "mdp_ap_plan", "mdp_plan_update_k", "mdp_plan_layout", "mdp_plan_output_size", "mdp_project_batch",
     "mdp_project_columns", "mdp_ap_adjoint", "mdp_ap_solve_batch", "mdp_plan_status", "mdp_plan_destroy",
-    "mdp_status_string", "mdp_plan_gamma_geometry", "mdp_host_mode_solve", "mdp_probe_dfma_gflops",
+    "mdp_status_string", "mdp_plan_gamma_geometry", "mdp_host_mode_solve", "mdp_probe_dfma_gflops", "mdp_probe_dmma_gflops",
 ]
 
 
@@ -79,6 +79,7 @@ def lib():
         "mdp_plan_gamma_geometry": (i, [vp, i, C.POINTER(i), C.POINTER(d), C.POINTER(d)]),
         "mdp_host_mode_solve": (i, [vp, i, i, i, vp, vp]),
         "mdp_probe_dfma_gflops": (i, [i, C.POINTER(d), vp]),
+        "mdp_probe_dmma_gflops": (i, [i, C.POINTER(d), vp]),
         "mdp_plan_profile": (i, [vp, i]),
         "mdp_plan_profile_read": (i, [vp, i, C.POINTER(d), C.POINTER(i)]),
         "mdp_kernel_family_count": (i, []),
