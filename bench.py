@@ -83,10 +83,15 @@ def class_workers(cls, workers):
         extra = min(spare, int(round(spare * wt[nx] / tot)) if tot else 0)
         alloc[nx] += extra
     big = max(cls)
-    if big >= 1025 and alloc[big] > 6 and len(cls) > 1:
-        nxt = max((n for n in cls if n != big), key=lambda n: wt[n])
-        alloc[nxt] += alloc[big] - 6
-        alloc[big] = 6
+    cap = {nx: (6 if nx >= 1025 and len(cls) > 1 else workers) for nx in cls}
+    if alloc[big] > cap[big]:
+        alloc[big] = cap[big]
+    # what rounding or the cap left over goes to the heaviest class below its cap
+    while sum(alloc.values()) < workers:
+        open_ = [n for n in cls if alloc[n] < cap[n]]
+        if not open_:
+            break
+        alloc[max(open_, key=lambda n: wt[n] / alloc[n])] += 1
     return alloc
 
 

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmdp.so")
-SOURCES = ["plan.cpp", "kernels.cu", "kernels_adj.cu", "factor.cu", "qr.cu", "api.cu", "probe.cu", "noalloc.cu"]
+SOURCES = ["plan.cpp", "kernels.cu", "kernels_adj.cu", "kernels_tc.cu", "factor.cu", "qr.cu", "api.cu", "probe.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -72,6 +72,7 @@ mdp_status upload_subs_tables(mdp_plan *p) {
 
 mdp_status alloc_device(mdp_plan *p) {
   CK(cudaGetDevice(&p->device));
+  CK(cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device));
   CK(set_kernel_attributes());
   auto al = [&](void **ptr, size_t bytes) -> bool { return cudaMalloc(ptr, std::max<size_t>(bytes, 256)) == cudaSuccess; };
   if (!al((void **)&p->d_subs, p->subs.size() * sizeof(SubDesc)) ||

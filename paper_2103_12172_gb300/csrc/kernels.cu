@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(256) k_residual(Batch bt, const SubDesc *subs,
   const int b = (local % cb) * 32 + threadIdx.x;
   const int u = (local / cb) * 8 + threadIdx.y;
   const int units = d.xsym ? 4 * d.Ph + 2 * (d.Py - 4) : d.R;
+  if (!GRAD && u == 0 && b < it.ncols && d.tc_cols) reinterpret_cast<int *>(ws + it.red_off)[b] = 0;  // for k_tri
   if (b >= it.ncols || u >= units) return;
   double *r = ws + it.r_off;
   double *sb = ws + it.s_off;
@@ -721,6 +722,8 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
   }
   const int ikeep = nhi + 1 - nfirst;
   cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
+  int emax = 0;   // largest biased exponent of the kept rows (integer compares only)
+  auto bexp = [](double v) { return (__double2hiint(v) >> 20) & 0x7ff; };
   for (i = itop; i >= i0; --i) {
     cp_async_wait<TRI_STAGES - 1>();
     __syncwarp(mask);
@@ -738,9 +741,14 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
     }
     __syncwarp(mask);
     if (i - TRI_STAGES >= i0) fetch_back(i - TRI_STAGES); else cp_async_commit();
-    if (i <= ikeep) ystore(i, x);
+    if (i <= ikeep) {
+      ystore(i, x);
+      emax = max(emax, max(bexp(x.re), bexp(x.im)));
+    }
     x2 = x1; x1 = x;
   }
+  // per column, over every mode: the common power-of-two scale of the tensor-core gamma columns
+  if (d.tc_cols) atomicMax(reinterpret_cast<int *>(ws + it.red_off) + b, emax);
 }
 
 template <bool CIN, bool FULL>
@@ -1370,6 +1378,7 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FFT_SMEM);
   if (e == cudaSuccess) e = set_adj_kernel_attributes();
+  if (e == cudaSuccess) e = set_tc_kernel_attributes();
   // the sweep's staging buffers take 32 x 2.4 KiB per SM at full occupancy: prefer shared memory
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tri<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -1407,6 +1416,8 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
     MDP_LAUNCH(F_IROWS, k_inv_rows<true><<<grid1(fb[F_IROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
     MDP_LAUNCH(F_ICOLS, k_inv_cols<true><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
   }
+  if (fb[F_TCOLS].total_blocks > 0)
+    MDP_LAUNCH(F_TCOLS, launch_inv_cols_tc(fb[F_TCOLS], ds, tab, ws, xi_user, out, out_kind, p->d_status, p->n_sm, st));
   if (out_rec)
     MDP_LAUNCH(F_IREC, k_inv_rec<<<grid1(fb[F_IREC].total_blocks), b8, 0, st>>>(fb[F_IREC], ds, tab, ws, out_rec, basis ? 0 : 1));
   return cudaGetLastError();

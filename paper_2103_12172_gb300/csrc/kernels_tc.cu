@@ -1,0 +1,387 @@
+// k_inv_cols_tc: the inverse sine transform at the 4 gamma columns of the middle rows
+// (Section 3.2.1 / 3.6: the AP solution u(m, n) = (2/Nx) sum_q sin(pi q m/Nx) yhat(q, n), taken
+// only where the trace on gamma needs it, Eqs. def_Pgamma and Q_construction) as a contraction
+// over the mode index q on the tensor cores, to FP64 accuracy.
+//
+// For one middle row n and a tile of 64 columns the sums are a product D = A B with
+//   A[r][q] = yhat(q, n) of matrix row r = (column, real or imaginary part): 128 rows, K = Nq;
+//   B[q][s] = sin(pi q m_s / Nx) for the outputs s (x-centred subdomains: the odd-q and even-q
+//            partial sums at m = mlo-1 and mlo, which give all four gamma columns; otherwise the
+//            four columns mlo-1, mlo, mhi, mhi+1 directly).
+// FP64 accuracy from bf16 operands follows the error-free splitting of Ozaki, Ogita, Oishi and
+// Rump (Numer. Algorithms 59, 2012). Every value of a column is scaled by one power of two (the
+// column's largest exponent) into a signed 54-bit fixed-point integer V, |V| < 2^54, written in
+// 7 balanced base-256 digits d_t in [-128, 127] (V = sum_t d_t 256^(6-t)): adding 128 to every
+// byte position of V makes each byte d_t + 128, so a digit costs one byte permute and one FP32
+// subtraction, and is exact in bf16. B is cut the same way with the fixed scale of |sin| <= 1.
+// A product of two digits is at most 2^14 in magnitude, so a sum over at most 1024 modes is an
+// integer of at most 2^24: exact in the tensor core's FP32 accumulator. That covers Nq <= 2047
+// on centred subdomains (each output sums one parity of q) and Nq <= 1023 otherwise. All 7 x 7
+// digit products are accumulated: D_t = A_t (B_0 .. B_6), one MMA per A digit (M = 128,
+// N = 4 outputs x 8 rows, the 8th of each output zero, K = 16), D in tensor memory (7 x 32 FP32
+// columns). The epilogue reads D back, converts every product sum to an integer, adds those of
+// equal weight t + u in 64-bit integers and scales them into FP64: the only roundings are the
+// truncation of the operands to 54 bits and the final conversions, against FP64's rounding at
+// every step of the plain sum.
+//
+// Work: persistent CTAs (two per SM) walk the tiles (item, middle row, 64 columns) in the same
+// order in all their warps. Eight producer warps cut the values into digits and fill 3
+// shared-memory stages of 16 modes each (canonical K-major layout without swizzle): each thread
+// loads 8 values, coalesced along the column and one stage ahead, and stores one 16-byte
+// core-matrix row per digit. A ninth warp issues the MMAs of a stage once its `full` mbarrier
+// has all 256 producer arrivals and commits them to the stage's `empty` mbarrier, which the
+// producers wait on before refilling it; after the last stage of a tile it commits to `tfull`,
+// and waits on `tempty` (every producer has read D) before the next tile overwrites D. Every wait
+// has a time limit; a wait that runs out sets the plan's status word to MDP_ERR_TIMEOUT and every
+// warp leaves its loop, frees the tensor memory and returns; the two producer halves exchange
+// their partial sums through an mbarrier (`xbar`) with the same limit. The scale of a column is the
+// largest exponent over its modes and kept rows, which the per-mode sweep (k_tri) records as it
+// stores them.
+#include "kernels_common.cuh"
+
+namespace mdp {
+namespace {
+
+constexpr int TC_PRODUCERS = 256;             // 8 warps: matrix row r = 32 (warp % 4) + lane
+constexpr int TC_THREADS = TC_PRODUCERS + 32; // + the MMA warp
+constexpr int TC_KC = 16;                     // modes per stage (one MMA K step)
+constexpr int TC_STAGES = 3;
+constexpr int TC_DIG = 7;                     // balanced base-256 digits of |V| < 2^54
+constexpr int TC_A_BYTES = 128 * TC_KC * 2;   // one digit of A: 128 rows x 16 bf16
+constexpr int TC_B_BYTES = 32 * TC_KC * 2;    // B: 4 outputs x 8 rows x 16 bf16
+constexpr int TC_STAGE_BYTES = TC_DIG * TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_TMEM_COLS = 256;             // D: 7 A digits x 32 FP32 columns
+constexpr long long TC_WAIT_CYCLES = 4000000000LL;   // about 2 s at the maximum clock
+
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  // shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte offsets of
+  // the 8 x 16-byte core matrices, descriptor version 1, no swizzle
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, N = 32, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
+  return ok != 0;
+}
+// wait for the completion of the phase with parity `parity`, at most TC_WAIT_CYCLES; false when
+// the limit ran out or another warp has already given up (*abort)
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, volatile int *abort) {
+  const long long t0 = clock64();
+  while (!mbar_try(addr, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > TC_WAIT_CYCLES) { *abort = 1; return false; }
+  }
+  return true;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(unsigned mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float *v) {
+  unsigned r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// x as the signed fixed-point integer trunc(x 2^(54 - (E - 1022))), |.| < 2^54, for a column
+// whose largest biased exponent is E (E >= 64; values of exponent e are shifted by E - e >= 0,
+// zeros and subnormals by at least 64, i.e. to 0), plus 0x0080808080808080: byte t of the
+// result is the balanced digit t plus 128. Returned as (hi, lo).
+__device__ __forceinline__ void digits54(double x, int E, unsigned &hi, unsigned &lo) {
+  const unsigned xh = (unsigned)__double2hiint(x), xl = (unsigned)__double2loint(x);
+  const int e = (xh >> 20) & 0x7ff;
+  const unsigned h = (((xh & 0xFFFFFu) | 0x100000u) << 1) | (xl >> 31);   // significand << 1: 54 bits
+  const unsigned long long m = ((unsigned long long)h << 32) | (xl << 1);
+  const unsigned long long v = m >> min(E - e, 63);
+  const long long sv = ((int)xh < 0) ? -(long long)v : (long long)v;
+  const unsigned long long w = (unsigned long long)sv + 0x0080808080808080ull;
+  hi = (unsigned)(w >> 32);
+  lo = (unsigned)w;
+}
+
+// FP32 bits of the balanced digit in byte K (0 = least significant) of (hi, lo): the byte
+// placed under the exponent of 2^23, minus 2^23 + 128 (exact)
+template <int K>
+__device__ __forceinline__ unsigned digit_f32(unsigned hi, unsigned lo) {
+  const unsigned src = K >= 4 ? hi : lo;
+  const unsigned sel = (unsigned)(K & 3) | 0x7440u;      // bytes: src byte, 0x00, 0x00, 0x4B
+  const unsigned b = __byte_perm(src, 0x4B000000u, sel);
+  return __float_as_uint(__uint_as_float(b) - 8388736.0f);
+}
+// two bf16 (the high halves of two FP32 values) in one word, the first in the low half
+__device__ __forceinline__ unsigned pack_bf16(unsigned f0, unsigned f1) { return __byte_perm(f0, f1, 0x7632); }
+
+}  // namespace
+
+// One CTA: tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the launch's virtual blocks (F_TCOLS
+// numbering: per item, (Py - 2) middle rows x ceil(ncols / 64) column tiles, column tile fastest).
+template <bool CIN>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    k_inv_cols_tc(Batch bt, const SubDesc *subs, const double *tab, const double *ws, const double2 *xi_user,
+                  double2 *out, int kind, int *status) {
+  extern __shared__ __align__(1024) unsigned char tc_sm[];
+  __shared__ __align__(8) unsigned long long full_bar[TC_STAGES], empty_bar[TC_STAGES], tfull_bar, tempty_bar, xbar;
+  __shared__ unsigned tmem_slot;
+  __shared__ double half_sh[128][5];        // the second producer half's 4 values per row (padded)
+  __shared__ volatile int abort_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_bar[s])), "r"(TC_PRODUCERS) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[s])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull_bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty_bar)), "r"(TC_PRODUCERS) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&xbar)), "r"(TC_PRODUCERS / 2) : "memory");
+    abort_sh = 0;
+  }
+  // the zero rows of B (digit slot 7 of every output) are never written again
+  for (int i = tid; i < TC_STAGES * 4 * TC_KC; i += TC_THREADS) {
+    const int st = i / (4 * TC_KC), so = (i / TC_KC) & 3, kk = i % TC_KC, n = so * 8 + 7;
+    unsigned short *sb = reinterpret_cast<unsigned short *>(tc_sm + st * TC_STAGE_BYTES + TC_DIG * TC_A_BYTES);
+    sb[((n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) >> 1] = 0;
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_slot;
+  const unsigned sbase = smem_u32(tc_sm);
+
+  if (warp == 8) {
+    // ---------------------------------------------------------------- MMA warp
+    if (lane == 0) {
+      unsigned g = 0, T = 0;
+      for (int v = blockIdx.x; v < bt.total_blocks && !abort_sh; v += gridDim.x, ++T) {
+        Item it; int local;
+        locate(bt, v, it, local);
+        const int nchunk = (subs[it.sub].Nq + TC_KC - 1) / TC_KC;
+        if (T > 0 && !mbar_wait(smem_u32(&tempty_bar), (T - 1) & 1u, &abort_sh)) break;
+        tc_fence_after();
+        bool ok = true;
+        for (int c = 0; c < nchunk; ++c, ++g) {
+          const unsigned st = g % TC_STAGES;
+          if (!mbar_wait(smem_u32(&full_bar[st]), (g / TC_STAGES) & 1u, &abort_sh)) { ok = false; break; }
+          tc_fence_after();
+          const unsigned a0 = sbase + st * TC_STAGE_BYTES;
+          const uint64_t db = smem_desc(a0 + TC_DIG * TC_A_BYTES, 128, 256);
+          const unsigned acc = c > 0 ? 1u : 0u;
+#pragma unroll
+          for (int dgt = 0; dgt < TC_DIG; ++dgt) {
+            const uint64_t da = smem_desc(a0 + dgt * TC_A_BYTES, 128, 256);
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + 32u * dgt),
+                "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc)
+                : "memory");
+          }
+          tc_commit(smem_u32(&empty_bar[st]));
+        }
+        if (!ok) break;
+        tc_commit(smem_u32(&tfull_bar));
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- producer warps
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = 32 * quarter + lane;        // matrix row of A (TMEM lane) of this thread
+    unsigned g = 0, T = 0;
+    for (int v = blockIdx.x; v < bt.total_blocks && !abort_sh; v += gridDim.x, ++T) {
+      Item it; int local;
+      locate(bt, v, it, local);
+      const SubDesc &d = subs[it.sub];
+      const bool CD = d.cplx || CIN;
+      const int nct = (it.ncols + 63) >> 6;
+      const int t = local / nct, b0 = (local % nct) * 64;
+      const int yrow = t + 2;                 // middle row n = nlo + 1 + t
+      const int b = b0 + (r >> 1), ri = r & 1;
+      const bool live = b < it.ncols && (CD || ri == 0);
+      const int Nq = d.Nq;
+      const long long ncd = (long long)it.ncols * (CD ? 2 : 1);   // doubles per stored row
+      const long long qstride = (long long)d.NYf * ncd;
+      const double *y = ws + it.y_off + (long long)yrow * ncd + (CD ? 2LL * b + ri : (long long)b);
+      const int nchunk = (Nq + TC_KC - 1) / TC_KC;
+      // the column's scale: its largest biased exponent, recorded by k_tri (at least 64)
+      const int E = max(live ? reinterpret_cast<const int *>(ws + it.red_off)[b] : 0, 64);
+      // output columns of B: x-centred -> (odd q, m0), (odd q, m1), (even q, m0), (even q, m1)
+      const int N2 = 2 * d.Nx;
+      const double *sn = tab + d.sin_off;
+      int msel = 0, par = -1;
+      if (tid < 4 * TC_KC) {
+        const int so = tid / TC_KC;
+        if (d.xsym) { msel = (so & 1) ? d.mlo : d.mlo - 1; par = (so < 2) ? 1 : 0; }
+        else msel = so == 0 ? d.mlo - 1 : so == 1 ? d.mlo : so == 2 ? d.mhi : d.mhi + 1;
+      }
+      // this thread's 8 modes of a stage: the current ones in xv, the next ones in flight in xn
+      double xv[8], xn[8];
+      auto load8 = [&](double *dst, int c) {
+        const int q0 = c * TC_KC + 1 + 8 * half;
+        const double *p = y + (long long)(q0 - 1) * qstride;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          dst[j] = (live && q0 + j <= Nq) ? *p : 0.0;
+          p += qstride;
+        }
+      };
+      load8(xv, 0);
+      bool ok = true;
+      for (int c = 0; c < nchunk; ++c, ++g) {
+        if (c + 1 < nchunk) load8(xn, c + 1);
+        const unsigned st = g % TC_STAGES;
+        // the stage is free once the MMAs that last read it have completed
+        if (g >= TC_STAGES && !mbar_wait(smem_u32(&empty_bar[st]), (g / TC_STAGES - 1) & 1u, &abort_sh)) {
+          ok = false;
+          break;
+        }
+        unsigned char *sa = tc_sm + st * TC_STAGE_BYTES;
+        {
+          unsigned hi[8], lo[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) digits54(xv[j], E, hi[j], lo[j]);
+          const int off = (r >> 3) * 256 + half * 128 + (r & 7) * 16;   // SBO 256 B, LBO 128 B
+#define MDP_TC_DIGIT(T)                                                                                     \
+  {                                                                                                         \
+    uint4 w;                                                                                                \
+    w.x = pack_bf16(digit_f32<6 - (T)>(hi[0], lo[0]), digit_f32<6 - (T)>(hi[1], lo[1]));                    \
+    w.y = pack_bf16(digit_f32<6 - (T)>(hi[2], lo[2]), digit_f32<6 - (T)>(hi[3], lo[3]));                    \
+    w.z = pack_bf16(digit_f32<6 - (T)>(hi[4], lo[4]), digit_f32<6 - (T)>(hi[5], lo[5]));                    \
+    w.w = pack_bf16(digit_f32<6 - (T)>(hi[6], lo[6]), digit_f32<6 - (T)>(hi[7], lo[7]));                    \
+    *reinterpret_cast<uint4 *>(sa + (T) * TC_A_BYTES + off) = w;                                            \
+  }
+          MDP_TC_DIGIT(0) MDP_TC_DIGIT(1) MDP_TC_DIGIT(2) MDP_TC_DIGIT(3) MDP_TC_DIGIT(4) MDP_TC_DIGIT(5)
+          MDP_TC_DIGIT(6)
+#undef MDP_TC_DIGIT
+        }
+        // B digits: 4 outputs x 16 modes, one (output, mode) per thread of the first 64
+        if (tid < 4 * TC_KC) {
+          const int so = tid / TC_KC, kk = tid % TC_KC, q = c * TC_KC + 1 + kk;
+          double sv = 0.0;
+          if (q <= Nq && (par < 0 || (q & 1) == par)) sv = sn[(int)(((long long)q * msel) % N2)];
+          unsigned hi, lo;
+          digits54(sv, 1023, hi, lo);
+          unsigned short *sb = reinterpret_cast<unsigned short *>(sa + TC_DIG * TC_A_BYTES);
+          const unsigned dg[7] = {digit_f32<6>(hi, lo), digit_f32<5>(hi, lo), digit_f32<4>(hi, lo), digit_f32<3>(hi, lo),
+                                  digit_f32<2>(hi, lo), digit_f32<1>(hi, lo), digit_f32<0>(hi, lo)};
+#pragma unroll
+          for (int u = 0; u < TC_DIG; ++u) {
+            const int n = so * 8 + u;         // B row: output so, digit u (row 7: zero)
+            sb[((n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) >> 1] = (unsigned short)(dg[u] >> 16);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> MMA reads
+        mbar_arrive(smem_u32(&full_bar[st]));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xv[j] = xn[j];
+      }
+      if (!ok) break;
+      // ---- epilogue: D_t[r][8 so + u] = sum_q A_t B_u; weight of (t, u): 2^(E - 1033 - 8 (t + u))
+      if (!mbar_wait(smem_u32(&tfull_bar), T & 1u, &abort_sh)) break;
+      tc_fence_after();
+      // products of weight c = t + u, as integers: P0 = sum_{c<=3} I_c 2^(8 (3 - c)),
+      // P1 = sum_{4<=c<=7} I_c 2^(8 (7 - c)), P2 = sum_{c>=8} I_c 2^(8 (12 - c)) (all below 2^60)
+      auto pow2 = [](int k) { return k < -1022 ? 0.0 : __longlong_as_double((long long)(k + 1023) << 52); };
+      const double s0 = pow2(E - 1057), s1 = pow2(E - 1089), s2 = pow2(E - 1129), sc = 2.0 / d.Nx;
+      double val[4];
+#pragma unroll 1
+      for (int so = 0; so < 4; ++so) {
+        long long p0 = 0, p1 = 0, p2 = 0;
+        for (int ta = (half ? 4 : 0); ta < (half ? TC_DIG : 4); ++ta) {
+          float dv[8];
+          tmem_ld8(tmem + ((unsigned)(32 * quarter) << 16) + 32u * ta + 8u * so, dv);
+#pragma unroll
+          for (int u = 0; u < TC_DIG; ++u) {
+            const int cw = ta + u;
+            const long long iv = (long long)__float2int_rn(dv[u]);
+            if (cw <= 3) p0 += iv * (1LL << (8 * (3 - cw)));
+            else if (cw <= 7) p1 += iv * (1LL << (8 * (7 - cw)));
+            else p2 += iv * (1LL << (8 * (12 - cw)));
+          }
+        }
+        val[so] = sc * fma((double)p0, s0, fma((double)p1, s1, (double)p2 * s2));
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&tempty_bar));     // D may be overwritten by the next tile
+      if (half == 1) {
+        for (int so = 0; so < 4; ++so) half_sh[r][so] = val[so];
+        mbar_arrive(smem_u32(&xbar));         // (release: the values above are visible to the waiters)
+      } else {
+        if (!mbar_wait(smem_u32(&xbar), T & 1u, &abort_sh)) break;
+        for (int so = 0; so < 4; ++so) val[so] += half_sh[r][so];
+        double u4[4];
+        if (d.xsym) {
+          u4[0] = val[0] + val[2]; u4[1] = val[1] + val[3]; u4[2] = val[1] - val[3]; u4[3] = val[0] - val[2];
+        } else {
+          u4[0] = val[0]; u4[1] = val[1]; u4[2] = val[2]; u4[3] = val[3];
+        }
+        // lanes 2i (real part) and 2i+1 (imaginary part) of column b: the even lane writes
+        double o4[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) o4[s] = __shfl_xor_sync(0xffffffffu, u4[s], 1);
+        if (ri == 0 && b < it.ncols) {
+          const int g0 = 2 * (d.Px + 2) + 4 * t;
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            cplx uv = cmk(-u4[s], CD ? -o4[s] : 0.0);
+            if (kind == MDP_OUT_P) uv = cadd(uv, density<CIN>(d, it, ws, tab, xi_user, b, g0 + s));
+            out[it.io_off + (long long)b * d.G + g0 + s] = make_double2(uv.re, uv.im);
+          }
+        }
+      }
+      // half_sh is rewritten only in the next tile's epilogue, which no producer reaches before
+      // every producer has filled that tile's stages (and so finished reading here)
+    }
+  }
+  if (abort_sh && tid == 0) atomicCAS(status, 0, (int)MDP_ERR_TIMEOUT);   // the first error sticks
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 8)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+}
+
+int tc_cols_smem_bytes() { return TC_STAGES * TC_STAGE_BYTES; }
+
+cudaError_t set_tc_kernel_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_inv_cols_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tc_cols_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_inv_cols_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_cols_smem_bytes());
+  return e;
+}
+
+cudaError_t launch_inv_cols_tc(const Batch &b, const SubDesc *subs, const double *tab, const double *ws,
+                               const double2 *xi_user, double2 *out, int kind, int *status, int n_sm,
+                               cudaStream_t st) {
+  const int grid = std::max(1, std::min(b.total_blocks, 2 * n_sm));
+  if (xi_user)
+    k_inv_cols_tc<true><<<grid, TC_THREADS, tc_cols_smem_bytes(), st>>>(b, subs, tab, ws, xi_user, out, kind, status);
+  else
+    k_inv_cols_tc<false><<<grid, TC_THREADS, tc_cols_smem_bytes(), st>>>(b, subs, tab, ws, xi_user, out, kind, status);
+  return cudaGetLastError();
+}
+
+}  // namespace mdp

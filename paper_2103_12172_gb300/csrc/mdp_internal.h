@@ -37,6 +37,7 @@ struct SubDesc {
   int rows_fft;     // inverse transform of the gamma rows by FFT (Nx a power of 2, 2Nx <= 4096)
   int fpb;          // FFTs (columns) per block of the dense-row kernels: max(1, 1024 / (2 Nx))
   int leader;       // index of the subdomain owning this one's tables (itself unless deduplicated)
+  int tc_cols;      // 1: the gamma columns of the middle rows are summed on the tensor cores (k_inv_cols_tc)
   double h, k;
   double x0, x1, y0, y1, ax0, ay0;
   double c0, c1, c2;  // 9-point coefficients: centre, edge, corner (Eq. FD_scheme)
@@ -63,7 +64,8 @@ struct Item {
   long long y_off;    // mode-space field [Nq][NY][ncols]
   long long a_off;    // adjoint mode-space field [Nq][Nt][ncols] (gradient pass)
   long long s_off;    // gradient source on the ring [R][ncols] (complex)
-  long long red_off;  // per-block partial sums of the k-gradient
+  long long red_off;  // per-block partial sums of the k-gradient (gradient pass); in the projection,
+                      // per column the largest biased exponent of the stored mode-space rows (int)
   long long io_off;   // complex elements: column col0 of this item in xi / out / cot / grad_xi
 };
 
@@ -164,6 +166,7 @@ struct mdp_plan {
   int *d_status = nullptr;
   int *d_fstatus = nullptr;               // status word of the device factorisation
   int fft_smem = 16;                     // dynamic shared memory of the FFT kernels: max fpb * 2 Nx * 16 B
+  int n_sm = 0;                          // multiprocessors of the plan's device (persistent grids)
   mdp::HostBuf<mdp::SubDesc> sub_stage;  // pinned copy of the subdomain descriptors (async upload)
   mdp::HostBuf<int> h_fstatus;           // pinned read-back of d_fstatus
   bool host_stale = false;               // device tables refactored since the host tables were built
@@ -200,7 +203,7 @@ enum Sched { S_PROJ = 0, S_GRAD = 1, S_BASIS = 2 };
 
 // kernel families (each has its own block decomposition of an item); F_A* are the adjoint's
 enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_ARINGC, F_AGAM, F_IREC,
-           F_ACOLS, NFAM };
+           F_ACOLS, F_TCOLS, NFAM };
 
 // Blocks of kernel family f for an item of ncols columns: 32 columns (x) times BY tasks (y).
 // The same function numbers the blocks on the host (prefix sums) and in the kernels.
@@ -216,7 +219,8 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
     case F_IROWS:
       if (d.rows_fft) return 4 * ((ncols + d.fpb - 1) / d.fpb);
       return cb * (((d.xsym ? 4 * (d.Ph + 1) : 4 * (d.Px + 2)) + 7) / 8);
-    case F_ICOLS: return cb * ((d.Py - 2 + 7) / 8);
+    case F_ICOLS: return d.tc_cols ? 0 : cb * ((d.Py - 2 + 7) / 8);
+    case F_TCOLS: return d.tc_cols ? ((ncols + 63) / 64) * (d.Py - 2) : 0;   // tiles: middle row x 64 columns
     case F_AFWD:
       if (d.rows_fft) return 5 * ((ncols + d.fpb - 1) / d.fpb);
       return cb * ((d.Nx / 2 + 7) / 8);
@@ -259,6 +263,11 @@ void host_mode_solve(const HostSub &hs, int q, int adjoint, const double *b, dou
 enum { PASS_FWD = 0, PASS_GRAD = 1 };
 cudaError_t set_kernel_attributes();      // kernels.cu: opt-in shared memory of the FFT kernels
 cudaError_t set_adj_kernel_attributes();  // kernels_adj.cu
+cudaError_t set_tc_kernel_attributes();   // kernels_tc.cu
+// the gamma columns of the middle rows on the tensor cores (items whose subdomain has tc_cols)
+cudaError_t launch_inv_cols_tc(const Batch &b, const SubDesc *subs, const double *tab, const double *ws,
+                               const double2 *xi_user, double2 *out, int kind, int *status, int n_sm,
+                               cudaStream_t st);
 cudaError_t launch_project(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,
                            double2 *out, double2 *out_rec, cudaStream_t st);
 cudaError_t launch_adjoint(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,

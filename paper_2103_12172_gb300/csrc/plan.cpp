@@ -23,7 +23,7 @@ static const double kSingularTol = 1e-13; // pivot below this x max|T| -> singul
 const char *fam_name(int f) {
   static const char *names[NFAM] = {"k_extend", "k_residual", "k_fwd_rows", "k_tri", "k_inv_rows", "k_inv_cols",
                                     "k_adj_rows", "k_adj_tri", "k_adj_ring_rows", "k_adj_ring_cols", "k_adj_gamma",
-                                    "k_inv_rec", "k_adj_cols"};
+                                    "k_inv_rec", "k_adj_cols", "k_inv_cols_tc"};
   return (f >= 0 && f < NFAM) ? names[f] : "?";
 }
 
@@ -39,7 +39,9 @@ void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long 
   s = off;  off += grad ? al((long long)d.R * ncols * 2) : 0;
   int rs[5];
   red_slots(d, ncols, rs);
-  red = off; off += grad ? al(rs[4] + 1) : 0;
+  // gradient pass: per-block partial sums of the k-gradient; projection: per column the largest
+  // biased exponent of the stored mode-space rows (ints, for the tensor-core gamma columns)
+  red = off; off += grad ? al(rs[4] + 1) : al((ncols + 1) / 2);
   total = off;
 }
 
@@ -81,6 +83,13 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   d.nrec = -1;
   d.rows_fft = (d.Nx & (d.Nx - 1)) == 0 && 2 * d.Nx <= FFT_POINTS && d.Nx >= 8;
   d.fpb = d.rows_fft ? std::max(1, FFT_BLOCK_POINTS / (2 * d.Nx)) : 0;
+  // gamma columns on the tensor cores: exact integer accumulation needs at most 512 modes per
+  // output (a parity half of Nq on centred subdomains); MDP_TC_COLS=0 keeps the FP64 sums
+  {
+    const char *tc = std::getenv("MDP_TC_COLS");
+    const bool on = !(tc && tc[0] == '0' && tc[1] == 0);
+    d.tc_cols = on && (d.xsym ? d.Nq <= 1023 : d.Nq <= 511);
+  }
   d.nfirst = d.cplx ? 0 : 1;
   d.Nt = d.cplx ? in.ny : in.ny - 2;
   d.i0 = (nlo - 1) - d.nfirst;
