@@ -83,12 +83,12 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   d.nrec = -1;
   d.rows_fft = (d.Nx & (d.Nx - 1)) == 0 && 2 * d.Nx <= FFT_POINTS && d.Nx >= 8;
   d.fpb = d.rows_fft ? std::max(1, FFT_BLOCK_POINTS / (2 * d.Nx)) : 0;
-  // gamma columns on the tensor cores: exact integer accumulation needs at most 512 modes per
+  // gamma columns on the tensor cores: exact integer accumulation needs at most 1024 modes per
   // output (a parity half of Nq on centred subdomains); MDP_TC_COLS=0 keeps the FP64 sums
   {
     const char *tc = std::getenv("MDP_TC_COLS");
     const bool on = !(tc && tc[0] == '0' && tc[1] == 0);
-    d.tc_cols = on && (d.xsym ? d.Nq <= 1023 : d.Nq <= 511);
+    d.tc_cols = on && (d.xsym ? d.Nq <= 2047 : d.Nq <= 1023);
   }
   d.nfirst = d.cplx ? 0 : 1;
   d.Nt = d.cplx ? in.ny : in.ny - 2;

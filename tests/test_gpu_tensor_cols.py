@@ -88,19 +88,25 @@ def test_tensor_core_columns_wide_dynamic_range(mdp):
 
 
 def test_tensor_core_columns_at_the_exactness_limit(mdp):
-    """Nq = 1023 (1025^2 grid): each parity half of the modes has 512 terms, the most that keep
-    every digit-product sum below 2^23; equal to the FP64 sums."""
-    sub = W.small_subdomain(1025, 60.0, W.AP_DIRX_SOMMY, 2)
+    """Nq = 2047 (2049^2 grid): each parity half of the modes has 1024 terms, the most that keep
+    every digit-product sum within 2^24; equal to the FP64 sums."""
+    sub = W.small_subdomain(2049, 60.0, W.AP_DIRX_SOMMY, 2)
     got, prof = project(mdp, [sub], True)
     ref64, _ = project(mdp, [sub], False)
     assert prof.get("k_inv_cols_tc", (0, 0))[1] > 0
     assert rel_col_err(got, ref64) < 1e-12
 
 
-def test_off_centre_grid_beyond_the_limit_keeps_fp64_sums(mdp):
-    """An off-centre subdomain with Nq = 600 > 511 (no parity halving) takes the FP64 kernel."""
-    sub = off_centre(601, 20.0, 2)
+def test_off_centre_grids_at_and_beyond_the_limit(mdp):
+    """Off-centre subdomains sum all modes into every output: Nq = 1023 is on the tensor cores
+    (equal to the FP64 sums), Nq = 1100 > 1023 keeps the FP64 kernel."""
+    sub = off_centre(1025, 40.0, 2)
     got, prof = project(mdp, [sub], True)
+    ref64, _ = project(mdp, [sub], False)
+    assert prof.get("k_inv_cols_tc", (0, 0))[1] > 0, prof
+    assert rel_col_err(got, ref64) < 1e-12
+    sub = off_centre(1101, 40.0, 2)
+    got, prof = project(mdp, [sub], True)
+    ref64, _ = project(mdp, [sub], False)
     assert prof.get("k_inv_cols", (0, 0))[1] > 0 and "k_inv_cols_tc" not in prof, prof
-    ref = APSystem(sub).columns(cols=[0, 5, 11])
-    assert rel_col_err(got[[0, 5, 11]], ref) < 1e-10
+    assert np.array_equal(got, ref64)
