@@ -8,12 +8,16 @@
 //   B[q][s] = sin(pi q m_s / Nx) for the outputs s (x-centred subdomains: the odd-q and even-q
 //            partial sums at m = mlo-1 and mlo, which give all four gamma columns; otherwise the
 //            four columns mlo-1, mlo, mhi, mhi+1 directly).
-// FP64 accuracy from bf16 operands follows the error-free splitting of Ozaki, Ogita, Oishi and
-// Rump (Numer. Algorithms 59, 2012). Every value of a column is scaled by one power of two (the
-// column's largest exponent) into a signed 54-bit fixed-point integer V, |V| < 2^54, written in
-// 7 balanced base-256 digits d_t in [-128, 127] (V = sum_t d_t 256^(6-t)): adding 128 to every
-// byte position of V makes each byte d_t + 128, so a digit costs one byte permute and one FP32
-// subtraction, and is exact in bf16. B is cut the same way with the fixed scale of |sin| <= 1.
+// FP64 accuracy from fp16 operands follows the error-free splitting of Ozaki, Ogita, Oishi and
+// Rump (Numer. Algorithms 59, 2012). Every value x of a column becomes a signed fixed-point
+// integer V on one scale common to the column: with p set by the column's largest exponent
+// (|x| < 2^(p-1)), the FP64 sum y = x + 1.5 2^p stays in the binade of 1.5 2^p, so its bit
+// pattern minus that of 1.5 2^p is V = round(x / 2^(p-52)), |V| < 2^51 (one FP64 add per value,
+// on a pipe this kernel leaves free). V is written in 7 balanced base-256 digits d_t in
+// [-128, 127] (V = sum_t d_t 256^(6-t)): adding 128 to every byte position of V makes each byte
+// d_t + 128, so two digits cost a byte permute, a mask and one packed fp16 subtraction, and are
+// exact in fp16. B, the sine factors, is cut the same way with the fixed scale of |sin| <= 1,
+// once, when the plan is built (a 1 KiB block per 16 modes in the shared-memory operand layout).
 // A product of two digits is at most 2^14 in magnitude, so a sum over at most 1024 modes is an
 // integer of at most 2^24: exact in the tensor core's FP32 accumulator. That covers Nq <= 2047
 // on centred subdomains (each output sums one parity of q) and Nq <= 1023 otherwise. All 7 x 7
@@ -59,8 +63,8 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsig
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
-// instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, N = 32, M = 128
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor of kind::f16: FP32 accumulator, fp16 A and B, both K-major, N = 32, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity) {
   unsigned ok;
@@ -88,45 +92,61 @@ __device__ __forceinline__ void tc_commit(unsigned mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-// 8 consecutive FP32 columns of this warp's 32 TMEM lanes
-__device__ __forceinline__ void tmem_ld8(unsigned taddr, float *v) {
-  unsigned r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float *v) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// x as the signed fixed-point integer trunc(x 2^(54 - (E - 1022))), |.| < 2^54, for a column
-// whose largest biased exponent is E (E >= 64; values of exponent e are shifted by E - e >= 0,
-// zeros and subnormals by at least 64, i.e. to 0), plus 0x0080808080808080: byte t of the
-// result is the balanced digit t plus 128. Returned as (hi, lo).
-__device__ __forceinline__ void digits54(double x, int E, unsigned &hi, unsigned &lo) {
+// The bit pattern of the magic constant 1.5 2^p for a column whose largest biased exponent is E:
+// p = E - 1021 makes every value of the column smaller than 2^(p-1) in magnitude.
+__device__ __forceinline__ long long magic_bits(int E) {
+  return ((long long)(min(max(E, 0), 2044) + 2) << 52) | (1LL << 51);
+}
+// x on the column's fixed-point scale plus 0x0080808080808080 (bytes: balanced digits + 128):
+// the bits of x + 1.5 2^p minus (the bits of 1.5 2^p - 0x0080808080808080) = cb. As (hi, lo).
+__device__ __forceinline__ void digits52(double x, double magic, long long cb, unsigned &hi, unsigned &lo) {
+  const long long w = __double_as_longlong(x + magic) - cb;
+  hi = (unsigned)((unsigned long long)w >> 32);
+  lo = (unsigned)w;
+}
+// The same fixed-point value by integer operations only (for the values the FP64 pipe does not
+// take): the significand m (53 bits) of x, exponent e, gives V = trunc(m 2^(e - E - 2)) on the
+// column scale of magic_bits(E); zeros and subnormals give 0 (their shift is at least 64 when
+// E >= 62; the column's scale then lies far below any value the tile can hold anyway).
+__device__ __forceinline__ void digits52i(double x, int E, unsigned &hi, unsigned &lo) {
   const unsigned xh = (unsigned)__double2hiint(x), xl = (unsigned)__double2loint(x);
   const int e = (xh >> 20) & 0x7ff;
-  const unsigned h = (((xh & 0xFFFFFu) | 0x100000u) << 1) | (xl >> 31);   // significand << 1: 54 bits
-  const unsigned long long m = ((unsigned long long)h << 32) | (xl << 1);
-  const unsigned long long v = m >> min(E - e, 63);
+  const unsigned long long m = ((unsigned long long)((xh & 0xFFFFFu) | 0x100000u) << 32) | xl;
+  const unsigned long long v = e ? m >> min(E + 2 - e, 63) : 0ull;
   const long long sv = ((int)xh < 0) ? -(long long)v : (long long)v;
   const unsigned long long w = (unsigned long long)sv + 0x0080808080808080ull;
   hi = (unsigned)(w >> 32);
   lo = (unsigned)w;
 }
-
-// FP32 bits of the balanced digit in byte K (0 = least significant) of (hi, lo): the byte
-// placed under the exponent of 2^23, minus 2^23 + 128 (exact)
+// two fp16 digits in one word: byte K (0 = least significant) of the values a (low half) and b
+// (high half), each under the fp16 exponent of 1024, minus 1024 + 128 (exact)
 template <int K>
-__device__ __forceinline__ unsigned digit_f32(unsigned hi, unsigned lo) {
-  const unsigned src = K >= 4 ? hi : lo;
-  const unsigned sel = (unsigned)(K & 3) | 0x7440u;      // bytes: src byte, 0x00, 0x00, 0x4B
-  const unsigned b = __byte_perm(src, 0x4B000000u, sel);
-  return __float_as_uint(__uint_as_float(b) - 8388736.0f);
+__device__ __forceinline__ unsigned digit_pair(unsigned ahi, unsigned alo, unsigned bhi, unsigned blo) {
+  constexpr unsigned k = K & 3;
+  constexpr unsigned sel = k | (k << 4) | ((4 + k) << 8) | ((4 + k) << 12);
+  const unsigned w = __byte_perm(K >= 4 ? ahi : alo, K >= 4 ? bhi : blo, sel);
+  unsigned r;
+  asm("{\n .reg .b32 t;\n lop3.b32 t, %1, %2, %3, 0xEA;\n sub.rn.f16x2 %0, t, %4;\n}\n"
+      : "=r"(r) : "r"(w), "r"(0x00FF00FFu), "r"(0x64006400u), "r"(0x64806480u));
+  return r;
 }
-// two bf16 (the high halves of two FP32 values) in one word, the first in the low half
-__device__ __forceinline__ unsigned pack_bf16(unsigned f0, unsigned f1) { return __byte_perm(f0, f1, 0x7632); }
 
 }  // namespace
 
@@ -151,12 +171,6 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty_bar)), "r"(TC_PRODUCERS) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&xbar)), "r"(TC_PRODUCERS / 2) : "memory");
     abort_sh = 0;
-  }
-  // the zero rows of B (digit slot 7 of every output) are never written again
-  for (int i = tid; i < TC_STAGES * 4 * TC_KC; i += TC_THREADS) {
-    const int st = i / (4 * TC_KC), so = (i / TC_KC) & 3, kk = i % TC_KC, n = so * 8 + 7;
-    unsigned short *sb = reinterpret_cast<unsigned short *>(tc_sm + st * TC_STAGE_BYTES + TC_DIG * TC_A_BYTES);
-    sb[((n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) >> 1] = 0;
   }
   if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -225,17 +239,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       const long long qstride = (long long)d.NYf * ncd;
       const double *y = ws + it.y_off + (long long)yrow * ncd + (CD ? 2LL * b + ri : (long long)b);
       const int nchunk = (Nq + TC_KC - 1) / TC_KC;
-      // the column's scale: its largest biased exponent, recorded by k_tri (at least 64)
-      const int E = max(live ? reinterpret_cast<const int *>(ws + it.red_off)[b] : 0, 64);
-      // output columns of B: x-centred -> (odd q, m0), (odd q, m1), (even q, m0), (even q, m1)
-      const int N2 = 2 * d.Nx;
-      const double *sn = tab + d.sin_off;
-      int msel = 0, par = -1;
-      if (tid < 4 * TC_KC) {
-        const int so = tid / TC_KC;
-        if (d.xsym) { msel = (so & 1) ? d.mlo : d.mlo - 1; par = (so < 2) ? 1 : 0; }
-        else msel = so == 0 ? d.mlo - 1 : so == 1 ? d.mlo : so == 2 ? d.mhi : d.mhi + 1;
-      }
+      // the column's scale: its largest biased exponent, recorded by k_tri, and its magic constant
+      const int E = live ? reinterpret_cast<const int *>(ws + it.red_off)[b] : 0;
+      const long long mb = magic_bits(E);
+      const double magic = __longlong_as_double(mb);
+      const long long cb = mb - 0x0080808080808080LL;
       // this thread's 8 modes of a stage: the current ones in xv, the next ones in flight in xn
       double xv[8], xn[8];
       auto load8 = [&](double *dst, int c) {
@@ -261,68 +269,69 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         {
           unsigned hi[8], lo[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) digits54(xv[j], E, hi[j], lo[j]);
+          for (int j = 0; j < 8; ++j) {
+            // the FP64 add takes half the values, the integer pipes the other half: each alone
+            // would bound the stage
+            if (j & 1) digits52i(xv[j], E, hi[j], lo[j]);
+            else digits52(xv[j], magic, cb, hi[j], lo[j]);
+          }
           const int off = (r >> 3) * 256 + half * 128 + (r & 7) * 16;   // SBO 256 B, LBO 128 B
 #define MDP_TC_DIGIT(T)                                                                                     \
   {                                                                                                         \
     uint4 w;                                                                                                \
-    w.x = pack_bf16(digit_f32<6 - (T)>(hi[0], lo[0]), digit_f32<6 - (T)>(hi[1], lo[1]));                    \
-    w.y = pack_bf16(digit_f32<6 - (T)>(hi[2], lo[2]), digit_f32<6 - (T)>(hi[3], lo[3]));                    \
-    w.z = pack_bf16(digit_f32<6 - (T)>(hi[4], lo[4]), digit_f32<6 - (T)>(hi[5], lo[5]));                    \
-    w.w = pack_bf16(digit_f32<6 - (T)>(hi[6], lo[6]), digit_f32<6 - (T)>(hi[7], lo[7]));                    \
+    w.x = digit_pair<6 - (T)>(hi[0], lo[0], hi[1], lo[1]);                                                 \
+    w.y = digit_pair<6 - (T)>(hi[2], lo[2], hi[3], lo[3]);                                                 \
+    w.z = digit_pair<6 - (T)>(hi[4], lo[4], hi[5], lo[5]);                                                 \
+    w.w = digit_pair<6 - (T)>(hi[6], lo[6], hi[7], lo[7]);                                                 \
     *reinterpret_cast<uint4 *>(sa + (T) * TC_A_BYTES + off) = w;                                            \
   }
           MDP_TC_DIGIT(0) MDP_TC_DIGIT(1) MDP_TC_DIGIT(2) MDP_TC_DIGIT(3) MDP_TC_DIGIT(4) MDP_TC_DIGIT(5)
           MDP_TC_DIGIT(6)
 #undef MDP_TC_DIGIT
         }
-        // B digits: 4 outputs x 16 modes, one (output, mode) per thread of the first 64
-        if (tid < 4 * TC_KC) {
-          const int so = tid / TC_KC, kk = tid % TC_KC, q = c * TC_KC + 1 + kk;
-          double sv = 0.0;
-          if (q <= Nq && (par < 0 || (q & 1) == par)) sv = sn[(int)(((long long)q * msel) % N2)];
-          unsigned hi, lo;
-          digits54(sv, 1023, hi, lo);
-          unsigned short *sb = reinterpret_cast<unsigned short *>(sa + TC_DIG * TC_A_BYTES);
-          const unsigned dg[7] = {digit_f32<6>(hi, lo), digit_f32<5>(hi, lo), digit_f32<4>(hi, lo), digit_f32<3>(hi, lo),
-                                  digit_f32<2>(hi, lo), digit_f32<1>(hi, lo), digit_f32<0>(hi, lo)};
-#pragma unroll
-          for (int u = 0; u < TC_DIG; ++u) {
-            const int n = so * 8 + u;         // B row: output so, digit u (row 7: zero)
-            sb[((n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) >> 1] = (unsigned short)(dg[u] >> 16);
-          }
-        }
+        // B: the plan's 1 KiB block of sine digits for these 16 modes, 16 bytes per thread
+        if (tid < 64)
+          *reinterpret_cast<uint4 *>(sa + TC_DIG * TC_A_BYTES + 16 * tid) =
+              reinterpret_cast<const uint4 *>(tab + d.tcb_off)[c * 64 + tid];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> MMA reads
         mbar_arrive(smem_u32(&full_bar[st]));
 #pragma unroll
         for (int j = 0; j < 8; ++j) xv[j] = xn[j];
       }
       if (!ok) break;
-      // ---- epilogue: D_t[r][8 so + u] = sum_q A_t B_u; weight of (t, u): 2^(E - 1033 - 8 (t + u))
+      // ---- epilogue: D_t[r][8 so + u] = sum_q A_t B_u. x = V 2^(E - 1073), sin = W 2^-50, so the
+      // weight of (t, u) is 2^(E - 1123 + 8 (12 - t - u)) = 2^(E - 1027 - 8 (t + u))
       if (!mbar_wait(smem_u32(&tfull_bar), T & 1u, &abort_sh)) break;
       tc_fence_after();
       // products of weight c = t + u, as integers: P0 = sum_{c<=3} I_c 2^(8 (3 - c)),
       // P1 = sum_{4<=c<=7} I_c 2^(8 (7 - c)), P2 = sum_{c>=8} I_c 2^(8 (12 - c)) (all below 2^60)
       auto pow2 = [](int k) { return k < -1022 ? 0.0 : __longlong_as_double((long long)(k + 1023) << 52); };
-      const double s0 = pow2(E - 1057), s1 = pow2(E - 1089), s2 = pow2(E - 1129), sc = 2.0 / d.Nx;
-      double val[4];
-#pragma unroll 1
-      for (int so = 0; so < 4; ++so) {
-        long long p0 = 0, p1 = 0, p2 = 0;
-        for (int ta = (half ? 4 : 0); ta < (half ? TC_DIG : 4); ++ta) {
-          float dv[8];
-          tmem_ld8(tmem + ((unsigned)(32 * quarter) << 16) + 32u * ta + 8u * so, dv);
+      const int Ec = min(max(E, 0), 2044);
+      const double s0 = pow2(Ec - 1051), s1 = pow2(Ec - 1083), s2 = pow2(Ec - 1123), sc = 2.0 / d.Nx;
+      long long acc[4][3];
+#pragma unroll
+      for (int so = 0; so < 4; ++so) acc[so][0] = acc[so][1] = acc[so][2] = 0;
+      // this warp's A digits: 0..3 (first half) or 4..6 (second half), one load and wait each
+#pragma unroll
+      for (int ta = 0; ta < TC_DIG; ++ta) {
+        if ((ta < 4) != (half == 0)) continue;
+        float dv[32];
+        tmem_ld32(tmem + ((unsigned)(32 * quarter) << 16) + 32u * ta, dv);
+#pragma unroll
+        for (int so = 0; so < 4; ++so)
 #pragma unroll
           for (int u = 0; u < TC_DIG; ++u) {
             const int cw = ta + u;
-            const long long iv = (long long)__float2int_rn(dv[u]);
-            if (cw <= 3) p0 += iv * (1LL << (8 * (3 - cw)));
-            else if (cw <= 7) p1 += iv * (1LL << (8 * (7 - cw)));
-            else p2 += iv * (1LL << (8 * (12 - cw)));
+            const long long iv = (long long)__float2int_rn(dv[so * 8 + u]);
+            if (cw <= 3) acc[so][0] += iv * (1LL << (8 * (3 - cw)));
+            else if (cw <= 7) acc[so][1] += iv * (1LL << (8 * (7 - cw)));
+            else acc[so][2] += iv * (1LL << (8 * (12 - cw)));
           }
-        }
-        val[so] = sc * fma((double)p0, s0, fma((double)p1, s1, (double)p2 * s2));
       }
+      double val[4];
+#pragma unroll
+      for (int so = 0; so < 4; ++so)
+        val[so] = sc * fma((double)acc[so][0], s0, fma((double)acc[so][1], s1, (double)acc[so][2] * s2));
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar));     // D may be overwritten by the next tile
       if (half == 1) {

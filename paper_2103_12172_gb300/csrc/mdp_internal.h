@@ -50,6 +50,8 @@ struct SubDesc {
   long long seg_off;    // doubles: per mode [Nq][5] = (rlo, rhi, frlo, frhi, itop): real rows of the
                         // factor table, real rows of the forward-sweep table, last swept row
   long long fs_off;     // doubles: projection forward-sweep table [Nq][NYf][FSW] (rows i0..)
+  long long tcb_off;    // doubles: tensor-core gamma columns: per 16 modes a 1 KiB block of the fp16 digits
+                        // of the sines, in the shared-memory operand layout of k_inv_cols_tc
   long long out_off;    // complex elements: start of the subdomain's output block
   long long rec_off;    // complex elements: start of the receiver block [n_cols][Px - 2]
 };

@@ -410,7 +410,7 @@ static bool layout_tables(mdp_plan *p) {
     if (d.leader != (int)(&hs - p->subs.data())) {   // a duplicate: the leader's tables
       const SubDesc &ld = p->subs[d.leader].d;
       d.fact_off = ld.fact_off; d.dT_off = ld.dT_off; d.sin_off = ld.sin_off; d.geo_off = ld.geo_off;
-      d.seg_off = ld.seg_off; d.fs_off = ld.fs_off; d.piv_off = ld.piv_off;
+      d.seg_off = ld.seg_off; d.fs_off = ld.fs_off; d.piv_off = ld.piv_off; d.tcb_off = ld.tcb_off;
       d.out_off = out;  out += (long long)d.G * d.n_cols;
       continue;
     }
@@ -421,6 +421,7 @@ static bool layout_tables(mdp_plan *p) {
     d.geo_off = off;  off += al(4LL * d.G);
     d.seg_off = off;  off += al(5LL * d.Nq);
     d.fs_off = off;   off += al((long long)d.Nq * d.NYf * FSW);
+    d.tcb_off = off;  off += d.tc_cols ? al(128LL * ((d.Nq + 15) / 16)) : 0;
     d.piv_off = poff; poff += al((long long)d.Nq * d.Nt);
     d.out_off = out;  out += (long long)d.G * d.n_cols;
   }
@@ -437,6 +438,49 @@ static bool layout_tables(mdp_plan *p) {
   return true;
 }
 
+// fp16 bit pattern of the integer v, |v| <= 128 (exact)
+static uint16_t f16_of_small_int(int v) {
+  if (v == 0) return 0;
+  const unsigned sgn = v < 0 ? 0x8000u : 0u;
+  unsigned a = (unsigned)std::abs(v);
+  int e = 0;
+  while ((a >> (e + 1)) != 0) ++e;
+  return (uint16_t)(sgn | ((unsigned)(e + 15) << 10) | ((a << (10 - e)) & 0x3FFu));
+}
+
+// The B operand of k_inv_cols_tc (the sine factors of the gamma-column sums) for every 16 modes:
+// row n = 8 so + u holds digit u (u < 7; row 7 zero) of output so, where the outputs are, on a
+// centred subdomain, sin(pi q m/Nx) at m = mlo-1, mlo for odd q, then the same for even q (zero
+// at the other parity), else the columns mlo-1, mlo, mhi, mhi+1. A factor s becomes the integer
+// W = round(s 2^50) through the bits of s + 6 (exact: |s| <= 1 keeps the sum in [4, 8)), written
+// in 7 balanced base-256 digits (the bytes of W + 0x0080808080808080, each minus 128). Stored in
+// the operand layout: 8 x 16-byte core matrices, K (the mode) fastest, 128 B between the two
+// K halves and 256 B between groups of 8 rows.
+static void fill_tc_block(const SubDesc &d, const double *S, uint16_t *blk) {
+  const int nch = (d.Nq + 15) / 16, N2 = 2 * d.Nx;
+  int64_t magic, w;
+  const double six = 6.0;
+  std::memcpy(&magic, &six, 8);
+  for (int c = 0; c < nch; ++c)
+    for (int so = 0; so < 4; ++so)
+      for (int kk = 0; kk < 16; ++kk) {
+        const int q = c * 16 + 1 + kk;
+        int m, par = -1;
+        if (d.xsym) { m = (so & 1) ? d.mlo : d.mlo - 1; par = so < 2 ? 1 : 0; }
+        else m = so == 0 ? d.mlo - 1 : so == 1 ? d.mlo : so == 2 ? d.mhi : d.mhi + 1;
+        const double s = (q <= d.Nq && (par < 0 || (q & 1) == par)) ? S[(int)(((long long)q * m) % N2)] : 0.0;
+        const double y = s + six;
+        std::memcpy(&w, &y, 8);
+        const uint64_t b = (uint64_t)(w - magic) + 0x0080808080808080ull;
+        for (int u = 0; u < 8; ++u) {
+          const int n = so * 8 + u;
+          const int dig = u < 7 ? (int)((b >> (8 * (6 - u))) & 0xFF) - 128 : 0;
+          blk[(size_t)c * 512 + (((n >> 3) * 256 + (kk >> 3) * 128 + (n & 7) * 16 + (kk & 7) * 2) >> 1)] =
+              f16_of_small_int(dig);
+        }
+      }
+}
+
 static void fill_tables(mdp_plan *p) {
   for (auto &hs : p->subs) {
     const SubDesc &d = hs.d;
@@ -447,6 +491,7 @@ static void fill_tables(mdp_plan *p) {
       S[2 * d.Nx + j] = (2.0 / d.Nx) * S[j];
     }
     for (int i = 0; i < 5 * d.Nq; ++i) p->host_tables[d.seg_off + i] = hs.seg[i];
+    if (d.tc_cols) fill_tc_block(d, S, reinterpret_cast<uint16_t *>(&p->host_tables[d.tcb_off]));
     double *g = &p->host_tables[d.geo_off];
     for (int i = 0; i < d.G; ++i) {
       g[4 * i + 0] = hs.owner[i];
