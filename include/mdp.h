@@ -51,7 +51,9 @@ typedef enum {
   MDP_ERR_NOMEM = 3,     /* device or host allocation failed in mdp_ap_plan */
   MDP_ERR_SINGULAR = 4,  /* a tridiagonal pivot below tolerance (discrete AP resonance) */
   MDP_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
-  MDP_ERR_STATE = 6      /* call not valid for this plan (e.g. host-only plan) */
+  MDP_ERR_STATE = 6,     /* call not valid for this plan (e.g. host-only plan) */
+  MDP_ERR_BOUNDS = 7     /* an index out of its table, workspace slice or output range, found and skipped
+                            by the bounds-checked build (libmdp_checked.so, MDP_CHECKED=1) */
 } mdp_status;
 
 enum { MDP_AP_DIRICHLET4 = 0, MDP_AP_DIRX_SOMMY = 1, MDP_AP_DIRX_SOMMY_PAPER = 2 };

@@ -16,6 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmdp.so")
+LIB_CHECKED = os.path.join(PKG, "libmdp_checked.so")   # MDP_CHECKED=1: bounds-checked kernels
 SOURCES = ["plan.cpp", "kernels.cu", "kernels_adj.cu", "kernels_tc.cu", "factor.cu", "qr.cu", "api.cu", "probe.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,19 +40,25 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if needed) and return the path of libmdp.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False, both: bool = False) -> str:
+    """Compile (if needed) and return the path of libmdp.so, or of the bounds-checked
+    libmdp_checked.so (checked=True: every translation unit with -DMDP_CHECKED=1). both=True
+    builds the two libraries (the translation units of both in one parallel pass)."""
+    variants = [False, True] if both else [checked]
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "mdp.h"))
-    objs = []
-    jobs = []
-    for src in SOURCES:
-        path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src + ".o")
-        objs.append(obj)
-        if force or _stale(obj, [path] + headers):
-            jobs.append([_nvcc()] + _flags() + ["-c", path, "-o", obj])
+    jobs, links = [], []
+    for chk in variants:
+        bdir = os.path.join(BUILD, "checked") if chk else BUILD
+        os.makedirs(bdir, exist_ok=True)
+        objs = []
+        for src in SOURCES:
+            path = os.path.join(CSRC, src)
+            obj = os.path.join(bdir, src + ".o")
+            objs.append(obj)
+            if force or _stale(obj, [path] + headers):
+                jobs.append([_nvcc()] + _flags() + (["-DMDP_CHECKED=1"] if chk else []) + ["-c", path, "-o", obj])
+        links.append((LIB_CHECKED if chk else LIB, objs))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -62,9 +69,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        run([_nvcc()] + ARCH + ["-shared", "-o", LIB] + objs + ["-lcudart"])
-    return LIB
+    for lib, objs in links:
+        if force or _stale(lib, objs):
+            run([_nvcc()] + ARCH + ["-shared", "-o", lib] + objs + ["-lcudart"])
+    return links[-1][0]
 
 
 if __name__ == "__main__":

@@ -5,9 +5,10 @@ import ctypes as C
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libmdp.so")
+# MDP_LIB_CHECKED=1 loads the bounds-checked build (libmdp_checked.so) instead
+LIB_PATH = os.path.join(_PKG, "libmdp_checked.so" if os.environ.get("MDP_LIB_CHECKED") == "1" else "libmdp.so")
 
-MDP_OK, MDP_ERR_ARG, MDP_ERR_CUDA, MDP_ERR_NOMEM, MDP_ERR_SINGULAR, MDP_ERR_TIMEOUT, MDP_ERR_STATE = range(7)
+MDP_OK, MDP_ERR_ARG, MDP_ERR_CUDA, MDP_ERR_NOMEM, MDP_ERR_SINGULAR, MDP_ERR_TIMEOUT, MDP_ERR_STATE, MDP_ERR_BOUNDS = range(8)
 MDP_AP_DIRICHLET4, MDP_AP_DIRX_SOMMY, MDP_AP_DIRX_SOMMY_PAPER = 0, 1, 2
 MDP_OUT_Q, MDP_OUT_P = 0, 1
 MDP_PLAN_HOST_ONLY = 0x1
@@ -46,7 +47,7 @@ def lib():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libmdp.so not found at {LIB_PATH}: build it with "
+        raise ImportError(f"{os.path.basename(LIB_PATH)} not found at {LIB_PATH}: build it with "
                           "`python -c 'import __graft_entry__ as g; g.build()'`")
     L = C.CDLL(LIB_PATH)
     vp, i, ll, d = C.c_void_p, C.c_int, C.c_longlong, C.c_double

@@ -83,6 +83,17 @@ mdp_status alloc_device(mdp_plan *p) {
     return MDP_ERR_NOMEM;
   CK(cudaMemset(p->d_status, 0, sizeof(int)));
   CK(cudaMemset(p->d_fstatus, 0, sizeof(int)));
+  for (auto &hs : p->subs) hs.d.dstatus = p->d_status;
+#if MDP_CHECKED
+  // fault injection (bounds-checked build only): MDP_FAULT_INJECT=factor scales one row of the
+  // first subdomain's factored sweep table (row 5 of mode 1, which every projection column goes
+  // through: wrong numbers, which the parity check must catch), =desc points the first
+  // projection item's mode-space slice past the end of the workspace (the checks must catch it and
+  // skip every access through it)
+  const char *fault = std::getenv("MDP_FAULT_INJECT");
+  if (fault && !std::strcmp(fault, "factor") && !p->subs.empty() && p->subs[0].d.NYf > 6)
+    for (int j = 0; j < FSW; ++j) p->host_tables[p->subs[0].d.fs_off + 5 * FSW + j] *= 1.5;
+#endif
   mdp_status st = upload_subs_tables(p);
   if (st != MDP_OK) return st;
   for (int sc = 0; sc < 3; ++sc) {
@@ -104,6 +115,13 @@ mdp_status alloc_device(mdp_plan *p) {
         for (int i = 0; i < n; ++i)
           pre[(size_t)f * (n + 1) + i + 1] =
               pre[(size_t)f * (n + 1) + i] + blocks_for((Fam)f, p->subs[w.items[i].sub].d, w.items[i].ncols);
+#if MDP_CHECKED
+      if (fault && !std::strcmp(fault, "desc") && sc == S_PROJ && &w == &waves.front() && n > 0) {
+        std::vector<Item> bad(w.items);
+        bad[0].y_off = p->ws_doubles;
+        CK(cudaMemcpy(di, bad.data(), n * sizeof(Item), cudaMemcpyHostToDevice));
+      } else
+#endif
       CK(cudaMemcpy(di, w.items.data(), n * sizeof(Item), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(dp, pre.data(), pre.size() * sizeof(int), cudaMemcpyHostToDevice));
       // launch order of the per-mode sweeps (k_tri, then k_adj_tri), longest first so that the
@@ -145,10 +163,11 @@ void wave_batches(const mdp_plan *p, size_t w, Batch *fb, int sc) {
                             : nullptr;
     b.n_items = n;
     b.total_blocks = p->h_prefix[sc][w][(size_t)f * (n + 1) + n];
+    set_bounds(p, b, p->out_size, sc == S_GRAD);
   }
 }
 
-void single_batches(const mdp_plan *p, const Item &it, Batch *fb) {
+void single_batches(const mdp_plan *p, const Item &it, Batch *fb, long long out_n) {
   for (int f = 0; f < NFAM; ++f) {
     Batch &b = fb[f];
     std::memset(&b, 0, sizeof b);
@@ -157,6 +176,7 @@ void single_batches(const mdp_plan *p, const Item &it, Batch *fb) {
     b.n_items = 1;
     b.one = it;
     b.total_blocks = blocks_for((Fam)f, p->subs[it.sub].d, it.ncols);
+    set_bounds(p, b, out_n, false);
   }
 }
 
@@ -222,6 +242,7 @@ const char *mdp_status_string(mdp_status s) {
     case MDP_ERR_SINGULAR: return "singular tridiagonal system (discrete AP resonance)";
     case MDP_ERR_TIMEOUT: return "device wait timed out";
     case MDP_ERR_STATE: return "call not valid for this plan";
+    case MDP_ERR_BOUNDS: return "index out of range (bounds-checked build)";
   }
   return "unknown status";
 }
@@ -481,7 +502,7 @@ mdp_status mdp_project_columns(mdp_plan *p, int sub, int col0, int ncols, const 
     it.xi_off = xo; it.r_off = ro; it.gr_off = go; it.y_off = yo; it.a_off = ao; it.s_off = so; it.red_off = reo;
     it.io_off = (long long)c * d.G;
     Batch fb[NFAM];
-    single_batches(p, it, fb);
+    single_batches(p, it, fb, (long long)ncols * d.G);
     CK(launch_project(p, fb, out_kind, (const double2 *)xi, (double2 *)out, nullptr, st));
   }
   CK(end_use(p, st));

@@ -26,6 +26,7 @@ namespace mdp {
 __global__ void __launch_bounds__(128) k_extend(Batch bt, const SubDesc *subs, const double *tab, double *ws, int grad) {
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_EXT);
   const SubDesc &d = subs[it.sub];
   const int g = local * 128 + threadIdx.x;
   if (g >= d.G) return;
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(256) k_residual(Batch bt, const SubDesc *subs,
                                                   const double2 *xi_user) {
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_RES);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
@@ -246,6 +248,7 @@ __global__ void __launch_bounds__(256) k_fwd_rows(Batch bt, const SubDesc *subs,
   extern __shared__ double2 fft_sm[];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_FROWS);
   const SubDesc &d = subs[it.sub];
   if (d.rows_fft) { fwd_rows_fft<CIN>(it, d, tab, ws, local, fft_sm); return; }
   const int cb = (it.ncols + 31) >> 5;
@@ -756,6 +759,7 @@ __global__ void __launch_bounds__(32 * TRI_WARPS, 32 / TRI_WARPS) k_tri(Batch bt
                                              double *ws) {
   Item it; int local;
   locate(bt, bt.order ? bt.order[blockIdx.x] : (int)blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_TRI);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
@@ -780,6 +784,7 @@ __global__ void __launch_bounds__(32 * TRI_WARPS, 32 / TRI_WARPS) k_tri(Batch bt
 template <bool CD, bool CIN>
 __device__ __forceinline__ void write_out(const SubDesc &d, const Item &it, const double *ws, const double *tab,
                                           const double2 *xi_user, double2 *out, int kind, int b, int g, cplx u) {
+  if (MDP_CHECKED && (g < 0 || g >= d.G || b < 0 || b >= it.ncols)) { flag_bounds(d.dstatus); return; }
   cplx v = cmk(-u.re, -u.im);
   if (kind == MDP_OUT_P) v = cadd(v, density<CIN>(d, it, ws, tab, xi_user, b, g));
   out[it.io_off + (long long)b * d.G + g] = make_double2(v.re, v.im);
@@ -888,6 +893,7 @@ __global__ void __launch_bounds__(256) k_inv_rows(Batch bt, const SubDesc *subs,
   extern __shared__ double2 fft_sm[];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_IROWS);
   const SubDesc &d = subs[it.sub];
   if (d.rows_fft) {
     if (d.cplx || CIN) inv_rows_fft_body<true, CIN>(it, d, tab, ws, xi_user, out, kind, local, fft_sm);
@@ -972,6 +978,7 @@ __global__ void __launch_bounds__(256) k_inv_cols(Batch bt, const SubDesc *subs,
                                                   const double2 *xi_user, double2 *out, int kind) {
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_ICOLS);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
@@ -1027,6 +1034,7 @@ __global__ void __launch_bounds__(256) k_inv_rec(Batch bt, const SubDesc *subs, 
                                                  double2 *out_rec, int cd) {
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_IREC);
   const SubDesc &d = subs[it.sub];
   if (d.nrec < 0) return;
   const int cb = (it.ncols + 31) >> 5;
@@ -1337,6 +1345,7 @@ cudaError_t launch_source_terms(mdp_plan *p, int sub, const double2 *f, const do
   for (int f_ = 0; f_ < NFAM; ++f_) {
     std::memset(&fb[f_], 0, sizeof fb[f_]);
     fb[f_].n_items = 1; fb[f_].one = it; fb[f_].total_blocks = blocks_for((Fam)f_, d, 1);
+    set_bounds(p, fb[f_], d.G, false);
   }
   e = launch_project(p, fb, MDP_OUT_Q, xi_i, F, nullptr, st);
   if (e != cudaSuccess) return e;
@@ -1357,6 +1366,7 @@ cudaError_t launch_basis_densities(const mdp_plan *p, int sub, int col0, int nco
     Batch b;
     std::memset(&b, 0, sizeof b);
     b.n_items = 1; b.one = it; b.total_blocks = blocks_for(F_EXT, d, it.ncols);
+    set_bounds(p, b, (long long)ncols * d.G, false);
     k_extend<<<dim3((unsigned)b.total_blocks), 128, 0, st>>>(b, p->d_subs, p->d_tables, p->d_ws, 0);
     const long long n = (long long)it.ncols * d.G;
     k_basis_out<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(it, p->d_subs, p->d_tables, p->d_ws,

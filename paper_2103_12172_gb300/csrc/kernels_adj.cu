@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(256) k_adj_rows(Batch bt, const SubDesc *subs,
   extern __shared__ double2 fft_sm[];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_AFWD);
   const SubDesc &d = subs[it.sub];
   if (d.rows_fft) { adj_rows_fft(it, d, tab, ws, cot, cot_rec, local, fft_sm); return; }
   // direct: mode pair (q, Nx - q) per thread
@@ -132,6 +133,7 @@ __global__ void __launch_bounds__(256) k_adj_rows(Batch bt, const SubDesc *subs,
 __global__ void __launch_bounds__(256) k_adj_cols(Batch bt, const SubDesc *subs, double *ws, const double2 *cot) {
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_ACOLS);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
@@ -373,6 +375,7 @@ __global__ void __launch_bounds__(128, 7) k_adj_tri(Batch bt, const SubDesc *sub
   extern __shared__ __align__(16) char adj_sm[];
   Item it; int local;
   locate(bt, bt.order ? bt.order[blockIdx.x] : (int)blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_ATRI);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
@@ -458,6 +461,7 @@ __global__ void __launch_bounds__(256) k_adj_ring_rows(Batch bt, const SubDesc *
   __shared__ double sh[256];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_ARING);
   const SubDesc &d = subs[it.sub];
   double dk = 0.0;
   if (d.rows_fft) {
@@ -506,6 +510,7 @@ __global__ void __launch_bounds__(256) k_adj_ring_cols(Batch bt, const SubDesc *
   __shared__ double sh[256];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_ARINGC);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
@@ -579,6 +584,7 @@ __global__ void __launch_bounds__(256) k_adj_gamma(Batch bt, const SubDesc *subs
   __shared__ double sh[256];
   Item it; int local;
   locate(bt, blockIdx.x, it, local);
+  MDP_CHECK_ITEM(bt, subs, it, local, F_AGAM);
   const SubDesc &d = subs[it.sub];
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;

@@ -55,6 +55,43 @@ __device__ __forceinline__ void locate(const Batch &b, int blk, Item &it, int &l
   local = blk - b.prefix[lo];
 }
 
+// ---------------------------------------------------------------- bounds checks (MDP_CHECKED)
+// The first violation is recorded as MDP_ERR_BOUNDS in the status word; the access is skipped.
+__device__ __forceinline__ void flag_bounds(int *status) {
+  if (status) atomicCAS(status, 0, (int)MDP_ERR_BOUNDS);
+}
+// A block's item against the call's ranges: the subdomain index, the column range, the block
+// number within the kernel family, every workspace slice of the item, every table of the
+// subdomain, its pivot flags, and its columns of the output (or density, cotangent) array.
+static __device__ __noinline__ bool item_in_bounds(const Batch &bt, const SubDesc *subs, const Item &it, int local, int fam,
+                                            bool grad) {
+  bool ok = it.sub >= 0 && it.sub < bt.n_subs && it.ncols >= 1 && local >= 0;
+  if (ok) {
+    const SubDesc &d = subs[it.sub];
+    ok = it.col0 >= 0 && it.col0 + it.ncols <= d.n_cols && local < blocks_for(fam, d, it.ncols);
+    long long xi, r, gr, y, a, s, red, tot;
+    item_workspace(d, it.ncols, grad, xi, r, gr, y, a, s, red, tot);
+    auto in_ws = [&](long long off, long long n) { return off >= 0 && off + n <= bt.ws_n; };
+    ok = ok && in_ws(it.xi_off, r - xi) && in_ws(it.r_off, gr - r) && in_ws(it.gr_off, y - gr) &&
+         in_ws(it.y_off, a - y) && in_ws(it.red_off, tot - red) &&
+         (!grad || (in_ws(it.a_off, s - a) && in_ws(it.s_off, red - s)));
+    auto in_tab = [&](long long off, long long n) { return off >= 0 && off + n <= bt.tab_n; };
+    const long long qt = (long long)d.Nq * d.Nt;
+    ok = ok && in_tab(d.fact_off, qt * (d.cplx ? 8 : 4)) && in_tab(d.dT_off, qt * 6) && in_tab(d.sin_off, 4LL * d.Nx) &&
+         in_tab(d.geo_off, 4LL * d.G) && in_tab(d.seg_off, 5LL * d.Nq) && in_tab(d.fs_off, (long long)d.Nq * d.NYf * FSW) &&
+         (!d.tc_cols || in_tab(d.tcb_off, 128LL * ((d.Nq + 15) / 16)));
+    ok = ok && d.piv_off >= 0 && d.piv_off + qt <= bt.piv_n;
+    ok = ok && it.io_off >= 0 && it.io_off + (long long)it.ncols * d.G <= bt.out_n;
+  }
+  if (!ok) flag_bounds(bt.status);
+  return ok;
+}
+// kernels: leave the block (uniformly: the item is the block's) when its item fails the checks
+#define MDP_CHECK_ITEM(bt, subs, it, local, fam)                                                \
+  do {                                                                                          \
+    if (MDP_CHECKED && !item_in_bounds(bt, subs, it, local, fam, bt.grad != 0)) return;         \
+  } while (0)
+
 // gamma index of node (n, m), or -1 (row-major order of the 2-node ring around M+)
 __device__ __forceinline__ int gamma_index(const SubDesc &d, int n, int m) {
   if (n < d.nlo - 1 || n > d.nhi + 1 || m < d.mlo - 1 || m > d.mhi + 1) return -1;
@@ -121,6 +158,7 @@ __device__ __forceinline__ int col_side(const SubDesc &d, int c) { return (c % (
 template <bool CIN>
 __device__ __forceinline__ cplx density(const SubDesc &d, const Item &it, const double *ws, const double *tab,
                                         const double2 *xi_user, int b, int g) {
+  if (MDP_CHECKED && (g < 0 || g >= d.G || b < 0 || b >= it.ncols)) { flag_bounds(d.dstatus); return cmk(0.0, 0.0); }
   if (!CIN) {
     const int own = (int)tab[d.geo_off + 4 * g];
     if (own != col_side(d, it.col0 + b)) return cmk(0.0, 0.0);

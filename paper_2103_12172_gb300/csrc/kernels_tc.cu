@@ -188,10 +188,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   if (warp == 8) {
     // ---------------------------------------------------------------- MMA warp
     if (lane == 0) {
-      unsigned g = 0, T = 0;
-      for (int v = blockIdx.x; v < bt.total_blocks && !abort_sh; v += gridDim.x, ++T) {
+      unsigned g = 0, T = 0;                  // stages and tiles processed (the barrier phases)
+      for (int v = blockIdx.x; v < bt.total_blocks && !abort_sh; v += gridDim.x) {
         Item it; int local;
         locate(bt, v, it, local);
+        if (MDP_CHECKED && !item_in_bounds(bt, subs, it, local, F_TCOLS, false)) continue;   // every warp skips it
         const int nchunk = (subs[it.sub].Nq + TC_KC - 1) / TC_KC;
         if (T > 0 && !mbar_wait(smem_u32(&tempty_bar), (T - 1) & 1u, &abort_sh)) break;
         tc_fence_after();
@@ -216,6 +217,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         }
         if (!ok) break;
         tc_commit(smem_u32(&tfull_bar));
+        ++T;
       }
     }
     __syncwarp();
@@ -223,10 +225,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     // ---------------------------------------------------------------- producer warps
     const int quarter = warp & 3, half = warp >> 2;
     const int r = 32 * quarter + lane;        // matrix row of A (TMEM lane) of this thread
-    unsigned g = 0, T = 0;
-    for (int v = blockIdx.x; v < bt.total_blocks && !abort_sh; v += gridDim.x, ++T) {
+    unsigned g = 0, T = 0;                    // stages and tiles processed (the barrier phases)
+    for (int v = blockIdx.x; v < bt.total_blocks && !abort_sh; v += gridDim.x) {
       Item it; int local;
       locate(bt, v, it, local);
+      if (MDP_CHECKED && !item_in_bounds(bt, subs, it, local, F_TCOLS, false)) continue;     // every warp skips it
       const SubDesc &d = subs[it.sub];
       const bool CD = d.cplx || CIN;
       const int nct = (it.ncols + 63) >> 6;
@@ -362,6 +365,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       }
       // half_sh is rewritten only in the next tile's epilogue, which no producer reaches before
       // every producer has filled that tile's stages (and so finished reading here)
+      ++T;
     }
   }
   if (abort_sh && tid == 0) atomicCAS(status, 0, (int)MDP_ERR_TIMEOUT);   // the first error sticks

@@ -9,6 +9,13 @@
 #include <cuda_runtime.h>
 #include "mdp.h"
 
+// The bounds-checked build (libmdp_checked.so) is compiled with MDP_CHECKED=1: every batched
+// kernel validates its block's work item and the gamma indices it writes through (first violation
+// in the status word as MDP_ERR_BOUNDS, the access skipped), and MDP_FAULT_INJECT is honoured.
+#ifndef MDP_CHECKED
+#define MDP_CHECKED 0
+#endif
+
 namespace mdp {
 
 // Per-subdomain geometry, coefficients and table offsets (POD; copied to the device).
@@ -54,6 +61,7 @@ struct SubDesc {
                         // of the sines, in the shared-memory operand layout of k_inv_cols_tc
   long long out_off;    // complex elements: start of the subdomain's output block
   long long rec_off;    // complex elements: start of the receiver block [n_cols][Px - 2]
+  int *dstatus;         // the plan's device status word (bounds-checked build: first error; else unused)
 };
 
 // One batch work item: columns [col0, col0 + ncols) of subdomain `sub`, with its
@@ -83,6 +91,13 @@ struct Batch {
   int n_items;
   int total_blocks;
   Item one;
+  // ranges the bounds-checked build validates every block's item against: subdomains, workspace
+  // doubles, table doubles, pivot-flag bytes, and complex elements of the output / density /
+  // cotangent arrays of the call; the status word that records the first violation
+  int n_subs;
+  int grad;             // the items are laid out for the gradient pass
+  long long ws_n, tab_n, piv_n, out_n;
+  int *status;
 };
 
 constexpr int FSW = 24;  // doubles per forward-sweep table row
@@ -203,6 +218,18 @@ namespace mdp {
 
 enum Sched { S_PROJ = 0, S_GRAD = 1, S_BASIS = 2 };
 
+// the ranges a launch's Batch carries for the bounds-checked build (out_n: complex elements of the
+// call's output, density and cotangent arrays)
+inline void set_bounds(const mdp_plan *p, Batch &b, long long out_n, bool grad) {
+  b.n_subs = p->n_subs;
+  b.grad = grad ? 1 : 0;
+  b.ws_n = p->ws_doubles;
+  b.tab_n = (long long)p->host_tables.size();
+  b.piv_n = (long long)p->host_piv.size();
+  b.out_n = out_n;
+  b.status = p->d_status;
+}
+
 // kernel families (each has its own block decomposition of an item); F_A* are the adjoint's
 enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_ARINGC, F_AGAM, F_IREC,
            F_ACOLS, F_TCOLS, NFAM };
@@ -246,6 +273,26 @@ inline __host__ __device__ void red_slots(const SubDesc &d, int ncols, int base[
   base[3] = base[2] + blocks_for(F_ARINGC, d, ncols);
   base[4] = base[3] + blocks_for(F_AGAM, d, ncols);
 }
+// Workspace slices of an item of ncols columns, in doubles from the item's base (each 256-byte
+// aligned): basis densities, ring residual, dense-row transforms, mode-space field, and for the
+// gradient pass the adjoint field, k-source and per-block partials; in the projection the last
+// slice holds per column the largest biased exponent of the kept mode-space rows (ints).
+inline __host__ __device__ void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long long &r,
+                                               long long &gr, long long &y, long long &a, long long &s,
+                                               long long &red, long long &total) {
+  auto al = [](long long v) { return (v + 31) & ~31LL; };
+  long long off = 0;
+  xi = off; off += al((long long)d.G * ncols * (grad ? 2 : 1));
+  r = off;  off += al((long long)(d.R > d.R2 ? d.R : d.R2) * ncols * 2);
+  gr = off; off += al(5LL * d.Nq * ncols * 2);  // 4 dense rows (+ the receiver row in the adjoint)
+  y = off;  off += al((long long)d.Nq * (grad ? d.Nt : d.NYf) * ncols * 2);
+  a = off;  off += grad ? al((long long)d.Nq * d.Nt * ncols * 2) : 0;
+  s = off;  off += grad ? al((long long)d.R * ncols * 2) : 0;
+  int rs[5];
+  red_slots(d, ncols, rs);
+  red = off; off += grad ? al(rs[4] + 1) : al((ncols + 1) / 2);
+  total = off;
+}
 const char *fam_name(int f);
 // event pair around a launch when profiling is on
 void prof_begin(mdp_plan *p, int fam, cudaStream_t st);
@@ -258,8 +305,6 @@ cudaError_t launch_factor(const mdp_plan *p, int *status, cudaStream_t st);   //
 // the same into an explicit table set (descriptors ds, tables tab, pivot flags piv)
 cudaError_t launch_factor_to(const mdp_plan *p, const SubDesc *ds, double *tab, uint8_t *piv, int *status,
                              cudaStream_t st);
-void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long long &r, long long &gr,
-                    long long &y, long long &a, long long &s, long long &red, long long &total);
 void host_mode_solve(const HostSub &hs, int q, int adjoint, const double *b, double *x);
 // kernel launchers (kernels.cu)
 enum { PASS_FWD = 0, PASS_GRAD = 1 };

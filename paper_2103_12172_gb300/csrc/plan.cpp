@@ -27,24 +27,6 @@ const char *fam_name(int f) {
   return (f >= 0 && f < NFAM) ? names[f] : "?";
 }
 
-void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long long &r, long long &gr,
-                    long long &y, long long &a, long long &s, long long &red, long long &total) {
-  auto al = [](long long v) { return (v + 31) & ~31LL; };  // 256-byte alignment (in doubles)
-  long long off = 0;
-  xi = off; off += al((long long)d.G * ncols * (grad ? 2 : 1));
-  r = off;  off += al((long long)std::max(d.R, d.R2) * ncols * 2);
-  gr = off; off += al(5LL * d.Nq * ncols * 2);  // 4 dense rows (+ the receiver row in the adjoint)
-  y = off;  off += al((long long)d.Nq * (grad ? d.Nt : d.NYf) * ncols * 2);
-  a = off;  off += grad ? al((long long)d.Nq * d.Nt * ncols * 2) : 0;
-  s = off;  off += grad ? al((long long)d.R * ncols * 2) : 0;
-  int rs[5];
-  red_slots(d, ncols, rs);
-  // gradient pass: per-block partial sums of the k-gradient; projection: per column the largest
-  // biased exponent of the stored mode-space rows (ints, for the tensor-core gamma columns)
-  red = off; off += grad ? al(rs[4] + 1) : al((ncols + 1) / 2);
-  total = off;
-}
-
 // ---------------------------------------------------------------- geometry
 static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   SubDesc &d = hs.d;
