@@ -422,13 +422,15 @@ def measure(mdp, wl, steps, warmup, world=1, barrier=None, clocks=None, full=Tru
     per-RHS comparator and (full) the graph-replayed and deduplicated variants."""
     import torch
 
-    from paper_2103_12172_gb300.autotune import tune_tile
+    from paper_2103_12172_gb300.autotune import plan_kwargs, tune_plan
 
     dev = torch.device("cuda", torch.cuda.current_device())
     subs = list(wl.subdomains)
     n_cols = wl.n_columns
-    tile = tune_tile(subs)                     # untimed: columns per work item for this GPU and shape
-    plan = mdp.Plan(subs, tile_cols=tile)
+    tuned = tune_plan(subs)                    # untimed: tile and kernel variants for this GPU and shape
+    kw = plan_kwargs(tuned)
+    tile = kw["tile_cols"]
+    plan = mdp.Plan(subs, **kw)
     out = torch.empty(plan.output_size, dtype=torch.complex128, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -494,7 +496,7 @@ def measure(mdp, wl, steps, warmup, world=1, barrier=None, clocks=None, full=Tru
         roof["dram_peak_gbs"] = hbm
         roof["dram_peak_note"] = f"{hbm_src} HBM copy bandwidth; DRAM fraction is context, the path is FP64-bound"
     res = {"value": value, "unit": UNIT, "ms_per_step": total_ms / steps, "columns_per_step": n_cols,
-           "tile_cols": tile, "roofline": roof,
+           "tile_cols": tile, "tuned": kw, "roofline": roof,
            "kernels_ms_per_step": {k: v[0] / steps for k, v in sorted(prof.items())},
            "gpu_launches": sum(n for (_, n) in prof.values()),
            "wall_s_timed": wall, "host_issue_ms_per_step": issue_ms}
@@ -576,7 +578,7 @@ def measure(mdp, wl, steps, warmup, world=1, barrier=None, clocks=None, full=Tru
     if full:
         # the same step replayed as one CUDA graph (library graph mode): the difference is what
         # the per-kernel, per-wave launches cost
-        gplan = mdp.Plan(subs, tile_cols=tile, graph=True)
+        gplan = mdp.Plan(subs, graph=True, **kw)
         gs = torch.cuda.Stream()
         with torch.cuda.stream(gs):
             graph_ms = event_time(lambda: gplan.project(out=out), max(3, min(steps, 10)), gs)
@@ -585,7 +587,7 @@ def measure(mdp, wl, steps, warmup, world=1, barrier=None, clocks=None, full=Tru
                         "launch_overhead_frac": max(0.0, 1.0 - graph_ms / res["ms_per_step"])}
         # identical subdomains solved once (MDP_PLAN_DEDUPE), reported separately: the same columns
         # of every subdomain, the distinct problems solved and their blocks copied
-        dplan = mdp.Plan(subs, tile_cols=tile, dedupe=True)
+        dplan = mdp.Plan(subs, dedupe=True, **kw)
         n_distinct = len(set(dplan.leaders()))
         if n_distinct < len(subs):
             dedupe_ms = event_time(lambda: dplan.project(out=out), max(3, min(steps, 10)), stream)
@@ -627,7 +629,7 @@ def run_ours(args, wl):
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "description": wl.description, "columns_per_step": head["columns_per_step"],
-                   "tile_cols": head["tile_cols"],
+                   "tile_cols": head["tile_cols"], "tuned": head["tuned"],
                    "l2": "flushed between timed steps (512 MiB write, untimed); every wave's workspace also "
                          "exceeds L2", "parallelism": f"replicas{world}"},
         "roofline": dict(head["roofline"], fp64_probe_tflops=fp64_probe / 1e3,
@@ -657,7 +659,7 @@ def run_ours(args, wl):
             r = measure(mdp, sub_wl, max(5, min(args.steps, 10)), 3, full=False)
             cfgs[name] = {"workload": sub_wl.name, "value": r["value"], "unit": UNIT,
                           "ms_per_step": r["ms_per_step"], "columns_per_step": r["columns_per_step"],
-                          "tile_cols": r["tile_cols"], "roofline_kernel": r["roofline"]["kernel"],
+                          "tile_cols": r["tile_cols"], "tuned": r["tuned"], "roofline_kernel": r["roofline"]["kernel"],
                           "roofline_frac": r["roofline"]["frac"],
                           "step_flop_frac": r["roofline"]["step_flop_frac"],
                           "dram_frac": r["roofline"].get("dram_frac"),

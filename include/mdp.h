@@ -69,12 +69,20 @@ enum { MDP_OUT_Q = 0, MDP_OUT_P = 1 };
  * subdomains (Section 4). User densities, receivers and the adjoint still run per subdomain
  * (on the shared tables). mdp_plan_update_k then requires equal k within each group. */
 #define MDP_PLAN_DEDUPE 0x4u
+/* Kernel variants (the same results to rounding; the autotuner times them): the gamma columns of
+ * the middle rows by FP64 sums instead of the tensor-core contraction, and the sine transforms of
+ * the dense ring and gamma rows by direct sums instead of the FFT. */
+#define MDP_PLAN_FP64_COLS 0x8u
+#define MDP_PLAN_DIRECT_ROWS 0x10u
 
 /* Plan options (0 selects the default: environment MDP_TILE_COLS / MDP_WS_MB, else 256 columns
- * per work item and a 4 GiB workspace budget). */
+ * per work item and a 4 GiB workspace budget; 1024 points per FFT block; 2 staged rows). */
 typedef struct {
   int tile_cols;              /* columns per work item (the batching tile) */
   long long workspace_bytes;  /* budget that packs work items into waves */
+  int fft_block_points;       /* complex values per block of the dense-row FFT kernels: 1024, 2048 or
+                                 4096 (a block takes max(1, points / (2 Nx)) columns) */
+  int tri_stages;             /* table rows the per-mode sweep stages ahead in shared memory: 2 or 4 */
 } mdp_plan_options;
 
 /* One subdomain Omega_i = (x0, x1) x (y0, y1) and its auxiliary problem

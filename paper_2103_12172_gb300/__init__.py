@@ -49,14 +49,21 @@ class Plan:
     """A plan over a list of subdomains (objects with the mdp_subdomain fields)."""
 
     def __init__(self, subdomains, host_only: bool = False, graph: bool = False, tile_cols: int = 0,
-                 workspace_bytes: int = 0, dedupe: bool = False):
+                 workspace_bytes: int = 0, dedupe: bool = False, fp64_cols: bool = False,
+                 direct_rows: bool = False, fft_block_points: int = 0, tri_stages: int = 0):
+        """Kernel variants (same results to rounding; see autotune.tune_plan): fp64_cols sums the
+        gamma columns of the middle rows on the FP64 pipe instead of the tensor cores, direct_rows
+        takes the dense-row sine transforms by direct sums instead of the FFT, fft_block_points
+        sets the complex values per FFT block (1024, 2048 or 4096), tri_stages the rows the per-mode
+        sweep stages ahead (2 or 4); 0 selects the defaults."""
         self.L = _lib.lib()
         self.subdomains = list(subdomains)
         self._c_subs = as_c_subdomains(self.subdomains)
         handle = C.c_void_p()
         flags = ((MDP_PLAN_HOST_ONLY if host_only else 0) | (MDP_PLAN_GRAPH if graph else 0)
-                 | (MDP_PLAN_DEDUPE if dedupe else 0))
-        opts = _lib.mdp_plan_options(int(tile_cols), int(workspace_bytes))
+                 | (MDP_PLAN_DEDUPE if dedupe else 0) | (_lib.MDP_PLAN_FP64_COLS if fp64_cols else 0)
+                 | (_lib.MDP_PLAN_DIRECT_ROWS if direct_rows else 0))
+        opts = _lib.mdp_plan_options(int(tile_cols), int(workspace_bytes), int(fft_block_points), int(tri_stages))
         _lib.check(self.L.mdp_ap_plan_ex(self._c_subs, len(self.subdomains), flags, C.byref(opts), C.byref(handle)),
                    "mdp_ap_plan")
         self.handle = handle

@@ -14,6 +14,8 @@ MDP_OUT_Q, MDP_OUT_P = 0, 1
 MDP_PLAN_HOST_ONLY = 0x1
 MDP_PLAN_GRAPH = 0x2
 MDP_PLAN_DEDUPE = 0x4
+MDP_PLAN_FP64_COLS = 0x8
+MDP_PLAN_DIRECT_ROWS = 0x10
 
 EXPORTED = [
     "mdp_ap_plan", "mdp_plan_update_k", "mdp_plan_layout", "mdp_plan_output_size", "mdp_project_batch",
@@ -29,7 +31,8 @@ class mdp_subdomain(C.Structure):
 
 
 class mdp_plan_options(C.Structure):
-    _fields_ = [("tile_cols", C.c_int), ("workspace_bytes", C.c_longlong)]
+    _fields_ = [("tile_cols", C.c_int), ("workspace_bytes", C.c_longlong), ("fft_block_points", C.c_int),
+                ("tri_stages", C.c_int)]
 
 
 class MdpError(RuntimeError):

@@ -254,8 +254,14 @@ mdp_status mdp_ap_plan(const mdp_subdomain *subs, int n_subs, unsigned flags, md
 mdp_status mdp_ap_plan_ex(const mdp_subdomain *subs, int n_subs, unsigned flags, const mdp_plan_options *opt,
                           mdp_plan **out) {
   if (!subs || n_subs < 1 || !out) return MDP_ERR_ARG;
-  if (flags & ~(MDP_PLAN_HOST_ONLY | MDP_PLAN_GRAPH | MDP_PLAN_DEDUPE)) return MDP_ERR_ARG;
+  if (flags & ~(MDP_PLAN_HOST_ONLY | MDP_PLAN_GRAPH | MDP_PLAN_DEDUPE | MDP_PLAN_FP64_COLS | MDP_PLAN_DIRECT_ROWS))
+    return MDP_ERR_ARG;
   if (opt && (opt->tile_cols < 0 || opt->workspace_bytes < 0)) return MDP_ERR_ARG;
+  if (opt && opt->fft_block_points != 0 &&
+      (opt->fft_block_points < FFT_BLOCK_POINTS || opt->fft_block_points > FFT_POINTS ||
+       (opt->fft_block_points & (opt->fft_block_points - 1))))
+    return MDP_ERR_ARG;
+  if (opt && opt->tri_stages != 0 && opt->tri_stages != 2 && opt->tri_stages != 4) return MDP_ERR_ARG;
   *out = nullptr;
   mdp_plan *p = new (std::nothrow) mdp_plan();
   if (!p) return MDP_ERR_NOMEM;
@@ -265,6 +271,8 @@ mdp_status mdp_ap_plan_ex(const mdp_subdomain *subs, int n_subs, unsigned flags,
   p->ws_budget = env_ll("MDP_WS_MB", 4096) << 20;
   if (opt && opt->tile_cols > 0) p->tile_cols = opt->tile_cols;
   if (opt && opt->workspace_bytes > 0) p->ws_budget = opt->workspace_bytes;
+  if (opt && opt->fft_block_points > 0) p->fft_block_points = opt->fft_block_points;
+  if (opt && opt->tri_stages > 0) p->tri_stages = opt->tri_stages;
   mdp_status st;
   try {
     st = build_host_plan(p, subs, n_subs);

@@ -501,14 +501,13 @@ __device__ __forceinline__ void tri_full_body(const Item &it, const SubDesc &d, 
   if (CF) for (; i >= 0; --i) back_complex(i);
 }
 
-// Staging of the projection sweep: each warp owns TRI_STAGES stages of shared memory and copies
-// the operands of row i + TRI_STAGES while row i is swept. Forward stage: the table row (FSW
-// doubles) and up to 4 ring values per lane ([slot][lane]); backward stage: table doubles 18..23
-// (u1, u2, swap flag) and the lane's stored y~.
-constexpr int TRI_STAGES = 2;
+// Staging of the projection sweep: each warp owns TRI_STAGES stages of shared memory (2 or 4: a
+// plan option the autotuner sets) and copies the operands of row i + TRI_STAGES while row i is
+// swept. Forward stage: the table row (FSW doubles) and up to 4 ring values per lane
+// ([slot][lane]); backward stage: table doubles 18..23 (u1, u2, swap flag) and the lane's y~.
 template <bool CIN>
 __host__ __device__ constexpr int tri_stage_bytes() { return FSW * 8 + 4 * 32 * (CIN ? 16 : 8); }
-template <bool CIN>
+template <bool CIN, int TRI_STAGES>
 __host__ __device__ constexpr int tri_smem_bytes() { return TRI_WARPS * TRI_STAGES * tri_stage_bytes<CIN>(); }
 
 // The projection's sweep over the condensed, pivot-scaled table (plan: build_fs): rows
@@ -517,7 +516,7 @@ __host__ __device__ constexpr int tri_smem_bytes() { return TRI_WARPS * TRI_STAG
 // sweep (real densities and the run starts at i0) the forward recurrence is real.
 // CD: complex mode-space data (complex AP or complex densities). sw: the warp's stages; the
 // active lanes are 0 .. nact-1 (mask).
-template <bool CD, bool CIN>
+template <bool CD, bool CIN, int TRI_STAGES>
 __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, const double *tab, double *ws, int b,
                                             int q, char *sw, int lane, int nact, unsigned mask) {
   constexpr int VS = CIN ? 16 : 8, SB = tri_stage_bytes<CIN>(), RING = FSW * 8;
@@ -754,7 +753,7 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
   if (d.tc_cols) atomicMax(reinterpret_cast<int *>(ws + it.red_off) + b, emax);
 }
 
-template <bool CIN, bool FULL>
+template <bool CIN, bool FULL, int TRI_STAGES>
 __global__ void __launch_bounds__(32 * TRI_WARPS, 32 / TRI_WARPS) k_tri(Batch bt, const SubDesc *subs, const double *tab, const uint8_t *pivtab,
                                              double *ws) {
   Item it; int local;
@@ -775,8 +774,8 @@ __global__ void __launch_bounds__(32 * TRI_WARPS, 32 / TRI_WARPS) k_tri(Batch bt
     else tri_full_body<false, CIN>(it, d, tab, pivtab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
   } else {
     char *sw = tri_sm + threadIdx.y * TRI_STAGES * tri_stage_bytes<CIN>();
-    if (d.cplx || CIN) tri_fs_body<true, CIN>(it, d, tab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
-    else tri_fs_body<false, CIN>(it, d, tab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
+    if (d.cplx || CIN) tri_fs_body<true, CIN, TRI_STAGES>(it, d, tab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
+    else tri_fs_body<false, CIN, TRI_STAGES>(it, d, tab, ws, b, q, sw, threadIdx.x, __popc(mask), mask);
   }
 }
 
@@ -1391,9 +1390,13 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess) e = set_tc_kernel_attributes();
   // the sweep's staging buffers take 32 x 2.4 KiB per SM at full occupancy: prefer shared memory
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_tri<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    e = cudaFuncSetAttribute(k_tri<false, false, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_tri<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    e = cudaFuncSetAttribute(k_tri<true, false, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tri<false, false, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tri<true, false, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   return e;
 }
 
@@ -1417,8 +1420,13 @@ cudaError_t launch_project(mdp_plan *p, const Batch *fb, int out_kind, const dou
   else MDP_LAUNCH(F_RES, k_residual<true, false><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
   if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
   else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
-  if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false><<<grid1(fb[F_TRI].total_blocks), btri, tri_smem_bytes<false>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
-  else MDP_LAUNCH(F_TRI, k_tri<true, false><<<grid1(fb[F_TRI].total_blocks), btri, tri_smem_bytes<true>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  if (p->tri_stages == 4) {
+    if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false, 4><<<grid1(fb[F_TRI].total_blocks), btri, tri_smem_bytes<false, 4>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+    else MDP_LAUNCH(F_TRI, k_tri<true, false, 4><<<grid1(fb[F_TRI].total_blocks), btri, tri_smem_bytes<true, 4>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  } else {
+    if (basis) MDP_LAUNCH(F_TRI, k_tri<false, false, 2><<<grid1(fb[F_TRI].total_blocks), btri, tri_smem_bytes<false, 2>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+    else MDP_LAUNCH(F_TRI, k_tri<true, false, 2><<<grid1(fb[F_TRI].total_blocks), btri, tri_smem_bytes<true, 2>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+  }
   if (basis) {
     MDP_LAUNCH(F_IROWS, k_inv_rows<false><<<grid1(fb[F_IROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_IROWS], ds, tab, ws, xi_user, out, out_kind));
     MDP_LAUNCH(F_ICOLS, k_inv_cols<false><<<grid1(fb[F_ICOLS].total_blocks), b8, 0, st>>>(fb[F_ICOLS], ds, tab, ws, xi_user, out, out_kind));
@@ -1446,8 +1454,8 @@ cudaError_t launch_adjoint(mdp_plan *p, const Batch *fb, int out_kind, const dou
     else MDP_LAUNCH(F_RES, k_residual<true, true><<<grid1(fb[F_RES].total_blocks), b8, 0, st>>>(fb[F_RES], ds, tab, ws, xi_user));
     if (basis) MDP_LAUNCH(F_FROWS, k_fwd_rows<false><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
     else MDP_LAUNCH(F_FROWS, k_fwd_rows<true><<<grid1(fb[F_FROWS].total_blocks), b8, p->fft_smem, st>>>(fb[F_FROWS], ds, tab, ws));
-    if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true><<<grid1(fb[F_TRI].total_blocks), btri, TRI_WARPS * 2 * full_stage_bytes<false>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
-    else MDP_LAUNCH(F_TRI, k_tri<true, true><<<grid1(fb[F_TRI].total_blocks), btri, TRI_WARPS * 2 * full_stage_bytes<true>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+    if (basis) MDP_LAUNCH(F_TRI, k_tri<false, true, 2><<<grid1(fb[F_TRI].total_blocks), btri, TRI_WARPS * 2 * full_stage_bytes<false>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
+    else MDP_LAUNCH(F_TRI, k_tri<true, true, 2><<<grid1(fb[F_TRI].total_blocks), btri, TRI_WARPS * 2 * full_stage_bytes<true>(), st>>>(fb[F_TRI], ds, tab, p->d_piv, ws));
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -249,9 +249,10 @@ __device__ __forceinline__ void dst1_twist(cplx xa, cplx xb, double s, cplx &ya,
 }
 
 // From C (nseq transforms of length N, stride N) to F[f N + q] = F_q (q = 1 .. N-1; F[f N] is
-// not written). nseq N / 2 must be a multiple of the block size (256 threads: the FFT kernels
-// use nseq = 1024 / (2N), or 1 when N >= 512). tot: shared scratch of nseq N / 64 values.
-// Called by every thread of the block.
+// not written). nseq N / 2 must be a multiple of the block size (256 threads): the FFT kernels
+// use nseq = P / (2N), or 1 when 2N >= P, with P = 1024, 2048 or 4096 points per block (the plan
+// accepts no other), so nseq N / 2 is P / 4 or N / 2 >= 256, a power of two. tot: shared scratch
+// of nseq N / 64 <= 32 values. Called by every thread of the block.
 __device__ __forceinline__ void dst1_post(const double2 *C, double2 *F, int nseq, int N, double2 *tot) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
   const int H = N >> 1, E = nseq * H, lane = tid & 31;

@@ -168,6 +168,8 @@ struct mdp_plan {
   long long out_size = 0;
   long long rec_size = 0;
   int tile_cols = 256;                   // columns per work item
+  int fft_block_points = mdp::FFT_BLOCK_POINTS;  // complex values per block of the dense-row FFT kernels
+  int tri_stages = 2;                    // table rows the projection sweep stages ahead (2 or 4)
   long long ws_budget = 0;               // bytes of workspace
   // batch schedules: [S_PROJ] mdp_project_batch over every subdomain, [S_GRAD] mdp_ap_adjoint
   // (larger workspace), [S_BASIS] basis columns of the distinct subdomains only (MDP_PLAN_DEDUPE

@@ -28,7 +28,7 @@ const char *fam_name(int f) {
 }
 
 // ---------------------------------------------------------------- geometry
-static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
+static mdp_status geometry(const mdp_subdomain &in, HostSub &hs, unsigned flags, int fft_block_points) {
   SubDesc &d = hs.d;
   std::memset(&d, 0, sizeof d);
   if (in.nx < 9 || in.ny < 9 || !(in.h > 0) || !(in.k > 0) || in.n_modes < 1 ||
@@ -63,13 +63,14 @@ static mdp_status geometry(const mdp_subdomain &in, HostSub &hs) {
   d.Ph = d.xsym ? d.Nx / 2 - mlo + 1 : 0;
   d.R2 = d.xsym ? 8 * d.Ph + 4 * (d.Py - 4) : d.R;  // (sum, difference) per pair unit
   d.nrec = -1;
-  d.rows_fft = (d.Nx & (d.Nx - 1)) == 0 && 2 * d.Nx <= FFT_POINTS && d.Nx >= 8;
-  d.fpb = d.rows_fft ? std::max(1, FFT_BLOCK_POINTS / (2 * d.Nx)) : 0;
+  d.rows_fft = !(flags & MDP_PLAN_DIRECT_ROWS) && (d.Nx & (d.Nx - 1)) == 0 && 2 * d.Nx <= FFT_POINTS && d.Nx >= 8;
+  d.fpb = d.rows_fft ? std::max(1, fft_block_points / (2 * d.Nx)) : 0;
   // gamma columns on the tensor cores: exact integer accumulation needs at most 1024 modes per
-  // output (a parity half of Nq on centred subdomains); MDP_TC_COLS=0 keeps the FP64 sums
+  // output (a parity half of Nq on centred subdomains); MDP_PLAN_FP64_COLS (or the environment
+  // MDP_TC_COLS=0) keeps the FP64 sums
   {
     const char *tc = std::getenv("MDP_TC_COLS");
-    const bool on = !(tc && tc[0] == '0' && tc[1] == 0);
+    const bool on = !(flags & MDP_PLAN_FP64_COLS) && !(tc && tc[0] == '0' && tc[1] == 0);
     d.tc_cols = on && (d.xsym ? d.Nq <= 2047 : d.Nq <= 1023);
   }
   d.nfirst = d.cplx ? 0 : 1;
@@ -561,7 +562,7 @@ static void find_leaders(mdp_plan *p) {
 mdp_status build_host_plan(mdp_plan *p, const mdp_subdomain *subs, int n) {
   p->subs.resize(n);
   for (int i = 0; i < n; ++i) {
-    mdp_status st = geometry(subs[i], p->subs[i]);
+    mdp_status st = geometry(subs[i], p->subs[i], p->flags, p->fft_block_points);
     if (st != MDP_OK) return st;
   }
   find_leaders(p);

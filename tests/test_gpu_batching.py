@@ -168,3 +168,24 @@ def test_structured_qr_equals_the_dense_least_squares(mdp):
     assert np.abs(x - xr).max() <= 1e-10 * np.abs(xr).max()
     R2, _ = householder_qr(At, bt)
     assert np.allclose(np.abs(np.diag(R)), np.abs(np.diag(R2.cpu().numpy())), rtol=1e-10)
+
+
+def test_plan_variants_agree_and_the_tuner_picks_one(mdp, tmp_path):
+    """Every kernel variant the autotuner searches (FP64 or tensor-core gamma columns, FFT or
+    direct dense rows, FFT block sizes, 2 or 4 staged sweep rows) gives the same columns to
+    rounding (1e-12 per column; the oracle pins the default), and tune_plan returns one of them
+    and caches it."""
+    from paper_2103_12172_gb300.autotune import plan_kwargs, tune_plan
+    subs = [W.unit_subdomain(0, 0, 129, 12.0, W.AP_DIRX_SOMMY, 3), W.unit_subdomain(1, 0, 65, 9.0, W.AP_DIRICHLET4, 3)]
+    ref = mdp.Plan(subs).project().cpu().numpy()
+    variants = [dict(fp64_cols=True), dict(direct_rows=True), dict(fft_block_points=2048),
+                dict(fft_block_points=4096), dict(tri_stages=4), dict(tile_cols=8, tri_stages=4, fp64_cols=True)]
+    for v in variants:
+        got = mdp.Plan(subs, **v).project().cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), v
+    path = str(tmp_path / "tune.json")
+    t = tune_plan(subs, tiles=(16, 64), cache_path=path)
+    assert t["tile_cols"] in (16, 24) and t["tri_stages"] in (2, 4) and t["fft_block_points"] in (1024, 2048, 4096)
+    assert plan_kwargs(tune_plan(subs, tiles=(16, 64), cache_path=path)) == plan_kwargs(t)
+    got = mdp.Plan(subs, **plan_kwargs(t)).project().cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()

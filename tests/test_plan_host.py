@@ -227,3 +227,26 @@ def test_source_foot_data_matches_the_oracle(mdp):
     fgrid, src4 = plan.source_foot_data(0, fun)
     assert np.allclose(fgrid, source_on_grid(sub, fun), rtol=0, atol=1e-15)
     assert np.allclose(src4, source_foot_data(grid_sets(sub), sub, fun), rtol=0, atol=1e-14)
+
+
+def test_plan_options_are_validated_and_fft_blocks_fit_the_dst_epilogue(mdp):
+    """FFT blocks of 1024, 2048 or 4096 points and 2 or 4 staged sweep rows are accepted, other
+    values rejected (MDP_ERR_ARG). For every accepted block size and power-of-two row length
+    the DST epilogue's requirements hold: the pair count per block, nseq N / 2 (nseq = P / (2 N)
+    transforms, or 1), is a multiple of the 256-thread block and at most 32 x 32 (its scan
+    scratch)."""
+    from paper_2103_12172_gb300 import MdpError
+    sub = W.small_subdomain(65, 7.0, W.AP_DIRX_SOMMY, 2)
+    for ok in (dict(fft_block_points=1024), dict(fft_block_points=4096), dict(tri_stages=4), dict(tri_stages=2)):
+        mdp.Plan([sub], host_only=True, **ok).close()
+    for bad in (dict(fft_block_points=512), dict(fft_block_points=3000), dict(fft_block_points=8192),
+                dict(tri_stages=3)):
+        with pytest.raises(MdpError) as e:
+            mdp.Plan([sub], host_only=True, **bad)
+        assert e.value.code == 1, bad
+    for P in (1024, 2048, 4096):
+        for lg in range(3, 12):
+            N = 1 << lg
+            nseq = max(1, P // (2 * N))
+            pairs = nseq * N // 2
+            assert pairs % 256 == 0 and pairs // 32 <= 32, (P, N)
