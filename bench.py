@@ -284,7 +284,7 @@ def kernel_flops(plan, items):
 def kernel_source_sha():
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels_common.cuh", "mdp_internal.h"):
+    for f in ("kernels.cu", "kernels_tc.cu", "kernels_common.cuh", "mdp_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2103_12172_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
