@@ -218,18 +218,48 @@ mdp_status mdp_source_terms(mdp_plan *p, int sub, const mdp_c64 *f, const mdp_c6
 
 /* Householder QR of a dense complex matrix (the least-squares step of the coupled subdomain
  * system, Section 3.5 steps 2(b)-(c)). A: device, column-major, m rows, n + nrhs columns,
- * leading dimension lda >= m; n <= m. Factors the first n columns in place (R in the upper
- * triangle, the reflectors H_k = I - tau_k v_k v_k^H below the diagonal with v_k(k) = 1 implied)
- * and applies Q^H to the nrhs columns after them; tau: device [n]. The least-squares solution
- * of A(:, 0:n) x = b is then R^{-1} (Q^H b)(0:n). Enqueued on cuda_stream; no allocation. */
-mdp_status mdp_householder_qr(int m, int n, int nrhs, mdp_c64 *A, long long lda, mdp_c64 *tau, void *cuda_stream);
+ * leading dimension lda >= m; 1 <= n <= m. Factors the first n columns in place (R in the upper
+ * triangle with a real diagonal, the reflectors H_k = I - tau_k v_k v_k^H below the diagonal
+ * with v_k(k) = 1 implied) and applies Q^H to the nrhs columns after them; tau: device [n]. The
+ * least-squares solution of A(:, 0:n) x = b is then R^{-1} (Q^H b)(0:n) (mdp_triangular_solve).
+ * work: device, mdp_householder_qr_work_ints(1) caller-owned ints, zeroed by the call itself on
+ * cuda_stream (reflector counters, then a status word and an abort flag): after the stream has
+ * finished, work[batch] is MDP_OK, or MDP_ERR_TIMEOUT if a bounded wait of the kernel gave up
+ * (the output is then incomplete). One cooperative launch (all CTAs resident: the call fails
+ * with MDP_ERR_CUDA if the device cannot take it); no allocation. Calls that share `work` must
+ * not overlap in time. */
+long long mdp_householder_qr_work_ints(int batch);
+mdp_status mdp_householder_qr(int m, int n, int nrhs, mdp_c64 *A, long long lda, mdp_c64 *tau, int *work,
+                              void *cuda_stream);
 
 /* mdp_householder_qr of `batch` matrices of the same shape at A + b*stride (stride >=
- * lda * (n + nrhs)); tau: device [batch][n]. Used for the first stage of the structured least
- * squares: one QR per subdomain's rows (those touch only that subdomain's unknowns), then one of
- * the stacked triangular factors. */
+ * lda * (n + nrhs)); tau: device [batch][n]; work: mdp_householder_qr_work_ints(batch) ints,
+ * the status word at work[batch]. Used for the first stage of the structured least squares: one
+ * QR per subdomain's rows (those touch only that subdomain's unknowns), then one of the stacked
+ * triangular factors. All matrices are factored in the one launch. */
 mdp_status mdp_householder_qr_batched(int batch, int m, int n, int nrhs, mdp_c64 *A, long long lda,
-                                      long long stride, mdp_c64 *tau, void *cuda_stream);
+                                      long long stride, mdp_c64 *tau, int *work, void *cuda_stream);
+
+/* Triangular solve with the R of mdp_householder_qr (Section 3.5 step 2(c): c = R^{-1} Q^H F, and
+ * the R^{-H} of the least squares' derivative). R: device, column-major n x n with leading
+ * dimension ldr >= n; only the upper triangle (row <= column) is read, so the QR's output
+ * buffer is passed as it is. conj_trans = 0 solves R X = B, 1 solves R^H X = B. B: device,
+ * column-major n x nrhs (ldb >= n), overwritten by X. The diagonal must be nonzero (no check: a
+ * zero pivot gives inf/NaN). n * 16 bytes must fit in one CTA's shared memory (n <= 14848),
+ * else MDP_ERR_ARG. Enqueued on cuda_stream; no allocation. */
+mdp_status mdp_triangular_solve(int n, int nrhs, const mdp_c64 *R, long long ldr, int conj_trans, mdp_c64 *B,
+                                long long ldb, void *cuda_stream);
+
+/* C = op(A) op(B), or C += op(A) op(B) if accumulate != 0, for the small dense products of the
+ * coupled system's assembly (Sections 3.3-3.5: Q times a coefficient vector, the Chebyshev
+ * transform of boundary data, the receiver values). op(A) is m x k with element (i, l) at
+ * A[i*rsa + l*csa], conjugated if conja != 0; op(B) is k x n with (l, j) at B[l*rsb + j*csb],
+ * conjugated if conjb != 0; C(i, j) at C[i*rsc + j*csc] (C must not overlap A or B). Strides in
+ * elements, any sign or order (transposes are strides). Each element sums its k products in
+ * order: the result does not depend on the launch. m <= 1048560. Enqueued on cuda_stream. */
+mdp_status mdp_complex_matmul(int m, int n, int k, const mdp_c64 *A, long long rsa, long long csa, int conja,
+                              const mdp_c64 *B, long long rsb, long long csb, int conjb, mdp_c64 *C,
+                              long long rsc, long long csc, int accumulate, void *cuda_stream);
 
 /* The extended basis densities xi_c = Ex Psi_c on gamma (Sections 3.2.3-3.2.4: the Taylor
  * extension of the Chebyshev basis function of column c, zero on the nodes owned by other

@@ -66,8 +66,11 @@ def lib():
         "mdp_potential": (i, [vp, i, i, vp, vp, vp]),
         "mdp_basis_densities": (i, [vp, i, i, i, vp, vp]),
         "mdp_source_terms": (i, [vp, i, vp, vp, vp, vp, vp]),
-        "mdp_householder_qr": (i, [i, i, i, vp, ll, vp, vp]),
-        "mdp_householder_qr_batched": (i, [i, i, i, i, vp, ll, ll, vp, vp]),
+        "mdp_householder_qr_work_ints": (ll, [i]),
+        "mdp_householder_qr": (i, [i, i, i, vp, ll, vp, vp, vp]),
+        "mdp_householder_qr_batched": (i, [i, i, i, i, vp, ll, ll, vp, vp, vp]),
+        "mdp_triangular_solve": (i, [i, i, vp, ll, i, vp, ll, vp]),
+        "mdp_complex_matmul": (i, [i, i, i, vp, ll, ll, i, vp, ll, ll, i, vp, ll, ll, i, vp]),
         "mdp_probe_rcp": (i, [vp, vp, i, vp]),
         "mdp_plan_read_tables": (i, [vp, i, vp, vp]),
         "mdp_plan_table_offsets": (i, [vp, i, C.POINTER(ll)]),

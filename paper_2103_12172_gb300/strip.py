@@ -21,7 +21,7 @@ import math
 
 import torch
 
-from . import Plan
+from . import Plan, linalg
 
 
 class ProjectWithReceivers(torch.autograd.Function):
@@ -51,98 +51,59 @@ class ProjectWithReceivers(torch.autograd.Function):
         return gk.to(dtype=dtype, device=device), None
 
 
-def householder_qr(A, b):
-    """(R, (Q^H b)[:n]) of a tall complex CUDA matrix A [m, n] by mdp_householder_qr."""
-    import ctypes as C
-    from . import _lib
-    m, n = A.shape
-    M = torch.empty((n + 1, m), dtype=torch.complex128, device=A.device)   # column-major [A | b]
-    M[:n] = A.transpose(0, 1)
-    M[n] = b
-    tau = torch.empty(n, dtype=torch.complex128, device=A.device)
-    _lib.check(_lib.lib().mdp_householder_qr(m, n, 1, C.c_void_p(M.data_ptr()), m, C.c_void_p(tau.data_ptr()),
-                                             C.c_void_p(torch.cuda.current_stream().cuda_stream)),
-               "mdp_householder_qr")
-    return torch.triu(M[:n, :n].transpose(0, 1)), M[n, :n].clone()
-
-
-def structured_qr(A, b, rows, cols):
-    """(R, (Q^H b)[:n]) of the stacked system A [m, n] whose row block j (rows[j] rows) has
-    nonzeros only in the columns cols[j], in two stages: a batched QR of every block restricted
-    to its columns (mdp_householder_qr_batched; blocks zero-padded to a common shape), then the
-    QR of the stacked triangular factors placed in their global columns. A^H A and the
-    least-squares minimiser are those of the whole system; the work is a fraction of one QR of
-    A when the blocks are narrow."""
-    import ctypes as C
-    from . import _lib
-    n = A.shape[1]
-    batch = len(rows)
-    mmax = max(rows)
-    nmax = max(len(c) for c in cols)
-    if mmax < nmax or batch * nmax < n:
-        return householder_qr(A, b)
-    M = torch.zeros((batch, nmax + 1, mmax), dtype=torch.complex128, device=A.device)   # column-major blocks
-    r0 = 0
-    for j, (g, cj) in enumerate(zip(rows, cols)):
-        idx = torch.as_tensor(cj, device=A.device)
-        M[j, :len(cj), :g] = A[r0:r0 + g].index_select(1, idx).transpose(0, 1)
-        M[j, nmax, :g] = b[r0:r0 + g]
-        r0 += g
-    tau = torch.empty((batch, nmax), dtype=torch.complex128, device=A.device)
-    _lib.check(_lib.lib().mdp_householder_qr_batched(batch, mmax, nmax, 1, C.c_void_p(M.data_ptr()), mmax,
-                                                     (nmax + 1) * mmax, C.c_void_p(tau.data_ptr()),
-                                                     C.c_void_p(torch.cuda.current_stream().cuda_stream)),
-               "mdp_householder_qr_batched")
-    S = torch.zeros((batch * nmax, n), dtype=torch.complex128, device=A.device)
-    t = M[:, nmax, :nmax].reshape(-1).clone()
-    for j, cj in enumerate(cols):
-        Rj = torch.triu(M[j, :nmax, :nmax].transpose(0, 1))
-        S[j * nmax:(j + 1) * nmax].index_copy_(1, torch.as_tensor(cj, device=A.device), Rj[:, :len(cj)])
-    return householder_qr(S, t)
+def least_squares_grads(A, b, x, w, mm):
+    """Gradients of the least-squares minimiser x of ||A x - b|| for the incoming gradient g,
+    given w = (A^H A)^{-1} g: with r = b - A x, grad_b = A w and grad_A = r w^H - (A w) x^H.
+    mm: the matrix-vector product to use."""
+    Aw = mm(A, w)
+    r = b - mm(A, x)
+    grad_A = torch.outer(r, w.conj()) - torch.outer(Aw, x.conj())
+    return grad_A, Aw
 
 
 class LeastSquares(torch.autograd.Function):
-    """x = argmin ||A x - b|| for a full-column-rank A (m >= n) by Householder QR of the
-    column-equilibrated A D (Section 3.5, steps 2(b)-(c); the scaling leaves the minimiser
-    unchanged and improves the conditioning of R). The backward pass uses the closed form of the
-    minimiser's derivative instead of differentiating the factorisation: with r = b - A x and
-    w = (A^H A)^{-1} g = D R^{-1} R^{-H} D g for the incoming gradient g,
-        grad_b = A w,   grad_A = r w^H - (A w) x^H."""
+    """x = argmin ||A x - b|| for a full-column-rank CUDA matrix A (m >= n) by Householder QR of
+    the column-equilibrated A D (Section 3.5, steps 2(b)-(c); the scaling leaves the minimiser
+    unchanged and improves the conditioning of R), all on libmdp's kernels: the QR
+    (mdp_householder_qr, or the two-stage structured form when the row blocks are given), the
+    triangular solves (mdp_triangular_solve) and the products (mdp_complex_matmul). The backward
+    pass uses the closed form of the minimiser's derivative instead of differentiating the
+    factorisation: w = (A^H A)^{-1} g = D R^{-1} R^{-H} D g for the incoming gradient g, then
+    least_squares_grads."""
 
     @staticmethod
     def forward(ctx, A, b, blocks=None):
+        if not A.is_cuda:
+            raise TypeError("LeastSquares runs on libmdp's CUDA kernels: A must be a CUDA tensor")
+        linalg.check_pending()                         # status words of earlier solves that have completed
         D = 1.0 / torch.linalg.vector_norm(A, dim=0)
-        if A.is_cuda and blocks is not None:
-            R, qb = structured_qr(A * D, b, *blocks)  # per-subdomain QRs, then the stacked factors
-        elif A.is_cuda:
-            R, qb = householder_qr(A * D, b)          # libmdp's QR (mdp_householder_qr)
+        if blocks is not None:
+            fac = linalg.structured_qr(A * D, b, *blocks)   # per-subdomain QRs, then the shared unknowns
         else:
-            Qf, R = torch.linalg.qr(A * D)
-            qb = Qf.conj().transpose(0, 1) @ b
-        x = D * torch.linalg.solve_triangular(R, qb[:, None], upper=True)[:, 0]
-        ctx.save_for_backward(A, b, x, R, D)
+            fac = linalg.householder_qr(A * D, b)
+        linalg.defer_check(fac)                        # checked later, without stalling the stream
+        x = D * fac.lstsq()
+        ctx.fac = fac
+        ctx.save_for_backward(A, b, x, D)
         return x
 
     @staticmethod
     def backward(ctx, g):
-        A, b, x, R, D = ctx.saved_tensors
-        t = torch.linalg.solve_triangular(R.conj().transpose(0, 1), (D * g)[:, None], upper=False)
-        w = D * torch.linalg.solve_triangular(R, t, upper=True)[:, 0]
-        Aw = A @ w
-        r = b - A @ x
-        grad_A = torch.outer(r, w.conj()) - torch.outer(Aw, x.conj())
-        return grad_A, Aw, None
+        A, b, x, D = ctx.saved_tensors
+        w = D * ctx.fac.gram_solve((D * g).to(torch.complex128))
+        grad_A, grad_b = least_squares_grads(A, b, x, w, linalg.matmul)
+        return grad_A, grad_b, None
 
 
 def cheb_coeffs(fvals, n):
     """Chebyshev coefficients of the degree n-1 interpolant from values at the n first-kind
     Chebyshev points x_i = cos(pi (i + 1/2) / n) (i = 0..n-1): c_m = (2/n) sum_i f(x_i) T_m(x_i),
-    c_0 halved. fvals [..., n] complex."""
+    c_0 halved. fvals [n] complex (CUDA; the product runs on mdp_complex_matmul)."""
     i = torch.arange(n, dtype=torch.float64, device=fvals.device)
     m = torch.arange(n, dtype=torch.float64, device=fvals.device)
     T = torch.cos(m[:, None] * math.pi * (i[None, :] + 0.5) / n)   # T_m(x_i)
-    c = (2.0 / n) * (fvals @ T.T.to(fvals.dtype))
-    c[..., 0] = c[..., 0] / 2
+    c = (2.0 / n) * linalg.matmul(T, fvals)
+    c[0] = c[0] / 2
     return c
 
 
@@ -215,7 +176,7 @@ class LayeredStrip:
             row, m0, cnt, roff = self.rlayout[j]
             nc = self.layout[j][1]
             K = rec[roff:roff + nc * cnt].view(nc, cnt).transpose(0, 1)    # [cnt, 8M]
-            val = K @ cvecs[j]
+            val = linalg.matmul(K, cvecs[j])
             st = self.source_terms(j, self.plan_k(j))
             if st is not None:
                 val = val + st[1][row, m0:m0 + cnt]
@@ -236,19 +197,20 @@ class LayeredStrip:
             out = []
             for j in range(self.N):
                 dens = self.plan.basis_densities(j)                      # [8M, |gamma|]
-                xi = (cvecs[j].to(dens.dtype) @ dens)[None, :].contiguous()
+                xi = linalg.matmul(dens.transpose(0, 1), cvecs[j])[None, :].contiguous()
                 u = self.plan.potential(j, xi)[0]
                 st = self.source_terms(j, self.plan_k(j))
                 out.append(u if st is None else u + st[1])
             return out
 
-    def coefficients(self, k):
-        """The Chebyshev coefficients [c^(0) sides 1..4, c^(1) sides 1..4] of every layer's boundary
-        data from the coupled least-squares solve, and the receiver output of the projection."""
+    def _structure(self, device):
+        """What the coupled system's shape depends on, built once: the unknowns (one block of M
+        per outer side, two per interface), each subdomain's sides as ("outer", c) or
+        ("if", c, sign), the unknowns each subdomain's rows touch, the Chebyshev points of every
+        outer side, and the Chebyshev analysis matrix."""
+        if getattr(self, "_st", None) is not None and self._st["device"] == device:
+            return self._st
         M, N = self.M, self.N
-        out, rec = ProjectWithReceivers.apply(k, self.plan)
-        s = cheb_points(M, out.device)
-        # unknowns: one block per outer side, two per interface
         idx, n = {}, 0
         for j in range(N):
             for side in (1, 2, 3, 4):
@@ -259,54 +221,102 @@ class LayeredStrip:
                 if not self.outer(j, side):
                     idx[("if", j, side)] = n
                     n += 2 * M
-        A_rows, b_rows, coef, col_sets = [], [], [], []
+        s = cheb_points(M, device)
+        sides, col_sets, pts = [], [], {}
+        for j in range(N):
+            spec, used = [], []
+            for side in (1, 2, 3, 4):
+                if self.outer(j, side):
+                    c = idx[(j, side)]
+                    spec.append(("outer", c))
+                    used.extend(range(c, c + M))
+                    pts[(j, side)] = self._side_xy(j, side, s)
+                else:
+                    key, sgn = self.iface(j, side)
+                    c = idx[("if",) + key]
+                    spec.append(("if", c, sgn))
+                    used.extend(range(c, c + 2 * M))
+            sides.append(spec)
+            col_sets.append(sorted(set(used)))
+        i_ = torch.arange(M, dtype=torch.float64, device=device)
+        T = torch.cos(i_[:, None] * math.pi * (i_[None, :] + 0.5) / M)   # T_m(x_i)
+        w = torch.full((M,), 2.0 / M, dtype=torch.float64, device=device)
+        w[0] = 1.0 / M
+        self._st = {"device": device, "n": n, "sides": sides, "col_sets": col_sets, "pts": pts,
+                    "cheb": (T.transpose(0, 1).to(torch.complex128).contiguous(), w)}
+        return self._st
+
+    def coefficients(self, k):
+        """The Chebyshev coefficients [c^(0) sides 1..4, c^(1) sides 1..4] of every layer's boundary
+        data from the coupled least-squares solve, and the receiver output of the projection.
+        Outer side of unknown block u: alpha c0 + beta c1 = d (d the Chebyshev coefficients of
+        the data); with beta != 0 the unknown is c0 and the side's rows read Q0 - (alpha/beta) Q1
+        against u and -Q1 d / beta on the right; with beta = 0 the unknown is c1 (rows Q1) and
+        the right-hand side -Q0 d / alpha. Interfaces: c0 shared, c1 with opposite signs."""
+        M, N = self.M, self.N
+        out, rec = ProjectWithReceivers.apply(k, self.plan)
+        st = self._structure(out.device)
+        n = st["n"]
+        # boundary data of every outer side, analysed into Chebyshev coefficients in one product
+        bcs, phis = [], []
+        for j in range(N):
+            for side, spec in zip((1, 2, 3, 4), st["sides"][j]):
+                if spec[0] == "outer":
+                    x, y = st["pts"][(j, side)]
+                    alpha, beta, phi = self.bc(j, side, k[j], x, y)
+                    bcs.append((alpha, beta))
+                    phis.append(phi.to(torch.complex128))
+        Tt, w = st["cheb"]
+        d_all = linalg.matmul(torch.stack(phis), Tt) * w if phis else None   # [outer sides, M]
+        A_rows, b_rows, coef = [], [], []
+        q = 0
         for j in range(N):
             G, nc, off, _ = self.layout[j]
             Q = out[off:off + G * nc].view(nc, G).transpose(0, 1)          # [G, 8M]
             A = torch.zeros(G, n, dtype=torch.complex128, device=out.device)
-            b = torch.zeros(G, dtype=torch.complex128, device=out.device)
+            e = []                      # Q e is minus the right-hand side
             cj = []
-            used = []                 # the unknowns this subdomain's rows touch
-            for side in (1, 2, 3, 4):
+            for side, spec in zip((1, 2, 3, 4), st["sides"][j]):
                 Q0 = Q[:, (side - 1) * M: side * M]
                 Q1 = Q[:, 4 * M + (side - 1) * M: 4 * M + side * M]
-                if self.outer(j, side):
-                    x, y = self._side_xy(j, side, s)
-                    alpha, beta, phi = self.bc(j, side, k[j], x, y)
-                    d = cheb_coeffs(phi, M)
-                    c = idx[(j, side)]
-                    pad_l, pad_r = c, n - c - M
+                if spec[0] == "outer":
+                    c = spec[1]
+                    alpha, beta = bcs[q]
+                    d = d_all[q]
+                    q += 1
                     if beta != 0:
-                        blk = Q0 - (alpha / beta) * Q1
-                        b = b - Q1 @ (d / beta)
+                        A[:, c:c + M] = Q0 - (alpha / beta) * Q1
+                        e.append((4 * M + (side - 1) * M, d / beta))
                         cj.append(("robin", c, d, alpha, beta))
                     else:
-                        blk = Q1
-                        b = b - Q0 @ (d / alpha)
+                        A[:, c:c + M] = Q1
+                        e.append(((side - 1) * M, d / alpha))
                         cj.append(("dirichlet", c, d, alpha, beta))
-                    A = A + torch.nn.functional.pad(blk, (pad_l, pad_r))
-                    used.extend(range(c, c + M))
                 else:
-                    key, sgn = self.iface(j, side)
-                    c = idx[("if",) + key]
-                    blk = torch.cat([Q0, sgn * Q1], dim=1)
-                    A = A + torch.nn.functional.pad(blk, (c, n - c - 2 * M))
-                    used.extend(range(c, c + 2 * M))
+                    _, c, sgn = spec
+                    A[:, c:c + M] = Q0
+                    A[:, c + M:c + 2 * M] = sgn * Q1
                     cj.append(("if", c, sgn))
-            st = self.source_terms(j, self.plan_k(j))
-            if st is not None:
-                b = b + st[0]
+            if e:
+                ev = torch.zeros(8 * M, dtype=torch.complex128, device=out.device)
+                for r, val in e:
+                    ev[r:r + M] = val
+                b = -linalg.matmul(Q, ev)
+            else:
+                b = torch.zeros(G, dtype=torch.complex128, device=out.device)
+            src = self.source_terms(j, self.plan_k(j))
+            if src is not None:
+                b = b + src[0]
             A_rows.append(A)
             b_rows.append(b)
             coef.append(cj)
-            col_sets.append(sorted(set(used)))
         A = torch.cat(A_rows)
         b = torch.cat(b_rows)
-        xsol = LeastSquares.apply(A, b, ([r.shape[0] for r in A_rows], col_sets))
+        xsol = LeastSquares.apply(A, b, ([r.shape[0] for r in A_rows], st["col_sets"]))
         cvecs = []
         for j in range(N):
             parts0, parts1 = [], []
-            for side, spec in zip((1, 2, 3, 4), coef[j]):
+            for spec in coef[j]:
                 if spec[0] == "robin":
                     _, c, d, alpha, beta = spec
                     u0 = xsol[c:c + M]

@@ -125,51 +125,6 @@ def test_qcache_stores_loads_and_fills_missing_blocks(mdp, tmp_path):
     assert np.abs(third - ref).max() <= tol and len(os.listdir(tmp_path)) == 2
 
 
-@pytest.mark.parametrize("m,n", [(500, 60), (3424, 384), (64, 64)])
-def test_householder_qr_gram_identity_and_least_squares(mdp, m, n):
-    """mdp_householder_qr: R^H R = A^H A, and R^{-1} (Q^H b) is the least-squares solution."""
-    from paper_2103_12172_gb300.strip import householder_qr
-    rng = np.random.default_rng(m + n)
-    A = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
-    A[:, 1] = 0.0
-    A[1, 1] = 2.0 + 0.0j        # a column already of the form beta e_k below row 0 ... plus row 0
-    A[0, 1] = 0.5
-    b = rng.standard_normal(m) + 1j * rng.standard_normal(m)
-    R, qb = householder_qr(torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda())
-    R = R.cpu().numpy()
-    G = A.conj().T @ A
-    assert np.abs(R.conj().T @ R - G).max() <= 1e-12 * np.abs(G).max()
-    x = np.linalg.solve(R, qb.cpu().numpy())
-    xr = np.linalg.lstsq(A, b, rcond=None)[0]
-    assert np.abs(x - xr).max() <= 1e-10 * np.abs(xr).max()
-
-
-def test_structured_qr_equals_the_dense_least_squares(mdp):
-    """Two-stage QR (a batched QR per row block on its own columns, then the stacked factors)
-    gives the least-squares solution and the Gram matrix of the whole block-sparse system."""
-    from paper_2103_12172_gb300.strip import householder_qr, structured_qr
-    rng = np.random.default_rng(7)
-    n = 40
-    rows = [90, 70, 110]
-    cols = [list(range(0, 16)), list(range(10, 30)), list(range(24, 40)) + [2, 3]]
-    A = np.zeros((sum(rows), n), complex)
-    r0 = 0
-    for g, cj in zip(rows, cols):
-        A[r0:r0 + g, cj] = rng.standard_normal((g, len(cj))) + 1j * rng.standard_normal((g, len(cj)))
-        r0 += g
-    b = rng.standard_normal(sum(rows)) + 1j * rng.standard_normal(sum(rows))
-    At, bt = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
-    R, qb = structured_qr(At, bt, rows, [sorted(c) for c in cols])
-    R = R.cpu().numpy()
-    G = A.conj().T @ A
-    assert np.abs(R.conj().T @ R - G).max() <= 1e-12 * np.abs(G).max()
-    x = np.linalg.solve(R, qb.cpu().numpy())
-    xr = np.linalg.lstsq(A, b, rcond=None)[0]
-    assert np.abs(x - xr).max() <= 1e-10 * np.abs(xr).max()
-    R2, _ = householder_qr(At, bt)
-    assert np.allclose(np.abs(np.diag(R)), np.abs(np.diag(R2.cpu().numpy())), rtol=1e-10)
-
-
 def test_plan_variants_agree_and_the_tuner_picks_one(mdp, tmp_path):
     """Every kernel variant the autotuner searches (FP64 or tensor-core gamma columns, FFT or
     direct dense rows, FFT block sizes, 2 or 4 staged sweep rows) gives the same columns to
