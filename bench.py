@@ -290,15 +290,17 @@ def kernel_source_sha():
 
 
 def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from profiles/traffic.json (an ncu
-    capture, or a smaller capture scaled by the units processed, as recorded there), or None
-    when absent or taken on a different kernel source."""
+    """DRAM bytes per step of `kernel` on `workload` from profiles/traffic.json (an ncu capture
+    of every launch of one step, or a smaller capture scaled by the units processed, as recorded
+    there), or None when absent or taken on a different kernel source. Per step, not per launch:
+    the plan's workspace budget decides how many waves (launches) a step takes, not how many
+    bytes it moves."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[workload][kernel]
     except (OSError, ValueError, KeyError):
         return None
-    return rec["dram_bytes_per_launch"] if rec.get("source_sha256") == kernel_source_sha() else None
+    return rec["dram_bytes_per_step"] if rec.get("source_sha256") == kernel_source_sha() else None
 
 
 # ------------------------------------------------------------------ reference arm
@@ -482,7 +484,8 @@ def measure(mdp, wl, steps, warmup, world=1, barrier=None, clocks=None, full=Tru
     launch_s = dom_ms / dom_launches / 1e3
     achieved = flops_per_launch / launch_s / 1e12
     peak = NOMINAL_FP64_GFLOPS / 1e3
-    traffic = recorded_traffic(dom, wl.name)
+    step_traffic = recorded_traffic(dom, wl.name)
+    traffic = step_traffic / launches_per_step if step_traffic else None
     hbm, hbm_src = hbm_peak()
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
