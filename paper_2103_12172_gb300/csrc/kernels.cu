@@ -381,10 +381,17 @@ __device__ __forceinline__ void tri_full_body(const Item &it, const SubDesc &d, 
     const double *p = reinterpret_cast<const double *>(st + RING + VS * lane + slot * 32 * VS);
     return CIN ? ld2(p) : cmk(p[0], 0.0);
   };
-  // right-hand side of grid row n from the staged ring values
+  // right-hand side of grid row n from the staged ring values (real data: the real part only,
+  // as in the projection sweep)
   auto rhs = [&](const char *st, int n) -> cplx {
     if (n < nlo || n > nhi) return cmk(0.0, 0.0);
     if (dense(n) >= 0) return sv(st, 0);
+    if (!CIN) {
+      if (xsym) return cmk(fma(sm1, sv(st, 1).re, sm0 * sv(st, 0).re), 0.0);
+      double v = sm0 * sv(st, 0).re;
+      v = fma(sm1, sv(st, 1).re, v); v = fma(sm2, sv(st, 2).re, v); v = fma(sm3, sv(st, 3).re, v);
+      return cmk(v, 0.0);
+    }
     if (xsym) {
       const cplx v0 = sv(st, 0);
       return caxpy(sm1, sv(st, 1), cmk(sm0 * v0.re, sm0 * v0.im));
@@ -577,10 +584,18 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
     const double *p = reinterpret_cast<const double *>(st + RING + VS * lane + slot * 32 * VS);
     return CIN ? ld2(p) : cmk(p[0], 0.0);
   };
-  // raw right-hand side of grid row n (swapped steps)
+  // raw right-hand side of grid row n (swapped steps). Real data (basis columns, !CIN): only the
+  // real part is formed; multiplying the zero imaginary parts would cost FP64 instructions that
+  // the compiler cannot drop (0 x is not 0 for every x in IEEE arithmetic).
   auto graw = [&](const char *st, int n) -> cplx {
     if (n < nlo || n > nhi) return cmk(0.0, 0.0);
     if (dense(n) >= 0) return sv(st, 0);
+    if (!CIN) {
+      if (xsym) return cmk(fma(sm1, sv(st, 1).re, sm0 * sv(st, 0).re), 0.0);
+      double v = sm0 * sv(st, 0).re;
+      v = fma(sm1, sv(st, 1).re, v); v = fma(sm2, sv(st, 2).re, v); v = fma(sm3, sv(st, 3).re, v);
+      return cmk(v, 0.0);
+    }
     if (xsym) {
       const cplx a0 = sv(st, 0);
       return caxpy(sm1, sv(st, 1), cmk(sm0 * a0.re, sm0 * a0.im));
@@ -608,7 +623,7 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
     for (int s_ = 0; s_ < 4; ++s_) v = cadd(v, cmul(ld2(row + 10 + 2 * s_), sv(st, s_)));
     return v;
   };
-  // the same with real coefficients (rows of the real run)
+  // the same with real coefficients (rows of the real run); real data: the real part only
   auto ghat_r = [&](const char *st, const double *row, int n) -> cplx {
     if (n < nlo || n > nhi) return cmk(0.0, 0.0);
     const double sc = row[8];
@@ -616,6 +631,12 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
       const cplx g = sv(st, 0);
       if (CIN) return cmk(sc * g.re, sc * g.im);
       return cmk(sc * g.re, 0.0);
+    }
+    if (!CIN) {
+      if (xsym) return cmk(fma(row[12], sv(st, 1).re, row[10] * sv(st, 0).re), 0.0);
+      double v = row[10] * sv(st, 0).re;
+      for (int s_ = 1; s_ < 4; ++s_) v = fma(row[10 + 2 * s_], sv(st, s_).re, v);
+      return cmk(v, 0.0);
     }
     if (xsym) {
       const cplx a0 = sv(st, 0);
