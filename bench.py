@@ -293,8 +293,9 @@ def recorded_traffic(kernel, workload):
     """DRAM bytes per step of `kernel` on `workload` from profiles/traffic.json (an ncu capture
     of every launch of one step, or a smaller capture scaled by the units processed, as recorded
     there), or None when absent or taken on a different kernel source. Per step, not per launch:
-    the plan's workspace budget decides how many waves (launches) a step takes, not how many
-    bytes it moves."""
+    the plan's workspace budget decides how many waves (launches) a step takes; the record is
+    taken with the plan the autotuner picks, whose packing also sets how many table rows come
+    from L2."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))[workload][kernel]
