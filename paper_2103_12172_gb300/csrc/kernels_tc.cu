@@ -152,6 +152,8 @@ __device__ __forceinline__ unsigned digit_pair(unsigned ahi, unsigned alo, unsig
 
 // One CTA: tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the launch's virtual blocks (F_TCOLS
 // numbering: per item, (Py - 2) middle rows x ceil(ncols / 64) column tiles, column tile fastest).
+constexpr int TC_PREFETCH = 3;   // stages ahead of the L2 prefetch of the field
+
 template <bool CIN>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     k_inv_cols_tc(Batch bt, const SubDesc *subs, const double *tab, const double *ws, const double2 *xi_user,
@@ -258,9 +260,22 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           p += qstride;
         }
       };
+      // the values TC_PREFETCH stages ahead are prefetched into L2 (no registers held), so the
+      // register loads one stage ahead find them there
+      auto prefetch8 = [&](int c) {
+        const int q0 = c * TC_KC + 1 + 8 * half;
+        const double *p = y + (long long)(q0 - 1) * qstride;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (live && q0 + j <= Nq) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+          p += qstride;
+        }
+      };
+      for (int c = 1; c < TC_PREFETCH && c < nchunk; ++c) prefetch8(c);
       load8(xv, 0);
       bool ok = true;
       for (int c = 0; c < nchunk; ++c, ++g) {
+        if (c + TC_PREFETCH < nchunk) prefetch8(c + TC_PREFETCH);
         if (c + 1 < nchunk) load8(xn, c + 1);
         const unsigned st = g % TC_STAGES;
         // the stage is free once the MMAs that last read it have completed
