@@ -138,6 +138,13 @@ __global__ void __launch_bounds__(256) k_adj_cols(Batch bt, const SubDesc *subs,
   const int cb = (it.ncols + 31) >> 5;
   const int b = (local % cb) * 32 + threadIdx.x;
   const int t = (local / cb) * 8 + threadIdx.y;
+  if (d.tc_cols && local == 0 && threadIdx.y == 0) {
+    // the adjoint field's per-column exponents, maxed by k_adj_tri, start at 0
+    int base[5];
+    red_slots(d, it.ncols, base);
+    int *ex = reinterpret_cast<int *>(ws + it.red_off + base[4] + 1);
+    for (int i = threadIdx.x; i < it.ncols; i += 32) ex[i] = 0;
+  }
   if (b >= it.ncols || t >= d.Py - 2) return;
   const double2 *c = cot + it.io_off + (long long)b * d.G + 2 * (d.Px + 2) + 4 * t;
   const cplx c0 = cmk(c[0].x, c[0].y), c1 = cmk(c[1].x, c[1].y), c2 = cmk(c[2].x, c[2].y), c3 = cmk(c[3].x, c[3].y);
@@ -325,6 +332,8 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
   double dk = 0.0, s_off = 0.0, s_dg = 0.0;
   cplx uj1 = cmk(0.0, 0.0), uj = DK ? ld2(y + 2 * (ybase + (long long)(Nt - 1) * nc)) : cmk(0.0, 0.0);
   const int jlo = nlo - nfirst, jhi = nhi - nfirst;
+  int emax = 0;   // largest biased exponent of muhat on the inner middle rows (integer compares only)
+  auto bexp = [](double v) { return (__double2hiint(v) >> 20) & 0x7ff; };
   // ujm: uhat(j - 1)
   auto emit = [&](int j, cplx mu, cplx ujm) {
     if (DK) {
@@ -341,6 +350,7 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
       uj1 = uj; uj = ujm;
     }
     if (j >= jlo && j <= jhi) st2(aptr(j), mu);
+    if (j >= jlo + 2 && j <= jhi - 2) emax = max(emax, max(bexp(mu.re), bexp(mu.im)));   // the rows the ring columns sum
   };
   cplx up = ld2(aptr(Nt - 1));
   for (int j = 0; j < 2; ++j) {
@@ -365,6 +375,11 @@ __device__ __forceinline__ double adj_tri_body(const Item &it, const SubDesc &d,
   }
   emit(0, up, cmk(0.0, 0.0));
   if (DK && Nt >= 3) dk = fma(dT[6 + 0], s_off, fma(dT[6 + 2], s_dg, dk));
+  if (d.tc_cols) {   // per column, over every mode: the common scale of the tensor-core ring sums
+    int base[5];
+    red_slots(d, nc, base);
+    atomicMax(reinterpret_cast<int *>(ws + it.red_off + base[4] + 1) + b, emax);
+  }
   return dk;
 }
 
@@ -683,9 +698,11 @@ cudaError_t launch_adjoint_tail(mdp_plan *p, const Batch *fb, int out_kind, cons
   if (dk) {
     ADJ_LAUNCH(F_ARING, k_adj_ring_rows<true><<<g1(fb[F_ARING].total_blocks), b8, p->fft_smem, st>>>(fb[F_ARING], ds, tab, ws));
     ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<true><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));
+    ADJ_LAUNCH(F_ATCOLS, launch_adj_cols_tc(fb[F_ATCOLS], ds, tab, ws, true, p->d_status, p->n_sm, st));
   } else {
     ADJ_LAUNCH(F_ARING, k_adj_ring_rows<false><<<g1(fb[F_ARING].total_blocks), b8, p->fft_smem, st>>>(fb[F_ARING], ds, tab, ws));
     ADJ_LAUNCH(F_ARINGC, k_adj_ring_cols<false><<<g1(fb[F_ARINGC].total_blocks), b8, 0, st>>>(fb[F_ARINGC], ds, tab, ws));
+    ADJ_LAUNCH(F_ATCOLS, launch_adj_cols_tc(fb[F_ATCOLS], ds, tab, ws, false, p->d_status, p->n_sm, st));
   }
   if (dk && basis)
     ADJ_LAUNCH(F_AGAM, k_adj_gamma<false, true><<<g1(fb[F_AGAM].total_blocks), b8, 0, st>>>(fb[F_AGAM], ds, tab, ws, cot, grad_xi, out_kind));

@@ -79,7 +79,7 @@ static __device__ __noinline__ bool item_in_bounds(const Batch &bt, const SubDes
     const long long qt = (long long)d.Nq * d.Nt;
     ok = ok && in_tab(d.fact_off, qt * (d.cplx ? 8 : 4)) && in_tab(d.dT_off, qt * 6) && in_tab(d.sin_off, 4LL * d.Nx) &&
          in_tab(d.geo_off, 4LL * d.G) && in_tab(d.seg_off, 5LL * d.Nq) && in_tab(d.fs_off, (long long)d.Nq * d.NYf * FSW) &&
-         (!d.tc_cols || in_tab(d.tcb_off, 128LL * ((d.Nq + 15) / 16)));
+         (!d.tc_cols || in_tab(d.tcb_off, 256LL * ((d.Nq + 15) / 16)));
     ok = ok && d.piv_off >= 0 && d.piv_off + qt <= bt.piv_n;
     ok = ok && it.io_off >= 0 && it.io_off + (long long)it.ncols * d.G <= bt.out_n;
   }

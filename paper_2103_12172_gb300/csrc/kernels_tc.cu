@@ -154,7 +154,13 @@ __device__ __forceinline__ unsigned digit_pair(unsigned ahi, unsigned alo, unsig
 // numbering: per item, (Py - 2) middle rows x ceil(ncols / 64) column tiles, column tile fastest).
 constexpr int TC_PREFETCH = 3;   // stages ahead of the L2 prefetch of the field
 
-template <bool CIN>
+// ADJ: the adjoint's sums (k_adj_ring_cols) instead: A[r][q] = muhat(q, n) on the inner middle
+// rows n = nlo + 2 + t, B at the ring columns mlo, mlo+1, mhi-1, mhi (the plan's second digit
+// block), the 4 sums per row and column written to the workspace rows 2 Px + 4 t + s that
+// k_adj_gamma reads, and with kind != 0 the k-gradient partials -Re <sum, s> of each warp of the
+// first producer half, 4 per tile, into the item's reduction slots (summed in order by
+// k_red_items).
+template <bool CIN, bool ADJ>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     k_inv_cols_tc(Batch bt, const SubDesc *subs, const double *tab, const double *ws, const double2 *xi_user,
                   double2 *out, int kind, int *status) {
@@ -194,7 +200,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       for (int v = blockIdx.x; v < bt.total_blocks && !abort_sh; v += gridDim.x) {
         Item it; int local;
         locate(bt, v, it, local);
-        if (MDP_CHECKED && !item_in_bounds(bt, subs, it, local, F_TCOLS, false)) continue;   // every warp skips it
+        if (MDP_CHECKED && !item_in_bounds(bt, subs, it, local, ADJ ? F_ATCOLS : F_TCOLS, ADJ)) continue;   // every warp skips it
         const int nchunk = (subs[it.sub].Nq + TC_KC - 1) / TC_KC;
         if (T > 0 && !mbar_wait(smem_u32(&tempty_bar), (T - 1) & 1u, &abort_sh)) break;
         tc_fence_after();
@@ -231,21 +237,34 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     for (int v = blockIdx.x; v < bt.total_blocks && !abort_sh; v += gridDim.x) {
       Item it; int local;
       locate(bt, v, it, local);
-      if (MDP_CHECKED && !item_in_bounds(bt, subs, it, local, F_TCOLS, false)) continue;     // every warp skips it
+      if (MDP_CHECKED && !item_in_bounds(bt, subs, it, local, ADJ ? F_ATCOLS : F_TCOLS, ADJ)) continue;     // every warp skips it
       const SubDesc &d = subs[it.sub];
-      const bool CD = d.cplx || CIN;
+      const bool CD = ADJ || d.cplx || CIN;
       const int nct = (it.ncols + 63) >> 6;
       const int t = local / nct, b0 = (local % nct) * 64;
-      const int yrow = t + 2;                 // middle row n = nlo + 1 + t
       const int b = b0 + (r >> 1), ri = r & 1;
       const bool live = b < it.ncols && (CD || ri == 0);
       const int Nq = d.Nq;
-      const long long ncd = (long long)it.ncols * (CD ? 2 : 1);   // doubles per stored row
-      const long long qstride = (long long)d.NYf * ncd;
-      const double *y = ws + it.y_off + (long long)yrow * ncd + (CD ? 2LL * b + ri : (long long)b);
       const int nchunk = (Nq + TC_KC - 1) / TC_KC;
-      // the column's scale: its largest biased exponent, recorded by k_tri, and its magic constant
-      const int E = live ? reinterpret_cast<const int *>(ws + it.red_off)[b] : 0;
+      int rbase[5];
+      if (ADJ) red_slots(d, it.ncols, rbase);
+      // this thread's value of mode q = 1 at y, of mode q at y + (q - 1) qstride; the column's
+      // scale: its largest biased exponent, recorded by the sweep that stored the field
+      const double *y;
+      long long qstride;
+      int E;
+      if (ADJ) {
+        const int j = d.nlo + 2 + t - d.nfirst;   // inner middle row n = nlo + 2 + t (matrix numbering)
+        qstride = 2LL * d.Nt * it.ncols;
+        y = ws + it.a_off + 2LL * ((long long)j * it.ncols + b) + ri;
+        E = live ? reinterpret_cast<const int *>(ws + it.red_off + rbase[4] + 1)[b] : 0;
+      } else {
+        const int yrow = t + 2;                 // middle row n = nlo + 1 + t
+        const long long ncd = (long long)it.ncols * (CD ? 2 : 1);   // doubles per stored row
+        qstride = (long long)d.NYf * ncd;
+        y = ws + it.y_off + (long long)yrow * ncd + (CD ? 2LL * b + ri : (long long)b);
+        E = live ? reinterpret_cast<const int *>(ws + it.red_off)[b] : 0;
+      }
       const long long mb = magic_bits(E);
       const double magic = __longlong_as_double(mb);
       const long long cb = mb - 0x0080808080808080LL;
@@ -310,7 +329,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         // B: the plan's 1 KiB block of sine digits for these 16 modes, 16 bytes per thread
         if (tid < 64)
           *reinterpret_cast<uint4 *>(sa + TC_DIG * TC_A_BYTES + 16 * tid) =
-              reinterpret_cast<const uint4 *>(tab + d.tcb_off)[c * 64 + tid];
+              reinterpret_cast<const uint4 *>(tab + d.tcb_off + (ADJ ? 128LL * nchunk : 0LL))[c * 64 + tid];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> MMA reads
         mbar_arrive(smem_u32(&full_bar[st]));
 #pragma unroll
@@ -364,17 +383,36 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         } else {
           u4[0] = val[0]; u4[1] = val[1]; u4[2] = val[2]; u4[3] = val[3];
         }
-        // lanes 2i (real part) and 2i+1 (imaginary part) of column b: the even lane writes
-        double o4[4];
+        if (ADJ) {
+          // each lane writes its part (real: even lane, imaginary: odd lane) of the 4 sums
+          double *wsw = const_cast<double *>(ws);   // rows and slots no other lane of the launch reads
+          double part = 0.0;
+          if (b < it.ncols) {
 #pragma unroll
-        for (int s = 0; s < 4; ++s) o4[s] = __shfl_xor_sync(0xffffffffu, u4[s], 1);
-        if (ri == 0 && b < it.ncols) {
-          const int g0 = 2 * (d.Px + 2) + 4 * t;
+            for (int s = 0; s < 4; ++s) {
+              const long long o = 2LL * ((long long)(2 * d.Px + 4 * t + s) * it.ncols + b) + ri;
+              wsw[it.r_off + o] = u4[s];
+              if (kind) part = fma(-u4[s], ws[it.s_off + o], part);
+            }
+          }
+          if (kind) {
 #pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            cplx uv = cmk(-u4[s], CD ? -o4[s] : 0.0);
-            if (kind == MDP_OUT_P) uv = cadd(uv, density<CIN>(d, it, ws, tab, xi_user, b, g0 + s));
-            out[it.io_off + (long long)b * d.G + g0 + s] = make_double2(uv.re, uv.im);
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if (lane == 0) wsw[it.red_off + rbase[2] + 4 * local + quarter] = part;
+          }
+        } else {
+          // lanes 2i (real part) and 2i+1 (imaginary part) of column b: the even lane writes
+          double o4[4];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) o4[s] = __shfl_xor_sync(0xffffffffu, u4[s], 1);
+          if (ri == 0 && b < it.ncols) {
+            const int g0 = 2 * (d.Px + 2) + 4 * t;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              cplx uv = cmk(-u4[s], CD ? -o4[s] : 0.0);
+              if (kind == MDP_OUT_P) uv = cadd(uv, density<CIN>(d, it, ws, tab, xi_user, b, g0 + s));
+              out[it.io_off + (long long)b * d.G + g0 + s] = make_double2(uv.re, uv.im);
+            }
           }
         }
       }
@@ -394,10 +432,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 int tc_cols_smem_bytes() { return TC_STAGES * TC_STAGE_BYTES; }
 
 cudaError_t set_tc_kernel_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_inv_cols_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tc_cols_smem_bytes());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_inv_cols_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_cols_smem_bytes());
+  const int sm = tc_cols_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_inv_cols_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_cols_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_inv_cols_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   return e;
 }
 
@@ -406,9 +444,17 @@ cudaError_t launch_inv_cols_tc(const Batch &b, const SubDesc *subs, const double
                                cudaStream_t st) {
   const int grid = std::max(1, std::min(b.total_blocks, 2 * n_sm));
   if (xi_user)
-    k_inv_cols_tc<true><<<grid, TC_THREADS, tc_cols_smem_bytes(), st>>>(b, subs, tab, ws, xi_user, out, kind, status);
+    k_inv_cols_tc<true, false><<<grid, TC_THREADS, tc_cols_smem_bytes(), st>>>(b, subs, tab, ws, xi_user, out, kind, status);
   else
-    k_inv_cols_tc<false><<<grid, TC_THREADS, tc_cols_smem_bytes(), st>>>(b, subs, tab, ws, xi_user, out, kind, status);
+    k_inv_cols_tc<false, false><<<grid, TC_THREADS, tc_cols_smem_bytes(), st>>>(b, subs, tab, ws, xi_user, out, kind, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_cols_tc(const Batch &b, const SubDesc *subs, const double *tab, double *ws, bool dk,
+                               int *status, int n_sm, cudaStream_t st) {
+  const int grid = std::max(1, std::min(b.total_blocks, 2 * n_sm));
+  k_inv_cols_tc<false, true><<<grid, TC_THREADS, tc_cols_smem_bytes(), st>>>(b, subs, tab, ws, nullptr, nullptr,
+                                                                            dk ? 1 : 0, status);
   return cudaGetLastError();
 }
 

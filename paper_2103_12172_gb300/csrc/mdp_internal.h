@@ -57,7 +57,8 @@ struct SubDesc {
   long long seg_off;    // doubles: per mode [Nq][5] = (rlo, rhi, frlo, frhi, itop): real rows of the
                         // factor table, real rows of the forward-sweep table, last swept row
   long long fs_off;     // doubles: projection forward-sweep table [Nq][NYf][FSW] (rows i0..)
-  long long tcb_off;    // doubles: tensor-core gamma columns: per 16 modes a 1 KiB block of the fp16 digits
+  long long tcb_off;    // doubles: tensor-core sums: per 16 modes a 1 KiB block of the fp16 sine digits at the
+                        // gamma columns, then as many at the adjoint's ring columns (one column further in)
                         // of the sines, in the shared-memory operand layout of k_inv_cols_tc
   long long out_off;    // complex elements: start of the subdomain's output block
   long long rec_off;    // complex elements: start of the receiver block [n_cols][Px - 2]
@@ -234,7 +235,7 @@ inline void set_bounds(const mdp_plan *p, Batch &b, long long out_n, bool grad) 
 
 // kernel families (each has its own block decomposition of an item); F_A* are the adjoint's
 enum Fam { F_EXT = 0, F_RES, F_FROWS, F_TRI, F_IROWS, F_ICOLS, F_AFWD, F_ATRI, F_ARING, F_ARINGC, F_AGAM, F_IREC,
-           F_ACOLS, F_TCOLS, NFAM };
+           F_ACOLS, F_TCOLS, F_ATCOLS, NFAM };
 
 // Blocks of kernel family f for an item of ncols columns: 32 columns (x) times BY tasks (y).
 // The same function numbers the blocks on the host (prefix sums) and in the kernels.
@@ -259,7 +260,8 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
     case F_ARING:
       if (d.rows_fft) return 4 * ((ncols + d.fpb - 1) / d.fpb);
       return cb * ((4 * d.Px + 7) / 8);
-    case F_ARINGC: return cb * ((d.Py - 4 + 7) / 8);
+    case F_ARINGC: return d.tc_cols ? 0 : cb * ((d.Py - 4 + 7) / 8);
+    case F_ATCOLS: return d.tc_cols && d.Py > 4 ? ((ncols + 63) / 64) * (d.Py - 4) : 0;   // tiles: inner middle row x 64 columns
     case F_AGAM: return cb * ((d.G + 7) / 8);
     case F_IREC: return d.nrec < 0 ? 0 : cb * (((d.xsym ? d.Ph - 1 : d.Px - 2) + 7) / 8);
     case F_ACOLS: return cb * ((d.Py - 2 + 7) / 8);
@@ -267,18 +269,20 @@ inline __host__ __device__ int blocks_for(int f, const SubDesc &d, int ncols) {
   }
 }
 
-// slot bases of the per-block gradient partials of an item: [ATRI | ARING | ARINGC | AGAM], total
+// slot bases of the per-block gradient partials of an item: [ATRI | ARING | ARINGC or 4 per ATCOLS
+// tile | AGAM], total
 inline __host__ __device__ void red_slots(const SubDesc &d, int ncols, int base[5]) {
   base[0] = 0;
   base[1] = base[0] + blocks_for(F_ATRI, d, ncols);
   base[2] = base[1] + blocks_for(F_ARING, d, ncols);
-  base[3] = base[2] + blocks_for(F_ARINGC, d, ncols);
+  base[3] = base[2] + blocks_for(F_ARINGC, d, ncols) + 4 * blocks_for(F_ATCOLS, d, ncols);
   base[4] = base[3] + blocks_for(F_AGAM, d, ncols);
 }
 // Workspace slices of an item of ncols columns, in doubles from the item's base (each 256-byte
 // aligned): basis densities, ring residual, dense-row transforms, mode-space field, and for the
-// gradient pass the adjoint field, k-source and per-block partials; in the projection the last
-// slice holds per column the largest biased exponent of the kept mode-space rows (ints).
+// gradient pass the adjoint field, k-source and per-block partials; the last slice holds per
+// column the largest biased exponent (ints) of the kept mode-space rows (projection) or of the
+// adjoint field's inner middle rows (gradient pass, after the partials and their total).
 inline __host__ __device__ void item_workspace(const SubDesc &d, int ncols, bool grad, long long &xi, long long &r,
                                                long long &gr, long long &y, long long &a, long long &s,
                                                long long &red, long long &total) {
@@ -292,7 +296,7 @@ inline __host__ __device__ void item_workspace(const SubDesc &d, int ncols, bool
   s = off;  off += grad ? al((long long)d.R * ncols * 2) : 0;
   int rs[5];
   red_slots(d, ncols, rs);
-  red = off; off += grad ? al(rs[4] + 1) : al((ncols + 1) / 2);
+  red = off; off += grad ? al(rs[4] + 1 + (ncols + 1) / 2) : al((ncols + 1) / 2);
   total = off;
 }
 const char *fam_name(int f);
@@ -317,6 +321,9 @@ cudaError_t set_tc_kernel_attributes();   // kernels_tc.cu
 cudaError_t launch_inv_cols_tc(const Batch &b, const SubDesc *subs, const double *tab, const double *ws,
                                const double2 *xi_user, double2 *out, int kind, int *status, int n_sm,
                                cudaStream_t st);
+// the adjoint's sums at the 4 ring columns of the inner middle rows (dk: with the k-gradient partials)
+cudaError_t launch_adj_cols_tc(const Batch &b, const SubDesc *subs, const double *tab, double *ws, bool dk,
+                               int *status, int n_sm, cudaStream_t st);
 cudaError_t launch_project(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,
                            double2 *out, double2 *out_rec, cudaStream_t st);
 cudaError_t launch_adjoint(mdp_plan *p, const Batch *fam_batches, int out_kind, const double2 *xi_user,

@@ -23,7 +23,7 @@ static const double kSingularTol = 1e-13; // pivot below this x max|T| -> singul
 const char *fam_name(int f) {
   static const char *names[NFAM] = {"k_extend", "k_residual", "k_fwd_rows", "k_tri", "k_inv_rows", "k_inv_cols",
                                     "k_adj_rows", "k_adj_tri", "k_adj_ring_rows", "k_adj_ring_cols", "k_adj_gamma",
-                                    "k_inv_rec", "k_adj_cols", "k_inv_cols_tc"};
+                                    "k_inv_rec", "k_adj_cols", "k_inv_cols_tc", "k_adj_ring_cols_tc"};
   return (f >= 0 && f < NFAM) ? names[f] : "?";
 }
 
@@ -404,7 +404,7 @@ static bool layout_tables(mdp_plan *p) {
     d.geo_off = off;  off += al(4LL * d.G);
     d.seg_off = off;  off += al(5LL * d.Nq);
     d.fs_off = off;   off += al((long long)d.Nq * d.NYf * FSW);
-    d.tcb_off = off;  off += d.tc_cols ? al(128LL * ((d.Nq + 15) / 16)) : 0;
+    d.tcb_off = off;  off += d.tc_cols ? al(256LL * ((d.Nq + 15) / 16)) : 0;
     d.piv_off = poff; poff += al((long long)d.Nq * d.Nt);
     d.out_off = out;  out += (long long)d.G * d.n_cols;
   }
@@ -439,7 +439,9 @@ static uint16_t f16_of_small_int(int v) {
 // in 7 balanced base-256 digits (the bytes of W + 0x0080808080808080, each minus 128). Stored in
 // the operand layout: 8 x 16-byte core matrices, K (the mode) fastest, 128 B between the two
 // K halves and 256 B between groups of 8 rows.
-static void fill_tc_block(const SubDesc &d, const double *S, uint16_t *blk) {
+// inner: the adjoint's ring columns mlo, mlo+1, mhi-1, mhi instead of the gamma columns
+// mlo-1, mlo, mhi, mhi+1 (one column further in on either side)
+static void fill_tc_block(const SubDesc &d, const double *S, uint16_t *blk, bool inner) {
   const int nch = (d.Nq + 15) / 16, N2 = 2 * d.Nx;
   int64_t magic, w;
   const double six = 6.0;
@@ -449,8 +451,8 @@ static void fill_tc_block(const SubDesc &d, const double *S, uint16_t *blk) {
       for (int kk = 0; kk < 16; ++kk) {
         const int q = c * 16 + 1 + kk;
         int m, par = -1;
-        if (d.xsym) { m = (so & 1) ? d.mlo : d.mlo - 1; par = so < 2 ? 1 : 0; }
-        else m = so == 0 ? d.mlo - 1 : so == 1 ? d.mlo : so == 2 ? d.mhi : d.mhi + 1;
+        if (d.xsym) { m = ((so & 1) ? d.mlo : d.mlo - 1) + (inner ? 1 : 0); par = so < 2 ? 1 : 0; }
+        else m = (so == 0 ? d.mlo - 1 : so == 1 ? d.mlo : so == 2 ? d.mhi : d.mhi + 1) + (inner ? (so < 2 ? 1 : -1) : 0);
         const double s = (q <= d.Nq && (par < 0 || (q & 1) == par)) ? S[(int)(((long long)q * m) % N2)] : 0.0;
         const double y = s + six;
         std::memcpy(&w, &y, 8);
@@ -474,7 +476,10 @@ static void fill_tables(mdp_plan *p) {
       S[2 * d.Nx + j] = (2.0 / d.Nx) * S[j];
     }
     for (int i = 0; i < 5 * d.Nq; ++i) p->host_tables[d.seg_off + i] = hs.seg[i];
-    if (d.tc_cols) fill_tc_block(d, S, reinterpret_cast<uint16_t *>(&p->host_tables[d.tcb_off]));
+    if (d.tc_cols) {
+      fill_tc_block(d, S, reinterpret_cast<uint16_t *>(&p->host_tables[d.tcb_off]), false);
+      fill_tc_block(d, S, reinterpret_cast<uint16_t *>(&p->host_tables[d.tcb_off + 128LL * ((d.Nq + 15) / 16)]), true);
+    }
     double *g = &p->host_tables[d.geo_off];
     for (int i = 0; i < d.G; ++i) {
       g[4 * i + 0] = hs.owner[i];

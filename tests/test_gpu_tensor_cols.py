@@ -110,3 +110,49 @@ def test_off_centre_grids_at_and_beyond_the_limit(mdp):
     ref64, _ = project(mdp, [sub], False)
     assert prof.get("k_inv_cols", (0, 0))[1] > 0 and "k_inv_cols_tc" not in prof, prof
     assert np.array_equal(got, ref64)
+
+
+def adjoint(mdp, subs, tc, cot, xi=None, kind="Q"):
+    old = os.environ.get("MDP_TC_COLS")
+    os.environ["MDP_TC_COLS"] = "1" if tc else "0"
+    try:
+        plan = mdp.Plan(subs)
+    finally:
+        if old is None:
+            del os.environ["MDP_TC_COLS"]
+        else:
+            os.environ["MDP_TC_COLS"] = old
+    plan.profile(True)
+    gx, gk = plan.adjoint(torch.from_numpy(cot).cuda(), xi=None if xi is None else torch.from_numpy(xi).cuda(),
+                          kind=kind)
+    torch.cuda.synchronize()
+    plan.status()
+    prof = plan.profile_read()
+    plan.profile(False)
+    plan.close()
+    return gx.cpu().numpy(), gk.cpu().numpy(), prof
+
+
+@pytest.mark.parametrize("case", ["centred", "off_centre", "user_P"])
+def test_adjoint_ring_sums_on_the_tensor_cores_match_fp64(mdp, case):
+    """The adjoint's sums over the modes at the 4 ring columns of the inner middle rows
+    (k_adj_ring_cols) on the tensor cores: grad_xi and dLoss/dk equal the FP64 sums' to 1e-11
+    (the same split as the forward gamma columns, on the adjoint field's own per-column scale)."""
+    if case == "centred":
+        subs, user, kind = [W.unit_subdomain(0, 0, 257, 30.0, W.AP_DIRX_SOMMY, 8),
+                            W.unit_subdomain(1, 0, 129, 12.0, W.AP_DIRICHLET4, 6)], False, "Q"
+    elif case == "off_centre":
+        subs, user, kind = [off_centre(65, 7.0, 4)], False, "Q"
+    else:
+        subs, user, kind = [W.small_subdomain(129, 20.0, W.AP_DIRX_SOMMY, 3)], True, "P"
+    plan = mdp.Plan(subs)
+    n = plan.output_size
+    plan.close()
+    rng = np.random.default_rng(17)
+    cot = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    xi = rng.standard_normal(n) + 1j * rng.standard_normal(n) if user else None
+    gx_tc, gk_tc, prof = adjoint(mdp, subs, True, cot, xi, kind)
+    gx_64, gk_64, prof64 = adjoint(mdp, subs, False, cot, xi, kind)
+    assert "k_adj_ring_cols_tc" in prof and "k_adj_ring_cols" in prof64
+    assert np.abs(gx_tc - gx_64).max() <= 1e-11 * np.abs(gx_64).max()
+    assert np.abs(gk_tc - gk_64).max() <= 1e-11 * np.abs(gk_64).max()
