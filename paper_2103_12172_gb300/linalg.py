@@ -168,7 +168,8 @@ class _Structure:
                      for o, p in zip(self.order, self.private)]
 
 
-_structures = {}
+_structures = {}   # per (n, rows, cols, device); the least recently built go first beyond 32
+_STRUCTURES_MAX = 32
 
 
 def structured_qr(A, b, rows, cols):
@@ -190,6 +191,8 @@ def structured_qr(A, b, rows, cols):
     key = (n, tuple(rows), tuple(tuple(c) for c in cols), str(dev))
     st = _structures.get(key)
     if st is None:
+        if len(_structures) >= _STRUCTURES_MAX:
+            _structures.pop(next(iter(_structures)))
         st = _structures[key] = _Structure(n, rows, cols, dev)
     if not st.ok:
         return householder_qr(A, b)
