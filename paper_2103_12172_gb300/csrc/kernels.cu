@@ -298,9 +298,11 @@ __global__ void __launch_bounds__(256) k_fwd_rows(Batch bt, const SubDesc *subs,
 // CF: complex factors (Sommerfeld AP). CIN: complex ring data. Factor rows [rlo, rhi) of a
 // complex AP are real to working precision (set by the plan): there the sweeps use real factors,
 // and the forward sweep stays in real arithmetic while the data are still real (real densities,
-// no complex factor row met yet). Operands are staged like the projection sweep's, TRI_STAGES
-// rows ahead: the factor row, the 4-byte word holding the row's swap flag, and the lane's ring
-// values (forward) or stored y (back).
+// no complex factor row met yet). The forward sweep stores y~_i = y_i / d_i (the pivot's
+// reciprocal is in the staged factor row), so the back substitution is x_i = y~_i - u1 x_{i+1}
+// - u2 x_{i+2} with no product by 1/d; while the data are real, y~ is stored packed as in the
+// projection sweep. Operands are staged 2 rows ahead: the factor row, the 4-byte word holding
+// the row's swap flag, and the lane's ring values (forward) or stored y~ (back).
 template <bool CIN>
 __host__ __device__ constexpr int full_stage_bytes() { return 80 + 4 * 32 * (CIN ? 16 : 8); }
 
@@ -331,6 +333,10 @@ __device__ __forceinline__ void tri_full_body(const Item &it, const SubDesc &d, 
     rhi = (int)sg[1];
   }
   auto ystore = [&](int i, cplx v) { st2(y + 2 * (ybase + (long long)i * nc), v); };
+  // a real y~ of the warp's 32 columns packed into the first half of their complex slots of row
+  // i (the back substitution stores x over them after every lane's copy of row i has landed)
+  auto ystore_re = [&](int i, double v) { y[2 * (ybase + (long long)i * nc) - lane] = v; };
+  int ipack = i0;   // rows i0 .. ipack-1 hold packed real y~
   auto dense = [&](int n) -> int {
     return n == nlo ? 0 : n == nlo + 1 ? 1 : n == nhi - 1 ? 2 : n == nhi ? 3 : -1;
   };
@@ -423,7 +429,7 @@ __device__ __forceinline__ void tri_full_body(const Item &it, const SubDesc &d, 
     const cplx l = ld2(row);
     cplx yv;
     if (flag(st, i)) { yv = g; cur = cfms(cur, l, g); } else { yv = cur; cur = cfms(g, l, cur); }
-    ystore(i, yv);
+    ystore(i, cmul(ld2(row + 2), yv));
     end_fwd(i);
   };
   if (CF) {  // complex factor rows below the real run
@@ -437,27 +443,31 @@ __device__ __forceinline__ void tri_full_body(const Item &it, const SubDesc &d, 
       for (; i < e; ++i) {
         const char *st = begin(i);
         const double g = rhs(st, i + 1 + nfirst).re;
-        const double l = reinterpret_cast<const double *>(st)[0];
+        const double l = reinterpret_cast<const double *>(st)[0], dinv = reinterpret_cast<const double *>(st)[CF ? 2 : 1];
         double yv;
         if (flag(st, i)) { yv = g; cur.re = fma(-l, g, cur.re); } else { yv = cur.re; cur.re = fma(-l, cur.re, g); }
-        ystore(i, cmk(yv, 0.0));
+        ystore_re(i, dinv * yv);
         end_fwd(i);
       }
+      ipack = i;
     } else {
       for (; i < e; ++i) {
         const char *st = begin(i);
         const cplx g = rhs(st, i + 1 + nfirst);
-        const double l = reinterpret_cast<const double *>(st)[0];
+        const double l = reinterpret_cast<const double *>(st)[0], dinv = reinterpret_cast<const double *>(st)[CF ? 2 : 1];
         cplx yv;
         if (flag(st, i)) { yv = g; cur = caxpy(-l, g, cur); } else { yv = cur; cur = caxpy(-l, cur, g); }
-        ystore(i, yv);
+        ystore(i, cmk(dinv * yv.re, dinv * yv.im));
         end_fwd(i);
       }
     }
   }
   if (CF)  // complex factor rows above the real run
     for (; i < iend; ++i) fwd_complex(i);
-  ystore(iend, cur);
+  {  // the top row's pivot is not staged by the forward sweep
+    const double *rt = F + (long long)iend * FW;
+    ystore(iend, CF ? cmul(ld2(rt + 2), cur) : cmk(rt[1] * cur.re, rt[1] * cur.im));
+  }
   // the stored rows are read back below by this thread's asynchronous copies: order them after
   // its stores
   __threadfence_block();
@@ -465,7 +475,8 @@ __device__ __forceinline__ void tri_full_body(const Item &it, const SubDesc &d, 
   auto fetch_back = [&](int i) {
     char *st = stage(i);
     fetch_row(st, i);
-    if (i >= i0) cp_async16(st + RING + 16 * lane, y + 2 * (ybase + (long long)i * nc));
+    if (i >= ipack) cp_async16(st + RING + 16 * lane, y + 2 * (ybase + (long long)i * nc));
+    else if (i >= i0) cp_async8(st + RING + 16 * lane, y + 2 * (ybase + (long long)i * nc) - lane);
     cp_async_commit();
   };
   auto end_back = [&](int i) {
@@ -476,12 +487,15 @@ __device__ __forceinline__ void tri_full_body(const Item &it, const SubDesc &d, 
     if (iend - j >= 0) fetch_back(iend - j); else cp_async_commit();
   }
   cplx x1 = cmk(0.0, 0.0), x2 = cmk(0.0, 0.0);
+  // the lane's y~ of row i from its stage (packed real rows: the real part only)
+  auto ytil = [&](const char *st, int i) -> cplx {
+    const double *p = reinterpret_cast<const double *>(st + RING + 16 * lane);
+    return i >= ipack ? ld2(p) : i >= i0 ? cmk(p[0], 0.0) : cmk(0.0, 0.0);
+  };
   auto back_complex = [&](int i) {
     const char *st = begin(i);
     const double *row = reinterpret_cast<const double *>(st);
-    const cplx yi = i >= i0 ? ld2(reinterpret_cast<const double *>(st + RING + 16 * lane)) : cmk(0.0, 0.0);
-    const cplx dinv = ld2(row + 2), u1 = ld2(row + 4);
-    cplx x = cfms(cmul(dinv, yi), u1, x1);
+    cplx x = cfms(ytil(st, i), ld2(row + 4), x1);
     if (flag(st, i)) x = cfms(x, ld2(row + 6), x2);
     end_back(i);
     ystore(i, x);
@@ -490,9 +504,9 @@ __device__ __forceinline__ void tri_full_body(const Item &it, const SubDesc &d, 
   auto back_real = [&](int i) {
     const char *st = begin(i);
     const double *row = reinterpret_cast<const double *>(st);
-    const cplx yi = i >= i0 ? ld2(reinterpret_cast<const double *>(st + RING + 16 * lane)) : cmk(0.0, 0.0);
-    const double dinv = row[CF ? 2 : 1], u1 = row[CF ? 4 : 2];
-    cplx x = cmk(fma(-u1, x1.re, dinv * yi.re), fma(-u1, x1.im, dinv * yi.im));
+    const cplx yi = ytil(st, i);
+    const double u1 = row[CF ? 4 : 2];
+    cplx x = cmk(fma(-u1, x1.re, yi.re), fma(-u1, x1.im, yi.im));
     if (flag(st, i)) {
       const double u2 = row[CF ? 6 : 3];
       x.re = fma(-u2, x2.re, x.re);
@@ -547,6 +561,14 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
     const long long o = ybase + (long long)(i - i0) * nc;
     if (CD) st2(y + 2 * o, v); else y[o] = v.re;
   };
+  // complex data whose y~ is still real (the real forward run of real data): the warp's 32 real
+  // values of row i packed into the first half of its 32 complex slots (lane's own column b), so
+  // the round trip moves 8 bytes a value instead of 16. The back substitution stores the kept x
+  // over them only after every lane's copy of row i has landed (the warp syncs first).
+  auto ystore_re = [&](int i, double v) {
+    if (CD) y[2 * (ybase + (long long)(i - i0) * nc) - lane] = v; else y[ybase + (long long)(i - i0) * nc] = v;
+  };
+  int ipack = i0;   // rows i0 .. ipack-1 hold packed real y~
   auto dense = [&](int n) -> int {
     return n == nlo ? 0 : n == nlo + 1 ? 1 : n == nhi - 1 ? 2 : n == nhi ? 3 : -1;
   };
@@ -686,14 +708,15 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
         const char *st = begin_fwd(i);
         const double *row = reinterpret_cast<const double *>(st);
         const int n = i + 1 + nfirst;
-        if (!swapped(row[22])) { ystore(i, ct); ct.re = fma(-row[0], ct.re, ghat_r(st, row, n).re); }
+        if (!swapped(row[22])) { ystore_re(i, ct.re); ct.re = fma(-row[0], ct.re, ghat_r(st, row, n).re); }
         else {
           const double g = graw(st, n).re;
-          ystore(i, cmk(row[6] * g, 0.0));
+          ystore_re(i, row[6] * g);
           ct.re = fma(-row[4], g, row[2] * ct.re);
         }
         end_fwd(i);
       }
+      ipack = i;
     } else {
       for (; i < e; ++i) {
         const char *st = begin_fwd(i);
@@ -737,7 +760,9 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
       for (int c = lane; c < 3; c += nact) cp_async16(st + 16 * c, src + 2 * c);
     }
     const long long o = ybase + (long long)(i - i0) * nc;
-    if (CD) cp_async16(st + RING + 16 * lane, y + 2 * o); else cp_async8(st + RING + 8 * lane, y + o);
+    if (!CD) cp_async8(st + RING + 8 * lane, y + o);
+    else if (i < ipack) cp_async8(st + RING + 16 * lane, y + 2 * o - lane);
+    else cp_async16(st + RING + 16 * lane, y + 2 * o);
     cp_async_commit();
   };
   for (int j = 0; j < TRI_STAGES; ++j) {
@@ -753,7 +778,7 @@ __device__ __forceinline__ void tri_fs_body(const Item &it, const SubDesc &d, co
     const char *st = sw + ((itop - i) & (TRI_STAGES - 1)) * SB;
     const double *rb = reinterpret_cast<const double *>(st);        // table doubles 18..23
     const double *yp = reinterpret_cast<const double *>(st + RING + (CD ? 16 : 8) * lane);
-    const cplx yi = CD ? ld2(yp) : cmk(yp[0], 0.0);
+    const cplx yi = CD && i >= ipack ? ld2(yp) : cmk(yp[0], 0.0);
     cplx x;
     if (!CD || (i >= frlo && i < frhi)) {
       x = cmk(fma(-rb[0], x1.re, yi.re), CD ? fma(-rb[0], x1.im, yi.im) : 0.0);
