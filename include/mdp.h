@@ -275,10 +275,11 @@ mdp_status mdp_basis_densities(mdp_plan *p, int sub, int col0, int ncols, mdp_c6
  * [nrhs][ny][nx] with the meaning of mdp_ap_solve_batch (u may equal g). Each call recomputes
  * the per-mode factors on the host and copies them, with the descriptor, into a fixed scratch
  * array of mdp_ap_solve_noalloc_limit_bytes() bytes (32 MiB) that lives in device memory for
- * the lifetime of the process on every device that loads the library; the mode-space buffer
- * uses the rest of it, in chunks of right-hand sides. Grids whose tables plus one right-hand
- * side do not fit return MDP_ERR_ARG (a 321^2 grid fits, 13 right-hand sides per chunk at
- * 257^2; a 385^2 grid does not). The copies come from pageable host memory, so each call
+ * the lifetime of the process on every device that loads the library (only the tables the solve
+ * reads: the factor rows, the sine table and the pivot flags); the mode-space buffer uses the
+ * rest of it, in chunks of right-hand sides. Grids whose tables plus one right-hand side do not
+ * fit return MDP_ERR_ARG (a 641^2 grid fits, 27 right-hand sides per chunk at 257^2; a 705^2
+ * grid does not). The copies come from pageable host memory, so each call
  * waits on the host until the work already queued on `cuda_stream` has finished. The call
  * cannot be captured into a CUDA graph: on a capturing stream it returns MDP_ERR_STATE and
  * enqueues nothing. The first call on a device looks up the array's device address

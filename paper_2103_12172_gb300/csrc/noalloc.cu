@@ -1,9 +1,10 @@
 // mdp_ap_solve_noalloc: the full-grid AP solve of mdp_ap_solve_batch for callers that cannot
 // allocate device memory (for example code running where cudaMalloc is unavailable or
 // forbidden, such as inside an allocator-free runtime or a caller that owns every device byte).
-// Its scratch -- the subdomain descriptor, the per-mode LU factors and sine tables, and the
-// mode-space buffer -- lives in one file-scope device array of fixed size that every GPU loading
-// this library holds until the process exits. Nothing is allocated on the device per call.
+// Its scratch -- the subdomain descriptor, the per-mode LU factor rows, the sine table, the
+// pivot flags (the only tables the full-grid solve reads) and the mode-space buffer -- lives in
+// one file-scope device array of fixed size that every GPU loading this library holds until the
+// process exits. Nothing is allocated on the device per call.
 #include "mdp_internal.h"
 
 #include <algorithm>
@@ -51,11 +52,20 @@ extern "C" mdp_status mdp_ap_solve_noalloc(const mdp_subdomain *sub, int nrhs, c
     st = MDP_ERR_NOMEM;
   }
   if (st != MDP_OK) return st;
-  const mdp::SubDesc &hd = hp.subs[0].d;
-  // scratch layout: [descriptor | tables | pivot flags | mode-space buffer]
+  const mdp::SubDesc &hs = hp.subs[0].d;
+  // scratch layout: [descriptor | factor rows, sine table | pivot flags | mode-space buffer]; the
+  // descriptor copied to the device is rebased onto that table (the full-grid solve reads the
+  // factor rows, the sines and the pivot flags only, so the other offsets are never followed)
+  mdp::SubDesc hd = hs;
+  const size_t n_fact = (size_t)hs.Nq * hs.Nt * (hs.cplx ? 8 : 4), n_sin = 4 * (size_t)hs.Nx;
+  const size_t n_piv = (size_t)hs.Nq * hs.Nt;
+  hd.fact_off = 0;
+  hd.sin_off = (long long)((n_fact + 31) & ~(size_t)31);
+  hd.piv_off = 0;
+  hd.dT_off = hd.geo_off = hd.seg_off = hd.fs_off = hd.tcb_off = 0;
   const size_t off_tab = align256(sizeof(mdp::SubDesc));
-  const size_t off_piv = off_tab + align256(hp.host_tables.size() * sizeof(double));
-  const size_t off_buf = off_piv + align256(hp.host_piv.size());
+  const size_t off_piv = off_tab + align256(((size_t)hd.sin_off + n_sin) * sizeof(double));
+  const size_t off_buf = off_piv + align256(n_piv);
   const size_t per_rhs = (size_t)hd.Nq * hd.Nt * 2 * sizeof(double);
   if (off_buf + per_rhs > kNoAllocScratchBytes) return MDP_ERR_ARG;  // grid too large for the fixed scratch
   if (nrhs == 0) return MDP_OK;
@@ -75,9 +85,11 @@ extern "C" mdp_status mdp_ap_solve_noalloc(const mdp_subdomain *sub, int nrhs, c
   // pageable-source copies are staged before these calls return, so the host tables may go (and
   // each call waits on the host for the work already queued on `s`)
   if (cudaMemcpyAsync(b, &hd, sizeof hd, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(b + off_tab, hp.host_tables.data(), hp.host_tables.size() * sizeof(double),
+      cudaMemcpyAsync(b + off_tab, hp.host_tables.data() + hs.fact_off, n_fact * sizeof(double),
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(b + off_piv, hp.host_piv.data(), hp.host_piv.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      cudaMemcpyAsync(b + off_tab + (size_t)hd.sin_off * sizeof(double), hp.host_tables.data() + hs.sin_off,
+                      n_sin * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(b + off_piv, hp.host_piv.data() + hs.piv_off, n_piv, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return MDP_ERR_CUDA;
   const long long buf_doubles = (long long)((kNoAllocScratchBytes - off_buf) / sizeof(double));
   if (mdp::launch_solve_raw((const mdp::SubDesc *)b, hd, (const double *)(b + off_tab), (const uint8_t *)(b + off_piv),

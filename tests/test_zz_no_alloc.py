@@ -38,28 +38,29 @@ def test_noalloc_rejects_grids_beyond_its_scratch(mdp):
     from paper_2103_12172_gb300 import _lib
     L = _lib.lib()
     assert L.mdp_ap_solve_noalloc_limit_bytes() == 32 << 20
-    for n in (385, 1025):                                      # tables alone exceed 32 MiB
+    for n in (705, 1025):                                      # factor rows + one right-hand side > 32 MiB
         big = W.small_subdomain(n, 40.0, W.AP_DIRX_SOMMY, 2)
         rc = L.mdp_ap_solve_noalloc(c_sub(mdp, big), 1, ctypes.c_void_p(0), ctypes.c_void_p(0), 0,
                                     ctypes.c_void_p(0))
         assert rc == _lib.MDP_ERR_ARG
-    fits = W.small_subdomain(321, 40.0, W.AP_DIRX_SOMMY, 2)    # zero right-hand sides: size check only
+    fits = W.small_subdomain(641, 40.0, W.AP_DIRX_SOMMY, 2)    # zero right-hand sides: size check only
     assert L.mdp_ap_solve_noalloc(c_sub(mdp, fits), 0, ctypes.c_void_p(0), ctypes.c_void_p(0), 0,
                                   ctypes.c_void_p(0)) == 0
 
 
 def scratch_chunk(mdp, sub):
     """Right-hand sides per chunk of the scratch's mode-space buffer (an estimate within one
-    of the library's own, from the host tables of the same subdomain)."""
+    of the library's own: the descriptor, the factor rows, the sine table and the pivot flags
+    of the same subdomain come first)."""
     from paper_2103_12172_gb300 import _lib
     p = mdp.Plan([sub], host_only=True)
-    nd, npv = ctypes.c_longlong(), ctypes.c_longlong()
-    p.L.mdp_plan_table_sizes(p.handle, ctypes.byref(nd), ctypes.byref(npv))
     info = p.sub_info(0)
     p.close()
     a = lambda v: (v + 255) // 256 * 256                      # noqa: E731
-    used = a(512) + a(nd.value * 8) + a(npv.value)
-    return (_lib.lib().mdp_ap_solve_noalloc_limit_bytes() - used) // (info["Nq"] * info["Nt"] * 16)
+    qt = info["Nq"] * info["Nt"]
+    sin_off = (qt * (8 if info["cplx"] else 4) + 31) // 32 * 32
+    used = a(512) + a((sin_off + 4 * info["Nx"]) * 8) + a(qt)
+    return (_lib.lib().mdp_ap_solve_noalloc_limit_bytes() - used) // (qt * 16)
 
 
 @pytest.mark.gpu
